@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Throughput of the compositional sparse-voxel rasterizer on one GB300.
+
+A step is one pass of the whole hot path over one frame of the compositional
+workload (500k-leaf LiDAR-shaped background + 3 actors of 20k leaves, SH degree
+3, one 1920x1080 camera): forward render through the C ABI, then the backward
+replay for a fixed upstream gradient.  The metric is rendered megapixels per
+second, fwd+bwd (``value``); the forward alone is reported beside it.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the rendering stream with an L2 flush (a 512 MB write) between steps outside
+the events; barrier + synchronize around the timed loop; max over ranks.
+``e2e`` repeats the step through the public API with the upstream gradient
+copied from pinned host memory and every result (images and gradients) copied
+back each step.  ``cpu_baseline`` times the FP64 oracle on a bounded pixel
+sample of the same frame on the host cores.
+
+``--impl reference`` runs the oracle as the reference arm (no GPU work).
+Under torchrun every rank renders its own frame (weak scaling, no collective).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+METRIC = "Mpix/s fwd & fwd+bwd; served p50/p99 latency vs plain path, 1 GB300"
+WORKLOAD = ("compositional fwd+bwd: LiDAR-shaped background 500k leaves (levels 6-12, 200 m root) + 3 actors x "
+            "20k leaves on straight lanes, SH degree 3, one 1920x1080 camera, K=1, eps_stop=1e-4")
+
+# FP32 operations per algorithmic unit, counted from the kernel source (FMA = 2)
+F_TEST = 28          # voxel slab test (per pixel x list entry examined)
+F_BOX = 50           # actor clip-box test (per pixel x box query)
+F_SAMPLE = 41        # one midpoint sample: position, trilinear (7 lerps), activation
+F_SEG = 30           # per segment: clipping, alpha, composite update, stop test
+F_SAMPLE_BWD = 74    # sample + trilinear weights and d tau / d dens
+F_SEG_BWD = 127      # segment + gradient of tau, colour, warp reduction
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    p.add_argument("--seed", type=int, default=0)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception as e:
+            log("clock sampler unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+
+def workload(seed):
+    import synth
+    return synth.config2(seed)
+
+
+def upstream(cam, seed, device):
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed + 17)
+    P = cam.W * cam.H
+    return (torch.randn((P, 3), generator=g).to(device), (0.01 * torch.randn((P,), generator=g)).to(device),
+            torch.randn((P,), generator=g).to(device))
+
+
+def stage_models(stats, work, n_vox_total, n_pix, K, sh_bytes_per_vox, key_bits):
+    """Algorithmic bytes (HBM stages) or FP32 ops (compositing) per launch of each stage."""
+    V, nv, P, T = n_vox_total, stats["n_visible"], stats["n_pairs"], stats["n_tiles"]
+    vb = max(1, math.ceil(key_bits / 8))       # radix passes of the depth-key sort
+    tb = max(1, math.ceil(math.log2(max(T, 2)) / 8))
+    tests, boxes, segs = work["tests"], work["box_tests"], work["segments"]
+    return {
+        "project": ("hbm", V * 32),
+        "records": ("hbm", nv * (4 + 8 + 32 + sh_bytes_per_vox + 4 + 8 + 64 + 4 + 8)),
+        "emit": ("hbm", nv * 16 + P * 8),
+        "sort_vox": ("hbm", vb * nv * 32),
+        "sort_pairs": ("hbm", tb * P * 20),
+        "ranges": ("hbm", P * 4 + T * 8),
+        "composite_fwd": ("alu", tests * F_TEST + boxes * F_BOX + segs * (K * F_SAMPLE + F_SEG)),
+        "composite_bwd": ("alu", tests * F_TEST + boxes * F_BOX + segs * (K * F_SAMPLE_BWD + F_SEG_BWD)),
+        "sh_bwd": ("hbm", nv * (48 + 16 + sh_bytes_per_vox + 64 + 2 * sh_bytes_per_vox + 4)),
+    }
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2606_23031_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2606_23031_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel):
+    try:
+        t = json.load(open(TRAFFIC))
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    v = t.get("per_launch_bytes", {}).get(kernel)
+    return v
+
+
+def peaks():
+    try:
+        m = json.load(open(MEASURED_PEAKS))
+        return {"hbm_gbs": float(m["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(m.get("sm_max_mhz", 2070.0))}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm (the FP64 oracle on host cores)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(sc, cam, n_px, seed):
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(cam.W * cam.H, size=n_px, replace=False))
+    g = np.random.default_rng(seed + 1)
+    g_rgb, g_d, g_a = g.normal(size=(n_px, 3)), 0.01 * g.normal(size=n_px), g.normal(size=n_px)
+    t0 = time.perf_counter()
+    oracle.render(sc.octrees, sc.poses, cam, oracle.Opts(1, 1e-4), pixels=pix)
+    oracle.backward(sc.octrees, sc.poses, cam, g_rgb, g_d, g_a, oracle.Opts(1, 1e-4), pixels=pix)
+    return time.perf_counter() - t0
+
+
+def calibrate_oracle(sc, cam, seconds, seed):
+    t = oracle_sample(sc, cam, 16, seed)
+    per_px = t / 16
+    n = int(min(max(seconds / max(per_px, 1e-6), 16), cam.W * cam.H, 8192))
+    return n, per_px
+
+
+def cpu_baseline(sc, cam, seconds, seed):
+    n, _ = calibrate_oracle(sc, cam, seconds, seed)
+    t = oracle_sample(sc, cam, n, seed + 5)
+    return {"value": n / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} uniformly sampled pixels of the 1920x1080 frame, forward + backward, FP64 brute force "
+                      f"over every voxel, {os.cpu_count()} threads ({t:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    sc, cams, _ = workload(args.seed)
+    cam = cams[0]
+    n, per_px = calibrate_oracle(sc, cam, max(1.0, min(args.cpu_seconds, 60.0 / max(args.steps + args.warmup, 1))),
+                                 args.seed)
+    for w in range(args.warmup):
+        oracle_sample(sc, cam, max(8, n // 8), args.seed + 100 + w)
+    times = [oracle_sample(sc, cam, n, args.seed + 200 + s) for s in range(args.steps)]
+    tot = sum(times)
+    value = n * args.steps / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_pixels_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n} sampled pixels per step, fwd+bwd, FP64 brute force"},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_23031_gb300 as dv
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    dv.load()
+    sc, cams, _ = workload(args.seed + rank)
+    cam = cams[0]
+    ds = [dv.DeviceOctree.from_host(o, dev) for o in sc.octrees]
+    opts = dv.make_opts(1, 1e-4)
+    g_rgb, g_d, g_a = upstream(cam, args.seed, dev)
+    d_dens = [torch.zeros_like(o.dens) for o in ds]
+    d_sh = [torch.zeros_like(o.sh) for o in ds]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = dv.default_context(local)
+    stream = torch.cuda.current_stream()
+    n_pix = cam.W * cam.H
+
+    def step():
+        rgb, depth, alpha, st = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
+        dv.dv_render_backward(st, g_rgb, g_d, g_a, d_dens, d_sh)
+        return st
+
+    def fwd_only():
+        dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx)
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        st = step()
+        st.free()
+    sync_all()
+    # one extra (untimed) step for the work counters and sizes of this frame
+    st = step()
+    stats = st.stats(0)
+    work = st.work(0)
+    st.free()
+
+    # ---- timed fwd+bwd ----
+    clk = ClockSampler(local)
+    clk.start()
+    launches0 = dv.dv_launch_count()
+    ctx.profile(True)
+    ctx.profile_read()
+    sync_all()
+    wall0 = time.perf_counter()
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = step()
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+        st.free()
+    sync_all()
+    wall = time.perf_counter() - wall0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = dv.dv_launch_count() - launches0
+    clocks = clk.stop()
+
+    # ---- timed forward only ----
+    for _ in range(2):
+        fwd_only()
+    sync_all()
+    ms_f = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fwd_only()
+        b.record(stream)
+        b.synchronize()
+        ms_f += a.elapsed_time(b)
+    sync_all()
+
+    t_step = torch.tensor([ms / args.steps, ms_f / args.steps], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    ms_step, ms_fwd = float(t_step[0]), float(t_step[1])
+    value = world * n_pix / (ms_step * 1e-3) / 1e6
+    value_fwd = world * n_pix / (ms_fwd * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_g = [x.cpu().pin_memory() for x in (g_rgb, g_d, g_a)]
+        d_g = [torch.empty_like(x) for x in (g_rgb, g_d, g_a)]
+        h_out = [torch.empty((n_pix, 3), pin_memory=True), torch.empty((n_pix,), pin_memory=True),
+                 torch.empty((n_pix,), pin_memory=True)]
+        h_grad = [torch.empty(t.shape, pin_memory=True) for t in d_dens + d_sh]
+        h2d = sum(x.numel() * 4 for x in h_g)
+        d2h = sum(x.numel() * 4 for x in h_out) + sum(x.numel() * 4 for x in h_grad)
+
+        def e2e_step():
+            for hd, dd in zip(h_g, d_g):
+                dd.copy_(hd, non_blocking=True)
+            rgb, depth, alpha, st = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
+            dv.dv_render_backward(st, d_g[0], d_g[1], d_g[2], d_dens, d_sh)
+            for ho, do in zip(h_out, (rgb, depth, alpha)):
+                ho.copy_(do, non_blocking=True)
+            for hg, dg in zip(h_grad, d_dens + d_sh):
+                hg.copy_(dg, non_blocking=True)
+            return st
+
+        for _ in range(2):
+            e2e_step().free()
+        sync_all()
+        ms_e = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = e2e_step()
+            b.record(stream)
+            b.synchronize()
+            ms_e += a.elapsed_time(b)
+            st.free()
+        t_e = torch.tensor([ms_e / args.steps], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n_pix / (float(t_e[0]) * 1e-3) / 1e6, "unit": "Mpix/s",
+               "ms_per_step": float(t_e[0]), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- roofline of the dominant stage ----
+    pk = peaks()
+    alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s, FP32 FMA issue at max clock
+    sh_bytes = sum(o.n * (o.sh_degree + 1) ** 2 * 12 for o in sc.octrees) / max(sum(o.n for o in sc.octrees), 1)
+    max_level = max(int((np.asarray(o.key, np.uint64) >> np.uint64(57)).max()) for o in sc.octrees if o.n)
+    key_bits = 3 * max_level + max(1, math.ceil(math.log2(len(sc.octrees))))
+    models = stage_models(stats, work, sum(o.n for o in sc.octrees), n_pix, 1, sh_bytes, key_bits)
+    kernels = {}
+    for name, (tot_ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        avg = tot_ms / cnt
+        ent = {"ms_total": tot_ms, "runs": cnt, "ms_per_run": avg}
+        if name in models:
+            bound, amount = models[name]
+            if bound == "hbm":
+                ach = amount / (avg * 1e-3) / 1e9
+                ent.update({"bound": "hbm", "algorithmic_bytes": amount, "achieved_gbs": ach,
+                            "frac": ach / pk["hbm_gbs"]})
+            else:
+                ach = amount / (avg * 1e-3) / 1e12
+                ent.update({"bound": "alu", "algorithmic_flops": amount, "achieved_tflops": ach,
+                            "frac": ach / alu_peak})
+        kernels[name] = ent
+    dom = max((k for k in kernels if k in models), key=lambda k: kernels[k]["ms_total"])
+    d = kernels[dom]
+    if d["bound"] == "hbm":
+        roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": d["frac"], "traffic": load_traffic(dom), "kernel": dom,
+                "peak_source": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback"}
+    else:
+        roof = {"bound": "alu", "achieved": d["achieved_tflops"], "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": d["frac"], "traffic": load_traffic(dom), "kernel": dom,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, cam, args.cpu_seconds, args.seed)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "pixels_per_step": n_pix, "per_rank": "one frame per rank",
+                           "l2": "flushed between timed steps (512 MB write outside the step events)",
+                           "visible_voxels": stats["n_visible"], "pairs": stats["n_pairs"]},
+                "fwd": {"value": value_fwd, "unit": "Mpix/s", "ms_per_step": ms_fwd},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "gpu_launches_per_step": launches / max(args.steps, 1), "wall_s_timed": wall,
+                "work": work, "kernels": kernels}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

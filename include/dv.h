@@ -1,0 +1,184 @@
+/*
+ * dv.h -- C ABI of the GB300 compositional sparse-voxel rasterizer.
+ *
+ * The library renders one static background octree plus any number of rigid
+ * actor octrees in a single pass and back-propagates through that pass
+ * (DrivingVoxels, Sec. 3.4 and Algorithm 1 of the supplement):
+ *
+ *   dv_render           octrees[], poses[], cameras[] -> RGB, depth, alpha
+ *   dv_render_backward  dL/dRGB, dL/ddepth, dL/dalpha -> dL/d corner densities,
+ *                       dL/d SH coefficients
+ *
+ * Everything on the compute path runs in this library's sm_103a kernels; the
+ * caller only supplies device buffers and a CUDA stream.  No function throws;
+ * every fallible call returns a dv_status and, on failure, leaves a message
+ * retrievable with dv_last_error().
+ *
+ * Conventions shared by every call
+ *  - Pointers named "device" are CUDA device pointers on the context's device;
+ *    the caller owns them and keeps them alive until the work enqueued on the
+ *    given stream has finished.  Structs passed by host pointer are read
+ *    during the call only.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All work is enqueued on it.  A render call synchronises that stream once
+ *    per camera to size its pair buffers (the only host wait on the path).
+ *  - Leaf keys: bits [0,19) = i, [19,38) = j, [38,57) = k, [57,62) = level.
+ *    A leaf spans min = center - root_size/2 + (i,j,k) * s to min + s with
+ *    s = root_size / 2^level, in its octree's local frame (Sec. 3.1, where each
+ *    leaf is stored as a level and an integer grid index).
+ *  - Corner c of the 8 densities sits at offset (c&1, (c>>1)&1, (c>>2)&1).
+ *  - Cameras use OpenCV axes (x right, y down, z forward); pixel (u,v) casts
+ *    the ray through (u+0.5, v+0.5); depth is distance along the unit ray.
+ *  - Output images are row-major [H][W] (RGB: [H][W][3]); for several
+ *    cameras the images are concatenated in camera order.
+ *
+ * Thread safety: a context may be used by one host thread at a time.  Distinct
+ * contexts are independent.
+ */
+#ifndef DV_H
+#define DV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DV_OK = 0,
+    DV_ERR_INVALID_ARG = 1,  /* a size, pointer, level or option is out of range */
+    DV_ERR_INVALID_POSE = 2, /* a rotation is not orthonormal with det +1 (tol 1e-5) */
+    DV_ERR_CAPACITY = 3,     /* a size exceeds the library's fixed limits */
+    DV_ERR_CUDA = 4,         /* a CUDA runtime call failed (message has the CUDA error) */
+    DV_ERR_TIMEOUT = 5,      /* a bounded wait ran out (serving loop) */
+    DV_ERR_NOMEM = 6         /* device or host allocation failed */
+} dv_status;
+
+enum { DV_ROLE_BG = 0, DV_ROLE_ACTOR = 1 };
+enum { DV_ACT_EXPLIN = 0, DV_ACT_IDENTITY = 1 };
+
+#define DV_MAX_OCTREES 128   /* background + up to 127 actors per call */
+#define DV_MAX_LEVEL 16      /* deepest leaf level accepted */
+#define DV_MAX_IMAGE 16384   /* maximum W and H */
+#define DV_MAX_SH_DEGREE 3
+
+typedef struct dv_ctx dv_ctx;
+typedef struct dv_state dv_state;
+
+/* One octree (Sec. 3.1 background, Sec. 3.2 actor in its canonical frame). */
+typedef struct {
+    int64_t n_vox;          /* number of leaves (>= 0, < 2^31 summed over a call) */
+    int32_t sh_degree;      /* 0..3 */
+    int32_t role;           /* DV_ROLE_BG for octree 0, DV_ROLE_ACTOR for the others */
+    int32_t max_level;      /* upper bound on the leaf levels present (0..16); a larger
+                               level found on the device fails the call */
+    int32_t reserved;
+    double center[3];       /* AABB centre (local frame) */
+    double root_size;       /* AABB edge length (local frame) */
+    float clip_half[3];     /* actor: clip box half extents around the local origin;
+                               the actor owns the ray interval inside this box
+                               (Sec. 3.4); ignored for the background */
+    const uint64_t* key;    /* device [n_vox] leaf keys (borrowed) */
+    const float* dens;      /* device [n_vox][8] raw corner densities (borrowed) */
+    const float* sh;        /* device [n_vox][(deg+1)^2][3] SH coefficients (borrowed) */
+} dv_octree;
+
+/* Rigid transform local -> world, p_w = R p_l + t, R row-major (Sec. 3.2 T_t^i). */
+typedef struct {
+    float R[9];
+    float t[3];
+} dv_pose;
+
+typedef struct {
+    int32_t W, H;           /* image size in pixels (0 allowed: nothing rendered) */
+    float fx, fy, cx, cy;   /* pinhole intrinsics (fx, fy > 0) */
+    dv_pose cam_to_world;   /* camera pose */
+    float near_, far_;      /* ray distance range, 0 < near < far */
+} dv_camera;
+
+typedef struct {
+    int32_t K;              /* midpoint samples per voxel segment, 1..16 */
+    float eps_stop;         /* stop a ray once its transmittance drops below this (Alg. 1) */
+    int32_t activation;     /* DV_ACT_EXPLIN (default) or DV_ACT_IDENTITY */
+    int32_t reserved;
+} dv_opts;
+
+/* Creates a context on CUDA device `device`.  The context owns a stream-ordered
+ * memory pool for the library's scratch; *ctx is NULL on failure. */
+dv_status dv_create(dv_ctx** ctx, int32_t device);
+void dv_destroy(dv_ctx* ctx);
+/* Message of the last failing call on this context ("" if none). */
+const char* dv_last_error(const dv_ctx* ctx);
+/* Library version string. */
+const char* dv_version(void);
+
+/*
+ * Forward render (Sec. 3.4, Algorithm 1).  For each pixel of each camera the
+ * ray is split into background and actor intervals by the actor clip boxes
+ * (the box entered first owns any overlap), and every interval is composited
+ * front to back from its octree's voxels with transmittance carried across
+ * the borders; a ray stops once T < opts->eps_stop.
+ *
+ *   oct[n_oct], poses[n_oct]  host arrays; oct[0] is the background (its pose
+ *                             places it in the world, normally identity)
+ *   cams[n_cam]               host array
+ *   rgb, depth, alpha         device outputs, concatenated per camera:
+ *                             rgb [sum H*W][3], depth/alpha [sum H*W]; alpha = 1 - T
+ *   saved                     if non-NULL, receives a state for
+ *                             dv_render_backward (free it with dv_state_free);
+ *                             the state borrows rgb/depth/alpha and the octree
+ *                             buffers: they must stay unchanged until it is freed
+ * Errors: DV_ERR_INVALID_ARG / DV_ERR_INVALID_POSE / DV_ERR_CAPACITY before any
+ * work is enqueued; DV_ERR_CUDA or DV_ERR_INVALID_ARG (a leaf level above its
+ * octree's max_level) after; the outputs are then undefined.
+ */
+dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* poses, const dv_camera* cams,
+                    int32_t n_cam, const dv_opts* opts, float* rgb, float* depth, float* alpha, dv_state** saved,
+                    void* stream);
+
+/*
+ * Backward of dv_render (gradients flow through every voxel segment, Sec. 3.4).
+ * Given dL/dRGB [sum H*W][3], dL/ddepth and dL/dalpha [sum H*W] (device; any of
+ * the three may be NULL = zero), ADDS dL/d dens into d_dens[i] ([n_vox][8]) and
+ * dL/d SH into d_sh[i] ([n_vox][nsh][3]) for every octree i (host arrays of
+ * device pointers; an entry may be NULL to skip that octree).  The replay
+ * follows the forward's segments exactly, including its early stop.
+ * Summation order of the per-voxel gradient sums is not fixed (atomics).
+ */
+dv_status dv_render_backward(dv_ctx* ctx, dv_state* state, const float* d_rgb, const float* d_depth,
+                             const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream);
+
+/* Releases a saved state (stream-ordered on the stream of its render call). */
+void dv_state_free(dv_state* state);
+
+/* Sizes of a saved state, per camera `cam`: visible voxels, (tile, voxel)
+ * pairs, tiles.  Returns DV_ERR_INVALID_ARG for a bad index. */
+dv_status dv_state_stats(const dv_state* state, int32_t cam, int64_t* n_visible, int64_t* n_pairs,
+                         int64_t* n_tiles);
+
+/* Work done by the forward compositing of camera `cam` of a saved state:
+ * voxel slab tests (pixel x list entry examined before the ray stopped),
+ * actor clip-box tests, and composited segments.  Synchronises the state's
+ * stream.  These are the algorithmic units behind the compositing roofline. */
+dv_status dv_state_work(const dv_state* state, int32_t cam, uint64_t* tests, uint64_t* box_tests,
+                        uint64_t* segments);
+
+/* Number of kernel launches this library has issued in this process (all
+ * contexts); reset to zero when `reset` is non-zero (returns the old value). */
+long long dv_launch_count(int32_t reset);
+
+/* Per-stage timing with CUDA events recorded on the call's stream.  While
+ * enabled, every stage below is bracketed by events; dv_profile_read()
+ * synchronises those events and returns, for stage k in names order, the
+ * summed milliseconds and the number of times the stage ran, then resets the
+ * counters.  Stages: "project", "scan", "compact", "sort_vox", "records",
+ * "emit", "sort_pairs", "ranges", "composite_fwd", "composite_bwd", "sh_bwd". */
+dv_status dv_profile_enable(dv_ctx* ctx, int32_t on);
+dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DV_H */

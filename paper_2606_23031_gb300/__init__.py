@@ -1,0 +1,433 @@
+"""GB300-native compositional sparse-voxel rasterizer (DrivingVoxels hot path).
+
+A thin Python layer over the C ABI in ``include/dv.h`` (``libdv.so``, built
+in-tree from ``csrc/`` for sm_103a).  Everything that renders or
+differentiates runs inside that library's CUDA kernels; this module only
+marshals torch device tensors into the ABI structs and passes the current
+CUDA stream.  There is no fallback: if the library cannot be loaded, every
+entry point raises.
+
+Names follow the ABI: :func:`dv_render`, :func:`dv_render_backward`,
+:func:`dv_state_free`, plus :class:`RenderFn` (a ``torch.autograd.Function``
+whose backward replays the compositing through ``dv_render_backward``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_INC = os.path.join(_ROOT, "include")
+LIB_PATH = os.path.join(_HERE, "libdv.so")
+SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV_ERR_TIMEOUT, DV_ERR_NOMEM = range(7)
+DV_ROLE_BG, DV_ROLE_ACTOR = 0, 1
+DV_ACT_EXPLIN, DV_ACT_IDENTITY = 0, 1
+DV_MAX_OCTREES = 128
+KERNELS = ("project", "scan", "compact", "sort_vox", "records", "emit", "sort_pairs", "ranges", "composite_fwd",
+           "composite_bwd", "sh_bwd")
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a (in parallel) and link libdv.so in-tree."""
+    srcs = [os.path.join(_CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(_CSRC, "dv_internal.cuh"), os.path.join(_INC, "dv.h")]
+    if not force and os.path.exists(LIB_PATH):
+        t = os.path.getmtime(LIB_PATH)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return LIB_PATH
+    bdir = os.path.join(_HERE, "_build")
+    os.makedirs(bdir, exist_ok=True)
+    nvcc = _nvcc()
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + _INC, "-I" + _CSRC]
+
+    def one(src):
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [nvcc] + flags + ["-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = list(ex.map(one, srcs))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ---------------------------------------------------------------------------
+# ABI structs
+# ---------------------------------------------------------------------------
+
+class dv_octree(C.Structure):
+    _fields_ = [("n_vox", C.c_int64), ("sh_degree", C.c_int32), ("role", C.c_int32), ("max_level", C.c_int32),
+                ("reserved", C.c_int32), ("center", C.c_double * 3), ("root_size", C.c_double),
+                ("clip_half", C.c_float * 3), ("key", C.c_void_p), ("dens", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class dv_pose(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3)]
+
+
+class dv_camera(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("cam_to_world", dv_pose), ("near_", C.c_float), ("far_", C.c_float)]
+
+
+class dv_opts(C.Structure):
+    _fields_ = [("K", C.c_int32), ("eps_stop", C.c_float), ("activation", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libdv.so (building it first if it is missing or stale).  Raises if that fails:
+    there is no CPU or eager fallback for any entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if path is None:
+        build()
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA extension {p} is missing; run build()")
+    lib = C.CDLL(p)
+    lib.dv_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32]
+    lib.dv_create.restype = C.c_int
+    lib.dv_destroy.argtypes = [C.c_void_p]
+    lib.dv_destroy.restype = None
+    lib.dv_last_error.argtypes = [C.c_void_p]
+    lib.dv_last_error.restype = C.c_char_p
+    lib.dv_version.restype = C.c_char_p
+    lib.dv_render.argtypes = [C.c_void_p, C.POINTER(dv_octree), C.c_int32, C.POINTER(dv_pose), C.POINTER(dv_camera),
+                              C.c_int32, C.POINTER(dv_opts), C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.POINTER(C.c_void_p), C.c_void_p]
+    lib.dv_render.restype = C.c_int
+    lib.dv_render_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]
+    lib.dv_render_backward.restype = C.c_int
+    lib.dv_state_free.argtypes = [C.c_void_p]
+    lib.dv_state_free.restype = None
+    lib.dv_state_stats.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]
+    lib.dv_state_stats.restype = C.c_int
+    lib.dv_state_work.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                  C.POINTER(C.c_uint64)]
+    lib.dv_state_work.restype = C.c_int
+    lib.dv_launch_count.argtypes = [C.c_int32]
+    lib.dv_launch_count.restype = C.c_longlong
+    lib.dv_profile_enable.argtypes = [C.c_void_p, C.c_int32]
+    lib.dv_profile_enable.restype = C.c_int
+    lib.dv_profile_read.argtypes = [C.c_void_p, C.POINTER(C.c_char_p), C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64)]
+    lib.dv_profile_read.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class DVError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dv status {status}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------------------
+# context / scene marshalling
+# ---------------------------------------------------------------------------
+
+class Context:
+    """Owns a dv_ctx (one per device and host thread)."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = C.c_void_p()
+        st = lib.dv_create(C.byref(h), int(device))
+        if st != DV_OK:
+            raise DVError(st, "dv_create failed")
+        self.handle = h
+        self.device = device
+
+    def check(self, st):
+        if st != DV_OK:
+            raise DVError(st, load().dv_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            load().dv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, on: bool):
+        self.check(load().dv_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, names=KERNELS):
+        n = len(names)
+        arr = (C.c_char_p * n)(*[s.encode() for s in names])
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        self.check(load().dv_profile_read(self.handle, arr, n, ms, cnt))
+        return {names[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+_ctx_cache = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    import torch
+    d = torch.cuda.current_device() if device is None else device
+    if d not in _ctx_cache:
+        _ctx_cache[d] = Context(d)
+    return _ctx_cache[d]
+
+
+class DeviceOctree:
+    """Device-resident octree tensors (torch) plus the metadata of dv_octree."""
+
+    def __init__(self, key, dens, sh, sh_degree, center, root_size, role, clip_half=(0.0, 0.0, 0.0), max_level=None):
+        self.key, self.dens, self.sh = key, dens, sh
+        self.sh_degree, self.center, self.root_size = int(sh_degree), tuple(center), float(root_size)
+        self.role, self.clip_half = int(role), tuple(clip_half)
+        if max_level is None:
+            max_level = 16
+        self.max_level = int(max_level)
+
+    @property
+    def n(self):
+        return int(self.key.shape[0])
+
+    @staticmethod
+    def from_host(oc, device="cuda"):
+        import numpy as np
+        import torch
+        key = torch.from_numpy(np.ascontiguousarray(oc.key).view(np.int64)).to(device)
+        dens = torch.from_numpy(np.ascontiguousarray(oc.dens, np.float32)).to(device)
+        sh = torch.from_numpy(np.ascontiguousarray(oc.sh, np.float32)).to(device)
+        lv = (np.asarray(oc.key, np.uint64) >> np.uint64(57)) & np.uint64(31)
+        ml = int(lv.max()) if lv.size else 0
+        return DeviceOctree(key, dens, sh, oc.sh_degree, oc.center, oc.root_size, oc.role, oc.clip_half, ml)
+
+    def struct(self, dens=None, sh=None) -> dv_octree:
+        o = dv_octree()
+        d = self.dens if dens is None else dens
+        s = self.sh if sh is None else sh
+        for t in (self.key, d, s):
+            if t.numel() and (not t.is_cuda or not t.is_contiguous()):
+                raise ValueError("octree tensors must be contiguous CUDA tensors")
+        o.n_vox = self.n
+        o.sh_degree = self.sh_degree
+        o.role = self.role
+        o.max_level = self.max_level
+        for k in range(3):
+            o.center[k] = float(self.center[k])
+            o.clip_half[k] = float(self.clip_half[k])
+        o.root_size = self.root_size
+        o.key = self.key.data_ptr() if self.n else None
+        o.dens = d.data_ptr() if self.n else None
+        o.sh = s.data_ptr() if self.n else None
+        return o
+
+
+def make_pose(p) -> dv_pose:
+    import numpy as np
+    P = dv_pose()
+    R = np.asarray(p.R, np.float32).reshape(9)
+    t = np.asarray(p.t, np.float32).reshape(3)
+    for i in range(9):
+        P.R[i] = float(R[i])
+    for i in range(3):
+        P.t[i] = float(t[i])
+    return P
+
+
+def make_camera(cam) -> dv_camera:
+    c = dv_camera()
+    c.W, c.H = int(cam.W), int(cam.H)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.cam_to_world = make_pose(cam.pose)
+    c.near_, c.far_ = float(cam.near), float(cam.far)
+    return c
+
+
+def make_opts(K=1, eps_stop=1e-4, activation=DV_ACT_EXPLIN) -> dv_opts:
+    o = dv_opts()
+    o.K, o.eps_stop, o.activation, o.reserved = int(K), float(eps_stop), int(activation), 0
+    return o
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# ABI-named entry points
+# ---------------------------------------------------------------------------
+
+class State:
+    """Owning wrapper of a dv_state*; freed stream-ordered on its render stream."""
+
+    def __init__(self, ctx: Context, handle, n_cam: int, keep):
+        self.ctx, self.handle, self.n_cam, self.keep = ctx, handle, n_cam, keep
+
+    def stats(self, cam=0):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self.ctx.check(load().dv_state_stats(self.handle, cam, C.byref(a), C.byref(b), C.byref(c)))
+        return {"n_visible": a.value, "n_pairs": b.value, "n_tiles": c.value}
+
+    def work(self, cam=0):
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        self.ctx.check(load().dv_state_work(self.handle, cam, C.byref(a), C.byref(b), C.byref(c)))
+        return {"tests": a.value, "box_tests": b.value, "segments": c.value}
+
+    def free(self):
+        if self.handle:
+            load().dv_state_free(self.handle)
+            self.handle = None
+            self.keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dv_render(octrees, poses, cams, opts=None, *, ctx: Context | None = None, save_state=False, out=None,
+              dens=None, sh=None, stream=None):
+    """Forward render; returns (rgb [P,3], depth [P], alpha [P], state or None) with P = sum of H*W
+    over the cameras (images concatenated in camera order)."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = len(octrees)
+    oct_arr = (dv_octree * n)(*[o.struct(None if dens is None else dens[i], None if sh is None else sh[i])
+                                for i, o in enumerate(octrees)])
+    pose_arr = (dv_pose * n)(*[make_pose(p) for p in poses])
+    cam_arr = (dv_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+    opts = opts or make_opts()
+    P = sum(int(c.W) * int(c.H) for c in cams)
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        rgb = torch.empty((P, 3), device=dev, dtype=torch.float32)
+        depth = torch.empty((P,), device=dev, dtype=torch.float32)
+        alpha = torch.empty((P,), device=dev, dtype=torch.float32)
+    else:
+        rgb, depth, alpha = out
+    st = C.c_void_p()
+    status = lib.dv_render(ctx.handle, oct_arr, n, pose_arr, cam_arr, len(cams), C.byref(opts),
+                           C.c_void_p(rgb.data_ptr() if P else None), C.c_void_p(depth.data_ptr() if P else None),
+                           C.c_void_p(alpha.data_ptr() if P else None), C.byref(st) if save_state else None,
+                           _stream_ptr(stream))
+    ctx.check(status)
+    state = State(ctx, st, len(cams), (octrees, dens, sh, rgb, depth, alpha)) if save_state else None
+    return rgb, depth, alpha, state
+
+
+def dv_render_backward(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_dens=None, d_sh=None, stream=None):
+    """Adds dL/d dens and dL/d sh into the given per-octree tensors (lists; None entries skipped)."""
+    lib = load()
+    n = len(d_dens) if d_dens is not None else len(d_sh)
+    pd = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_dens or [None] * n)])
+    ps = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_sh or [None] * n)])
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    status = lib.dv_render_backward(state.ctx.handle, state.handle, ptr(d_rgb), ptr(d_depth), ptr(d_alpha), pd, ps,
+                                    _stream_ptr(stream))
+    state.ctx.check(status)
+
+
+def dv_state_free(state: State):
+    state.free()
+
+
+def dv_launch_count(reset: bool = False) -> int:
+    """Kernel launches issued by the library in this process."""
+    return int(load().dv_launch_count(1 if reset else 0))
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+def _autograd_fn():
+    import torch
+
+    class RenderFn(torch.autograd.Function):
+        """Differentiable render w.r.t. every octree's corner densities and SH coefficients.
+        forward(meta, *tensors) with tensors = dens_0..dens_{n-1}, sh_0..sh_{n-1}."""
+
+        @staticmethod
+        def forward(ctx_, meta, *tensors):
+            octrees, poses, cams, opts = meta
+            n = len(octrees)
+            dens, sh = list(tensors[:n]), list(tensors[n:])
+            rgb, depth, alpha, state = dv_render(octrees, poses, cams, opts, save_state=True,
+                                                 dens=[d.detach() for d in dens], sh=[s.detach() for s in sh])
+            ctx_.state = state
+            ctx_.n = n
+            ctx_.shapes = [(d.shape, s.shape) for d, s in zip(dens, sh)]
+            return rgb, depth, alpha
+
+        @staticmethod
+        def backward(ctx_, g_rgb, g_depth, g_alpha):
+            import torch as T
+            n = ctx_.n
+            st = ctx_.state
+            dev = g_rgb.device if g_rgb is not None else g_alpha.device
+            d_dens = [T.zeros(s[0], device=dev, dtype=T.float32) for s in ctx_.shapes]
+            d_sh = [T.zeros(s[1], device=dev, dtype=T.float32) for s in ctx_.shapes]
+            c = lambda t: None if t is None else t.contiguous()
+            dv_render_backward(st, c(g_rgb), c(g_depth), c(g_alpha), d_dens, d_sh)
+            st.free()
+            ctx_.state = None
+            return (None, *d_dens, *d_sh)
+
+    return RenderFn
+
+
+_RenderFn = None
+
+
+def __getattr__(name):
+    global _RenderFn
+    if name == "RenderFn":
+        if _RenderFn is None:
+            _RenderFn = _autograd_fn()
+        return _RenderFn
+    raise AttributeError(name)
+
+
+def render(octrees, poses, cams, opts=None, dens=None, sh=None):
+    """Autograd entry: gradients flow to ``dens``/``sh`` (lists of per-octree tensors; defaults
+    to the octrees' own tensors)."""
+    global _RenderFn
+    if _RenderFn is None:
+        _RenderFn = _autograd_fn()
+    dens = [o.dens for o in octrees] if dens is None else dens
+    sh = [o.sh for o in octrees] if sh is None else sh
+    return _RenderFn.apply((octrees, poses, cams, opts or make_opts()), *dens, *sh)

@@ -1,0 +1,135 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dv.h"
+
+#define DV_TILE 16
+#define DV_BLOCK 256  // one thread per pixel of a 16x16 tile
+
+// Per (camera, octree) constants, computed on the host in double and rounded once.
+struct OctParams {
+    float A[9];          // unit camera-frame ray direction -> octree-local direction (R_i^T R_c)
+    float M[9];          // octree-local point -> camera frame, rotation (R_c^T R_i)
+    float m[3];          //   ... translation (R_c^T (t_i - t_c))
+    float o_loc[3];      // camera centre in the octree's local frame (R_i^T (t_c - t_i))
+    float clip_half[3];  // actor clip box half extents
+    float root_min[3];   // center - root/2
+    float root_size;
+    int32_t role;
+    int32_t sh_degree;
+    int32_t max_level;
+    int16_t rect[4];     // actor clip box tile rectangle [tx0, ty0, tx1, ty1] (tx0 > tx1: off screen)
+    int64_t O2[3];       // floor(2 * (o_loc - root_min) / root * 2^Lkey): BSP side tests in integers
+    int64_t vox_offset;  // first global voxel index of this octree
+    int64_t n_vox;
+    const uint64_t* key;
+    const float* dens;
+    const float* sh;
+};
+
+struct FrameParams {
+    int32_t W, H, tiles_x, tiles_y;
+    float fx, fy, cx, cy;
+    float near_, far_;
+    float z_clip;        // camera-frame depth below which no ray sample can lie (near * min unit dz)
+    int32_t K;
+    float eps_stop;
+    int32_t activation;
+    int32_t n_oct;
+    int32_t Lkey;        // BSP key depth (max level over the octrees)
+    int32_t oct_shift;   // 3 * Lkey
+    int64_t n_vox_total;
+    OctParams oc[DV_MAX_OCTREES];
+};
+
+static_assert(sizeof(FrameParams) < 31000, "FrameParams must fit the kernel parameter space");
+
+// 64-byte per-voxel render record, one per visible voxel in depth-sort order.
+//   v[0] = (min.x, min.y, min.z, size)   local frame
+//   v[1] = dens[0..3]
+//   v[2] = dens[4..7]
+//   v[3] = (r, g, b, bits(local voxel index))
+struct __align__(16) VoxRec {
+    float4 v[4];
+};
+
+// process-wide count of kernel launches issued by this library (all contexts)
+namespace dv {
+void count_launches(long long n);
+}
+
+// error flags written by kernels (bitmask in device memory)
+#define DV_FLAG_BAD_LEVEL 1u
+
+// host-side launchers (defined in the .cu files)
+namespace dv {
+
+struct Arena;  // stream-ordered scratch allocations of one call
+
+cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
+                            cudaStream_t s);
+cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, Arena& ar,
+                            cudaStream_t s);
+// LSD radix sort of (key, value) pairs on bits [0, n_bits). Returns the buffers holding the result.
+cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int n_bits, Arena& ar, cudaStream_t s);
+cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int n_bits, Arena& ar, cudaStream_t s);
+
+struct Arena {
+    cudaMemPool_t pool;
+    cudaStream_t stream;
+    void* ptrs[256];
+    int n = 0;
+    cudaError_t err = cudaSuccess;
+    template <typename T>
+    T* alloc(size_t count) {
+        if (err != cudaSuccess) return nullptr;
+        if (n >= 256) {
+            err = cudaErrorMemoryAllocation;
+            return nullptr;
+        }
+        void* p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        err = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+        if (err != cudaSuccess) return nullptr;
+        ptrs[n++] = p;
+        return (T*)p;
+    }
+    void release() {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], stream);
+        n = 0;
+    }
+};
+
+}  // namespace dv
+
+// kernel launchers, one per .cu file
+namespace dv {
+cudaError_t launch_project(const FrameParams& fp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
+                           uint32_t* flags, cudaStream_t s);
+cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
+                           uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
+cudaError_t launch_records(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
+                           const uint64_t* rect, VoxRec* rec, uint32_t* cnt_sorted, uint64_t* rect_sorted,
+                           cudaStream_t s);
+cudaError_t launch_vis_start(const uint64_t* sorted_key, int64_t n_vis, int oct_shift, int n_oct,
+                             uint32_t* vis_start, cudaStream_t s);
+cudaError_t launch_emit(const FrameParams& fp, const uint64_t* off, const uint64_t* rect_sorted, int64_t n_vis,
+                        uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t* pair_key, int64_t n_pairs, uint2* tile_range, int n_tiles, cudaStream_t s);
+cudaError_t launch_composite_fwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
+                                 const uint2* tile_range, const uint32_t* vis_start, float* rgb, float* depth,
+                                 float* alpha, uint32_t* n_seg, float* t_final, unsigned long long* work,
+                                 cudaStream_t s);
+cudaError_t launch_composite_bwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
+                                 const uint2* tile_range, const uint32_t* vis_start, const float* rgb,
+                                 const float* depth, const uint32_t* n_seg, const float* t_final, const float* g_rgb,
+                                 const float* g_depth, const float* g_alpha, float* grad_rec, cudaStream_t s);
+cudaError_t launch_sh_bwd(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
+                          const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s);
+}  // namespace dv

@@ -1,0 +1,336 @@
+// Per-voxel projection, visibility compaction, render records and tile binning.
+//
+// project  (one thread per voxel of every octree): leaf geometry from its key,
+//          the 8 corners placed in the camera frame by the composed pose
+//          (local -> world -> camera, Sec. 3.2), near/far culling, a conservative
+//          screen rectangle of the box (clipped against the near plane) turned
+//          into a tile rectangle, and the depth-order key.
+// records  (one thread per visible voxel, in depth-key order): 64-byte record
+//          with the local box, the 8 raw densities and the view-dependent SH
+//          colour for this camera.
+// emit     one (tile, record) pair per tile of the rectangle.
+// ranges   [start, end) of every tile in the tile-sorted pair list.
+//
+// Depth-order key.  Leaves of one octree are cells of a binary space partition
+// (each node split by the three planes through its centre).  For rays that all
+// start at one point o (a pinhole), visiting at every node the children on o's
+// side of each splitting plane first gives a front-to-back order that holds
+// for every ray at once: a ray from o meets the half-space containing o before
+// it crosses the plane, and never crosses back.  The key spells the leaf's
+// path with each child bit flipped when o lies on the positive side of that
+// node's plane, so sorting keys ascending yields that order.  The side tests
+// are exact integer comparisons of 2*(o - root_min)/root*2^L against the
+// node-centre lattice coordinates.  The octree index sits above the path bits,
+// so one sort groups each octree's voxels and orders them front to back.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+
+namespace {
+
+constexpr uint64_t M19 = (1ull << 19) - 1;
+
+__device__ __forceinline__ int find_octree(const FrameParams& fp, int64_t g) {
+    int lo = 0, hi = fp.n_oct - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (fp.oc[mid].vox_offset <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Leaf {
+    int level;
+    uint32_t i, j, k;
+    float mn[3];
+    float s;
+};
+
+__device__ __forceinline__ Leaf decode_leaf(const OctParams& P, uint64_t key) {
+    Leaf L;
+    L.level = (int)((key >> 57) & 31ull);
+    L.i = (uint32_t)(key & M19);
+    L.j = (uint32_t)((key >> 19) & M19);
+    L.k = (uint32_t)((key >> 38) & M19);
+    L.s = ldexpf(P.root_size, -L.level);
+    L.mn[0] = fmaf((float)L.i, L.s, P.root_min[0]);
+    L.mn[1] = fmaf((float)L.j, L.s, P.root_min[1]);
+    L.mn[2] = fmaf((float)L.k, L.s, P.root_min[2]);
+    return L;
+}
+
+__device__ __forceinline__ void proj_point(const FrameParams& fp, float x, float y, float z, float& u0, float& u1,
+                                           float& v0, float& v1) {
+    float iz = 1.0f / z;
+    float u = fmaf(fp.fx * x, iz, fp.cx);
+    float v = fmaf(fp.fy * y, iz, fp.cy);
+    u0 = fminf(u0, u);
+    u1 = fmaxf(u1, u);
+    v0 = fminf(v0, v);
+    v1 = fmaxf(v1, v);
+}
+
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ FrameParams fp, uint32_t* __restrict__ cnt,
+                                                 uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
+                                                 uint32_t* __restrict__ vis, uint32_t* __restrict__ flags) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= fp.n_vox_total) return;
+    const int o = find_octree(fp, g);
+    const OctParams& P = fp.oc[o];
+    const int64_t v = g - P.vox_offset;
+    const uint64_t key = P.key[v];
+    cnt[g] = 0;
+    vis[g] = 0;
+    const Leaf L = decode_leaf(P, key);
+    if (L.level > P.max_level || L.i >> L.level || L.j >> L.level || L.k >> L.level) {
+        atomicOr(flags, DV_FLAG_BAD_LEVEL);
+        return;
+    }
+    // corners in the camera frame: p = M (mn + s*offset) + m
+    float p0[3], e[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        p0[r] = fmaf(P.M[r * 3 + 0], L.mn[0], fmaf(P.M[r * 3 + 1], L.mn[1], fmaf(P.M[r * 3 + 2], L.mn[2], P.m[r])));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) e[c][r] = P.M[r * 3 + c] * L.s;
+    }
+    float cz[8], cx[8], cy[8];
+    float zmin = INFINITY, zmax = -INFINITY;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float x = p0[0], y = p0[1], z = p0[2];
+        if (c & 1) x += e[0][0], y += e[0][1], z += e[0][2];
+        if (c & 2) x += e[1][0], y += e[1][1], z += e[1][2];
+        if (c & 4) x += e[2][0], y += e[2][1], z += e[2][2];
+        cx[c] = x;
+        cy[c] = y;
+        cz[c] = z;
+        zmin = fminf(zmin, z);
+        zmax = fmaxf(zmax, z);
+    }
+    if (zmax < fp.z_clip || zmin > fp.far_) return;
+    float u0 = INFINITY, u1 = -INFINITY, w0 = INFINITY, w1 = -INFINITY;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (cz[c] >= fp.z_clip) proj_point(fp, cx[c], cy[c], cz[c], u0, u1, w0, w1);
+    if (zmin < fp.z_clip) {
+        // edges crossing the clip plane contribute their crossing points
+#pragma unroll
+        for (int bit = 1; bit < 8; bit <<= 1) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                if (a & bit) continue;
+                const int b = a | bit;
+                const float za = cz[a], zb = cz[b];
+                if ((za < fp.z_clip) != (zb < fp.z_clip)) {
+                    const float t = (fp.z_clip - za) / (zb - za);
+                    proj_point(fp, fmaf(t, cx[b] - cx[a], cx[a]), fmaf(t, cy[b] - cy[a], cy[a]), fp.z_clip, u0, u1,
+                               w0, w1);
+                }
+            }
+        }
+    }
+    // pixels whose centres (u+0.5, v+0.5) may fall inside the silhouette, with a rounding margin
+    const float mu = 0.1f + 4e-6f * fmaxf(fabsf(u0), fabsf(u1));
+    const float mv = 0.1f + 4e-6f * fmaxf(fabsf(w0), fabsf(w1));
+    const float lu = fmaxf(u0 - 0.5f - mu, -1.0f), hu = fminf(u1 - 0.5f + mu, (float)fp.W + 1.0f);
+    const float lv = fmaxf(w0 - 0.5f - mv, -1.0f), hv = fminf(w1 - 0.5f + mv, (float)fp.H + 1.0f);
+    const int pu0 = max((int)ceilf(lu), 0), pu1 = min((int)floorf(hu), fp.W - 1);
+    const int pv0 = max((int)ceilf(lv), 0), pv1 = min((int)floorf(hv), fp.H - 1);
+    if (!(pu0 <= pu1 && pv0 <= pv1)) return;
+    const uint32_t tx0 = pu0 >> 4, tx1 = pu1 >> 4, ty0 = pv0 >> 4, ty1 = pv1 >> 4;
+    cnt[g] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    vis[g] = 1;
+    rect[g] = (uint64_t)tx0 | ((uint64_t)tx1 << 16) | ((uint64_t)ty0 << 32) | ((uint64_t)ty1 << 48);
+    // depth-order key (see the file comment)
+    uint64_t bsp = 0;
+    const int Lk = fp.Lkey;
+    for (int l = 0; l < L.level; ++l) {
+        const int sh = L.level - 1 - l;
+        const uint32_t bi = (L.i >> sh) & 1u, bj = (L.j >> sh) & 1u, bk = (L.k >> sh) & 1u;
+        const int64_t ti = ((int64_t)(L.i >> (sh + 1)) * 2 + 1) << (Lk - l);
+        const int64_t tj = ((int64_t)(L.j >> (sh + 1)) * 2 + 1) << (Lk - l);
+        const int64_t tk = ((int64_t)(L.k >> (sh + 1)) * 2 + 1) << (Lk - l);
+        const uint32_t fi = bi ^ (uint32_t)(P.O2[0] >= ti);
+        const uint32_t fj = bj ^ (uint32_t)(P.O2[1] >= tj);
+        const uint32_t fk = bk ^ (uint32_t)(P.O2[2] >= tk);
+        bsp = (bsp << 3) | (fi << 2) | (fj << 1) | fk;
+    }
+    bsp <<= 3 * (Lk - L.level);
+    skey[g] = ((uint64_t)o << fp.oct_shift) | bsp;
+}
+
+__global__ void k_compact(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ pos,
+                          const uint64_t* __restrict__ skey, int64_t n, uint64_t* __restrict__ out_key,
+                          uint32_t* __restrict__ out_val) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n || !vis[g]) return;
+    const uint32_t p = pos[g];
+    out_key[p] = skey[g];
+    out_val[p] = (uint32_t)g;
+}
+
+// Real SH basis (degree <= 3) times coefficients, for a unit direction.
+// Constants: 1/(2 sqrt(pi)), sqrt(3/(4 pi)), sqrt(15/(4 pi)), sqrt(5/(16 pi)),
+// sqrt(15/(16 pi)), sqrt(35/(32 pi)), sqrt(105/(4 pi)), sqrt(21/(32 pi)),
+// sqrt(7/(16 pi)), sqrt(105/(16 pi)); odd-m terms carry the Condon-Shortley sign.
+__device__ __forceinline__ void sh_eval_basis(int deg, float x, float y, float z, float* b) {
+    b[0] = 0.28209479177387814f;
+    if (deg < 1) return;
+    b[1] = -0.48860251190291992f * y;
+    b[2] = 0.48860251190291992f * z;
+    b[3] = -0.48860251190291992f * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    b[4] = 1.0925484305920792f * x * y;
+    b[5] = -1.0925484305920792f * y * z;
+    b[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+    b[7] = -1.0925484305920792f * x * z;
+    b[8] = 0.54627421529603959f * (xx - yy);
+    if (deg < 3) return;
+    b[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+    b[10] = 2.8906114426405538f * x * y * z;
+    b[11] = -0.45704579946446572f * y * (4.0f * zz - xx - yy);
+    b[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    b[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
+    b[14] = 1.4453057213202769f * z * (xx - yy);
+    b[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+__global__ void __launch_bounds__(256) k_records(const __grid_constant__ FrameParams fp,
+                                                 const uint32_t* __restrict__ sorted_g, int64_t n_vis,
+                                                 const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ rect,
+                                                 VoxRec* __restrict__ rec, uint32_t* __restrict__ cnt_sorted,
+                                                 uint64_t* __restrict__ rect_sorted) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_vis) return;
+    const uint32_t g = sorted_g[r];
+    const int o = find_octree(fp, g);
+    const OctParams& P = fp.oc[o];
+    const int64_t v = (int64_t)g - P.vox_offset;
+    const Leaf L = decode_leaf(P, P.key[v]);
+    const float4* d4 = reinterpret_cast<const float4*>(P.dens + v * 8);
+    const float4 da = __ldg(d4), db = __ldg(d4 + 1);
+    // view direction: camera centre -> voxel centre, octree frame
+    float gx = L.mn[0] + 0.5f * L.s - P.o_loc[0];
+    float gy = L.mn[1] + 0.5f * L.s - P.o_loc[1];
+    float gz = L.mn[2] + 0.5f * L.s - P.o_loc[2];
+    const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float ig = gl > 0.0f ? 1.0f / gl : 0.0f;
+    gx *= ig;
+    gy *= ig;
+    gz *= ig;
+    float b[16];
+    sh_eval_basis(P.sh_degree, gx, gy, gz, b);
+    const int nsh = (P.sh_degree + 1) * (P.sh_degree + 1);
+    const float* shv = P.sh + v * nsh * 3;
+    float c0 = 0.5f, c1 = 0.5f, c2 = 0.5f;
+    for (int q = 0; q < nsh; ++q) {
+        c0 = fmaf(b[q], __ldg(shv + q * 3 + 0), c0);
+        c1 = fmaf(b[q], __ldg(shv + q * 3 + 1), c1);
+        c2 = fmaf(b[q], __ldg(shv + q * 3 + 2), c2);
+    }
+    VoxRec R;
+    R.v[0] = make_float4(L.mn[0], L.mn[1], L.mn[2], L.s);
+    R.v[1] = da;
+    R.v[2] = db;
+    R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), __int_as_float((int)v));
+    rec[r] = R;
+    cnt_sorted[r] = cnt[g];
+    rect_sorted[r] = rect[g];
+}
+
+__global__ void k_vis_start(const uint64_t* __restrict__ key, int64_t n_vis, int shift, int n_oct,
+                            uint32_t* __restrict__ vis_start) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_vis) return;
+    const int o = (int)(key[r] >> shift);
+    const int prev = r > 0 ? (int)(key[r - 1] >> shift) : -1;
+    for (int q = prev + 1; q <= o; ++q) vis_start[q] = (uint32_t)r;
+    if (r == n_vis - 1)
+        for (int q = o + 1; q <= n_oct; ++q) vis_start[q] = (uint32_t)n_vis;
+}
+
+__global__ void k_emit(int tiles_x, const uint64_t* __restrict__ off, const uint64_t* __restrict__ rect_sorted,
+                       int64_t n_vis, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_vis) return;
+    uint64_t p = off[r];
+    const uint64_t rc = rect_sorted[r];
+    const uint32_t tx0 = rc & 0xffff, tx1 = (rc >> 16) & 0xffff, ty0 = (rc >> 32) & 0xffff, ty1 = rc >> 48;
+    for (uint32_t ty = ty0; ty <= ty1; ++ty)
+        for (uint32_t tx = tx0; tx <= tx1; ++tx) {
+            pkey[p] = ty * (uint32_t)tiles_x + tx;
+            pval[p] = (uint32_t)r;
+            ++p;
+        }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ key, int64_t n, uint2* __restrict__ range) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = key[i];
+    if (i == 0 || key[i - 1] != t) range[t].x = (uint32_t)i;
+    if (i == n - 1 || key[i + 1] != t) range[t].y = (uint32_t)(i + 1);
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_project(const FrameParams& fp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
+                           uint32_t* flags, cudaStream_t s) {
+    if (fp.n_vox_total <= 0) return cudaSuccess;
+    k_project<<<nblk(fp.n_vox_total, 256), 256, 0, s>>>(fp, cnt, rect, skey, vis, flags);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
+                           uint64_t* out_key, uint32_t* out_val, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_compact<<<nblk(n, 256), 256, 0, s>>>(vis, pos, skey, n, out_key, out_val);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
+                           const uint64_t* rect, VoxRec* rec, uint32_t* cnt_sorted, uint64_t* rect_sorted,
+                           cudaStream_t s) {
+    if (n_vis <= 0) return cudaSuccess;
+    k_records<<<nblk(n_vis, 256), 256, 0, s>>>(fp, sorted_g, n_vis, cnt, rect, rec, cnt_sorted, rect_sorted);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vis_start(const uint64_t* sorted_key, int64_t n_vis, int oct_shift, int n_oct,
+                             uint32_t* vis_start, cudaStream_t s) {
+    if (n_vis <= 0) return cudaMemsetAsync(vis_start, 0, sizeof(uint32_t) * (n_oct + 1), s);
+    k_vis_start<<<nblk(n_vis, 256), 256, 0, s>>>(sorted_key, n_vis, oct_shift, n_oct, vis_start);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const FrameParams& fp, const uint64_t* off, const uint64_t* rect_sorted, int64_t n_vis,
+                        uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s) {
+    if (n_vis <= 0) return cudaSuccess;
+    k_emit<<<nblk(n_vis, 256), 256, 0, s>>>(fp.tiles_x, off, rect_sorted, n_vis, pair_key, pair_val);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t* pair_key, int64_t n_pairs, uint2* tile_range, int n_tiles, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(tile_range, 0, sizeof(uint2) * (size_t)n_tiles, s);
+    if (e != cudaSuccess || n_pairs <= 0) return e;
+    k_ranges<<<nblk(n_pairs, 256), 256, 0, s>>>(pair_key, n_pairs, tile_range);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace dv

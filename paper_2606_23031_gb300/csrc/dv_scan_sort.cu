@@ -1,0 +1,258 @@
+// Device-wide exclusive scans and an LSD radix sort of (key, value) pairs.
+//
+// Scans are reduce-then-scan: per-block totals, one block scanning the totals,
+// then per-block scans seeded with their offsets.  Inside a block the scan is
+// a warp shuffle scan over per-thread sums.
+//
+// The radix sort processes 8 bits per pass.  A pass is (1) a per-block digit
+// histogram, (2) an exclusive scan of the digit-major histogram table, (3) a
+// stable scatter.  Stability inside a block comes from warp-level ranking:
+// __match_any_sync groups the lanes holding the same digit, popc of the lower
+// lanes of that group gives the lane's rank, and per-warp digit counts in
+// shared memory order the warps; rounds inside a block keep a running count
+// per digit.  Every pass is therefore stable, so an LSD sequence of passes
+// sorts by the full key and keeps equal keys in input order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive block scan of one value per thread; returns the block total via *total.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T x, T* total) {
+    __shared__ T warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = warp_incl_scan(x);
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = wi - w;
+        if (lane == SCAN_THREADS / 32 - 1) *total = wi;
+    }
+    __syncthreads();
+    T r = incl - x + warp_sums[warp];
+    __syncthreads();
+    return r;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, Tout* __restrict__ bsum) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    Tout s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < n) s += (Tout)in[base + i];
+    __shared__ Tout tot;
+    block_excl_scan<Tout>(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// single block: in-place exclusive scan of the block sums, writes the grand total
+template <typename Tout>
+__global__ void k_scan_top(Tout* __restrict__ bsum, int64_t nb, Tout* __restrict__ total) {
+    __shared__ Tout carry_s;
+    __shared__ Tout tot;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
+        int64_t i = b0 + threadIdx.x;
+        Tout x = i < nb ? bsum[i] : Tout(0);
+        Tout e = block_excl_scan<Tout>(x, &tot);
+        Tout c = carry_s;
+        if (i < nb) bsum[i] = c + e;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = c + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry_s;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scan_down(const Tin* __restrict__ in, int64_t n, const Tout* __restrict__ bsum,
+                            Tout* __restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    Tout v[SCAN_ITEMS];
+    Tout s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < n ? (Tout)in[base + i] : Tout(0);
+        s += v[i];
+    }
+    __shared__ Tout tot;
+    Tout run = block_excl_scan<Tout>(s, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+template <typename Tin, typename Tout>
+cudaError_t scan_impl(const Tin* in, Tout* out, int64_t n, Tout* total_dev, Arena& ar, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(Tout), s);
+        return cudaSuccess;
+    }
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    Tout* bsum = ar.alloc<Tout>((size_t)nb);
+    if (!bsum) return ar.err;
+    k_scan_reduce<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
+    count_launches(1);
+    k_scan_top<Tout><<<1, SCAN_THREADS, 0, s>>>(bsum, nb, total_dev);
+    count_launches(1);
+    if (out) {
+        k_scan_down<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum, out);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// radix sort
+// ---------------------------------------------------------------------------
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_RADIX = 256;
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__ keys, int64_t n, int shift,
+                                                            uint32_t mask, uint32_t* __restrict__ hist,
+                                                            int64_t nblocks) {
+    __shared__ uint32_t h[RS_RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restrict__ keys,
+                                                               const uint32_t* __restrict__ vals, int64_t n,
+                                                               int shift, uint32_t mask,
+                                                               const uint32_t* __restrict__ offs, int64_t nblocks,
+                                                               K* __restrict__ okeys, uint32_t* __restrict__ ovals) {
+    __shared__ uint32_t run[RS_RADIX];       // next free slot per digit (global index)
+    __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    run[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
+        bool ok = i < n;
+        K key = ok ? keys[i] : K(0);
+        uint32_t val = ok ? vals[i] : 0u;
+        uint32_t d = ok ? ((uint32_t)(key >> shift) & mask) : 0xffffffffu;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        bool leader = rank == 0;
+        if (ok && leader) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            uint32_t before = 0;
+            for (int w = 0; w < warp; ++w) before += wcnt[w][d];
+            uint32_t pos = run[d] + before + (uint32_t)rank;
+            okeys[pos] = key;
+            ovals[pos] = val;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            add += wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = 0;
+        }
+        run[threadIdx.x] += add;
+        __syncthreads();
+    }
+}
+
+template <typename K>
+cudaError_t radix_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits, Arena& ar,
+                       cudaStream_t s) {
+    if (n <= 1 || n_bits <= 0) return cudaSuccess;
+    int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+    uint32_t* hist = ar.alloc<uint32_t>((size_t)(nblocks * RS_RADIX));
+    uint32_t* offs = ar.alloc<uint32_t>((size_t)(nblocks * RS_RADIX));
+    if (!hist || !offs) return ar.err;
+    K* src_k = keys;
+    uint32_t* src_v = vals;
+    K* dst_k = keys_alt;
+    uint32_t* dst_v = vals_alt;
+    for (int shift = 0; shift < n_bits; shift += 8) {
+        int bits = n_bits - shift < 8 ? n_bits - shift : 8;
+        uint32_t mask = (1u << bits) - 1u;
+        k_radix_hist<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, n, shift, mask, hist, nblocks);
+        count_launches(1);
+        cudaError_t e = scan_impl<uint32_t, uint32_t>(hist, offs, nblocks * RS_RADIX, nullptr, ar, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, src_v, n, shift, mask, offs, nblocks,
+                                                                     dst_k, dst_v);
+        count_launches(1);
+        K* tk = src_k;
+        src_k = dst_k;
+        dst_k = tk;
+        uint32_t* tv = src_v;
+        src_v = dst_v;
+        dst_v = tv;
+    }
+    keys = src_k;
+    vals = src_v;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
+                            cudaStream_t s) {
+    return scan_impl<uint32_t, uint64_t>(in, out, n, total_dev, ar, s);
+}
+
+cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, Arena& ar,
+                            cudaStream_t s) {
+    return scan_impl<uint32_t, uint32_t>(in, out, n, total_dev, ar, s);
+}
+
+cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int n_bits, Arena& ar, cudaStream_t s) {
+    return radix_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+}
+
+cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int n_bits, Arena& ar, cudaStream_t s) {
+    return radix_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+}
+
+}  // namespace dv

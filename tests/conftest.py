@@ -19,3 +19,10 @@ def dv():
     import paper_2606_23031_gb300 as m
     m.load()
     return m
+
+
+@pytest.fixture(scope="session")
+def config2_scene():
+    """The 1920x1080 compositional scene (500k background leaves, 3 actors), generated once."""
+    import synth
+    return synth.config2(0)
