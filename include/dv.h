@@ -168,6 +168,23 @@ dv_status dv_state_work(const dv_state* state, int32_t cam, uint64_t* tests, uin
  * contexts); reset to zero when `reset` is non-zero (returns the old value). */
 long long dv_launch_count(int32_t reset);
 
+/*
+ * dv_render_backward without any device allocation (the paper has no
+ * counterpart; this exists for callers that may not allocate while the
+ * backward runs: inside a CUDA-graph capture that must hold no allocation
+ * nodes, in a real-time loop that may not take an allocator lock, or with the
+ * device memory fully committed to another allocator).  Same arguments,
+ * results and accumulation semantics as dv_render_backward.  Its scratch is a
+ * file-scope device array sized for 131072 visible voxels per camera (6 MiB,
+ * held by every GPU that loads the library until exit); a state with a camera
+ * above that limit fails with DV_ERR_CAPACITY before any work is enqueued.
+ * All calls on a device share that array and clear it per camera before use:
+ * calls whose GPU work overlaps (unordered streams) race on it.  The first call
+ * on a device looks up the array's address; make it before any stream capture.
+ */
+dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* state, const float* d_rgb, const float* d_depth,
+                                    const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream);
+
 /* Per-stage timing with CUDA events recorded on the call's stream.  While
  * enabled, every stage below is bracketed by events; dv_profile_read()
  * synchronises those events and returns, for stage k in names order, the

@@ -431,3 +431,26 @@ def render(octrees, poses, cams, opts=None, dens=None, sh=None):
     dens = [o.dens for o in octrees] if dens is None else dens
     sh = [o.sh for o in octrees] if sh is None else sh
     return _RenderFn.apply((octrees, poses, cams, opts or make_opts()), *dens, *sh)
+
+
+STATIC_MAX_VISIBLE = 1 << 17
+
+
+def dv_render_backward_static(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_dens=None, d_sh=None,
+                              stream=None):
+    """Allocation-free variant of :func:`dv_render_backward` for callers that may not allocate device
+    memory while the backward runs (graph capture without allocation nodes, real-time loops, a device
+    whose memory belongs to another allocator).  Its scratch is a static device array for at most
+    ``STATIC_MAX_VISIBLE`` visible voxels per camera; calls that overlap on the GPU race on it, and the
+    first call on a device should precede any stream capture."""
+    lib = load()
+    fn = lib.dv_render_backward_static
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p),
+                   C.POINTER(C.c_void_p), C.c_void_p]
+    fn.restype = C.c_int
+    n = len(d_dens) if d_dens is not None else len(d_sh)
+    pd = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_dens or [None] * n)])
+    ps = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_sh or [None] * n)])
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    status = fn(state.ctx.handle, state.handle, ptr(d_rgb), ptr(d_depth), ptr(d_alpha), pd, ps, _stream_ptr(stream))
+    state.ctx.check(status)

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -740,3 +741,86 @@ dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, doub
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Backward without any allocation.
+//
+// Some callers cannot allocate device memory at the moment they run the
+// backward: a training loop captured into a CUDA graph that must not contain
+// allocation nodes, a real-time loop that may not take an allocator lock, or
+// a process whose device memory is fully committed to another framework's
+// caching allocator.  dv_render_backward_static() serves them: its only
+// scratch, the per-voxel gradient accumulator of one camera, lives in the
+// file-scope array below, so the call itself never allocates (no cudaMalloc,
+// no pool allocation, no library routine that allocates).
+//
+// Limits and sharing rules:
+//  * at most DV_STATIC_MAX_VISIBLE visible voxels per camera (12 floats each,
+//    6 MiB in total); a larger camera is rejected with DV_ERR_CAPACITY before
+//    any work is enqueued;
+//  * every GPU that loads this library holds the array until the process exits;
+//  * all calls on a device share the one array: each camera's slice is cleared
+//    (cudaMemsetAsync) before use, but two calls whose work overlaps on the GPU
+//    (different streams, no ordering between them) race on it and corrupt each
+//    other's gradients -- order such calls on one stream or with events;
+//  * the first call on a device looks up the array's device address
+//    (cudaGetSymbolAddress, with that device current); make that first call
+//    before any stream capture begins.
+// ---------------------------------------------------------------------------
+
+#define DV_STATIC_MAX_VISIBLE (1 << 17)
+#define DV_STATIC_GRAD_FLOATS (12 * DV_STATIC_MAX_VISIBLE)
+
+static __device__ __align__(256) float g_static_grad[DV_STATIC_GRAD_FLOATS];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_ptr[kStaticMaxDevices] = {};
+
+// device address of g_static_grad on `device` (which must be current)
+cudaError_t static_grad_ptr(int device, float** out) {
+    if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_grad);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[device] = (float*)p;
+    }
+    *out = g_static_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
+                                               const float* d_alpha, float* const* d_dens, float* const* d_sh,
+                                               void* stream) {
+    if (!ctx || !st) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
+    for (const auto& cs : st->cams)
+        if (cs.n_vis > DV_STATIC_MAX_VISIBLE)
+            return fail(ctx, DV_ERR_CAPACITY,
+                        "dv_render_backward_static: a camera has " + std::to_string(cs.n_vis) +
+                            " visible voxels, above the static limit of " + std::to_string(DV_STATIC_MAX_VISIBLE));
+    DeviceGuard g(ctx->device);
+    float* grad = nullptr;
+    cudaError_t e = static_grad_ptr(ctx->device, &grad);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(static gradient scratch)");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto& cs : st->cams) {
+        if (cs.n_vis == 0) continue;
+        const int64_t po = cs.pix_offset;
+        e = cudaMemsetAsync(grad, 0, sizeof(float) * 12 * (size_t)cs.n_vis, s);
+        if (e == cudaSuccess)
+            e = dv::launch_composite_bwd(*cs.fp, cs.rec, cs.pval, cs.range, cs.vis_start, cs.rgb, cs.depth, cs.n_seg,
+                                         cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
+                                         d_depth ? d_depth + po : nullptr, d_alpha ? d_alpha + po : nullptr, grad, s);
+        if (e == cudaSuccess) e = dv::launch_sh_bwd(*cs.fp, cs.sorted_g, cs.n_vis, cs.rec, grad, d_dens, d_sh, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dv_render_backward_static");
+    }
+    return DV_OK;
+}
