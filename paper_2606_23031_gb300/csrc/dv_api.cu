@@ -58,8 +58,10 @@ struct CamState {
     VoxRec* rec = nullptr;
     uint32_t* sorted_g = nullptr;
     uint32_t* pval = nullptr;
+    uint8_t* pmask = nullptr;  // per pair: 8x4-pixel blocks of the tile the voxel touches
     uint2* range = nullptr;
     uint32_t* vis_start = nullptr;
+    uint32_t* tile_order = nullptr;
     uint32_t* n_seg = nullptr;
     float* t_final = nullptr;
     unsigned long long* work = nullptr;  // [tests, box tests, segments] of the forward
@@ -252,6 +254,7 @@ dv_status make_params(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pos
     fp.near_ = cam.near_;
     fp.far_ = cam.far_;
     fp.K = opt.K;
+    fp.inv_k = 1.0f / (float)opt.K;
     fp.eps_stop = opt.eps_stop;
     fp.activation = opt.activation;
     fp.n_oct = n_oct;
@@ -411,6 +414,7 @@ dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_
     cs.t_final = pool_alloc<float>(ctx, s, (size_t)npix, own, e);
     cs.range = pool_alloc<uint2>(ctx, s, (size_t)n_tiles, own, e);
     cs.vis_start = pool_alloc<uint32_t>(ctx, s, (size_t)fp.n_oct + 1, own, e);
+    cs.tile_order = pool_alloc<uint32_t>(ctx, s, (size_t)n_tiles, own, e);
     cs.work = pool_alloc<unsigned long long>(ctx, s, 4, own, e);
     if (e == cudaSuccess) e = cudaMemsetAsync(cs.work, 0, 4 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate state");
@@ -509,7 +513,7 @@ dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_
     }
     {
         Prof p(ctx, KP_EMIT, s);
-        e = launch_emit(fp, off, rect_sorted, n_vis, pk0, pv0, s);
+        e = launch_emit(fp, off, rect_sorted, n_vis, P, pk0, pv0, s);
     }
     uint32_t* pk = pk0;
     uint32_t* pv = pv0;
@@ -520,15 +524,19 @@ dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_
     if (e == cudaSuccess && pv != pv0)
         e = cudaMemcpyAsync(pv0, pv, sizeof(uint32_t) * (size_t)P, cudaMemcpyDeviceToDevice, s);
     cs.pval = pv0;
+    cs.pmask = pool_alloc<uint8_t>(ctx, s, (size_t)P, own, e);
     {
         Prof p(ctx, KP_RANGES, s);
+        if (e == cudaSuccess) e = launch_pair_mask(fp, pk, cs.pval, rect_sorted, P, cs.pmask, s);
         if (e == cudaSuccess) e = launch_ranges(pk, P, cs.range, (int)n_tiles, s);
+        uint32_t* tscr = ar.alloc<uint32_t>(64);
+        if (e == cudaSuccess) e = tscr ? launch_tile_order(cs.range, (int)n_tiles, tscr, cs.tile_order, s) : ar.err;
     }
     {
         Prof p(ctx, KP_FWD, s);
         if (e == cudaSuccess)
-            e = launch_composite_fwd(fp, cs.rec, cs.pval, cs.range, cs.vis_start, rgb, depth, alpha, cs.n_seg,
-                                     cs.t_final, cs.work, s);
+            e = launch_composite_fwd(fp, cs.rec, cs.pval, cs.pmask, cs.range, cs.vis_start, cs.tile_order, rgb, depth, alpha,
+                                     cs.n_seg, cs.t_final, cs.work, s);
     }
     ar.release();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render");
@@ -663,8 +671,8 @@ dv_status dv_render_backward(dv_ctx* ctx, dv_state* st, const float* d_rgb, cons
         {
             Prof p(ctx, KP_BWD, s);
             if (e == cudaSuccess)
-                e = dv::launch_composite_bwd(fp, cs.rec, cs.pval, cs.range, cs.vis_start, cs.rgb, cs.depth, cs.n_seg,
-                                             cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
+                e = dv::launch_composite_bwd(fp, cs.rec, cs.pval, cs.pmask, cs.range, cs.vis_start, cs.tile_order, cs.rgb,
+                                             cs.depth, cs.n_seg, cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
                                              d_depth ? d_depth + po : nullptr, d_alpha ? d_alpha + po : nullptr,
                                              grad, s);
         }
@@ -816,8 +824,8 @@ extern "C" dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* st, const 
         const int64_t po = cs.pix_offset;
         e = cudaMemsetAsync(grad, 0, sizeof(float) * 12 * (size_t)cs.n_vis, s);
         if (e == cudaSuccess)
-            e = dv::launch_composite_bwd(*cs.fp, cs.rec, cs.pval, cs.range, cs.vis_start, cs.rgb, cs.depth, cs.n_seg,
-                                         cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
+            e = dv::launch_composite_bwd(*cs.fp, cs.rec, cs.pval, cs.pmask, cs.range, cs.vis_start, cs.tile_order, cs.rgb,
+                                         cs.depth, cs.n_seg, cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
                                          d_depth ? d_depth + po : nullptr, d_alpha ? d_alpha + po : nullptr, grad, s);
         if (e == cudaSuccess) e = dv::launch_sh_bwd(*cs.fp, cs.sorted_g, cs.n_vis, cs.rec, grad, d_dens, d_sh, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "dv_render_backward_static");

@@ -1,33 +1,41 @@
 // Front-to-back compositing over each ray's voxel segments (forward) and its
 // replay with gradients (backward), plus the SH-colour backward.
 //
-// One CTA renders one 16x16 tile, one thread per pixel (Sec. 3.4, Alg. 1):
+// Each CTA renders half of a 16x16 tile (16x8 pixels, 4 warps of 8x4 pixels),
+// one thread per pixel, tiles taken heaviest first (Sec. 3.4, Alg. 1):
 //  * The tile's pair list is grouped by octree and, inside an octree, sorted
 //    front to back for every ray of the camera (depth-order key, see
-//    dv_project.cu).  The background sub-list is streamed through shared
-//    memory in batches of 256 records that every pixel of the tile tests.
+//    dv_project.cu).
 //  * Each pixel splits its ray into background and actor intervals with the
 //    actor clip boxes (slab test in each actor's frame, reached through the
-//    inverse pose; the box entered first owns any overlap).  Intervals are
-//    found lazily: the next one is the unvisited box with the smallest entry
-//    distance among those still ahead.
-//  * While walking the background list, a hit that reaches past the next
-//    actor's entry first composites its part in front of the box, then the
-//    pixel walks that actor's sub-list (clipped to the actor's interval),
-//    then continues with the remainder of the background voxel behind the
-//    box.  The running state (C, D, T) is carried across every border, so the
-//    composite equals the global front-to-back order of all segments.
+//    inverse pose; the box entered first owns any overlap).
+//  * Phase 1: for every actor of the tile, each warp walks that actor's
+//    sub-list in lockstep; every lane composites the segments inside its own
+//    interval of that actor into a partial (C_A, D_A, T_A) starting from T = 1.
+//  * Phase 2: the background sub-list streams through a two-slot shared-memory
+//    ring (cp.async, one batch ahead).  A background hit that reaches past the
+//    next actor's entry composites its part in front of the box, then applies
+//    that actor's partial with the running transmittance (C += T C_A,
+//    D += T D_A, T *= T_A), then continues behind the box.  If T T_A < eps_stop
+//    the ray must stop inside the actor: the lane records its state and stops.
+//  * Phase 3: lanes that stop inside an actor replay that actor's sub-list in
+//    lockstep from the recorded state with the exact stop rule.
+//    Since T only decreases along the ray, applying a whole partial is exact
+//    unless the stop falls inside it, which is exactly when T T_A < eps_stop.
 //  * Per segment: trilinear interpolation of the raw corner densities at K
 //    midpoints, exponential-linear activation, tau = l/K sum sigma,
 //    alpha = 1 - exp(-tau), C += T alpha c, D += T alpha (t0+t1)/2,
 //    T *= 1 - alpha, stop once T < eps_stop.
-//  * The backward replays exactly the forward's segment sequence (same code,
-//    stopping after the forward's segment count) front to back.  With
-//    w_k = T_k alpha_k it uses dC/dtau_k = T_{k+1} c_k - sum_{j>k} w_j c_j where the
-//    suffix sum is C_final - (prefix through k), so no division by (1 - alpha)
-//    and no reverse traversal is needed.  Gradients of the background records
-//    are reduced across the warp (all lanes visit the same record together)
-//    before one atomic per value; actor-walk gradients use per-lane atomics.
+//  * The backward runs the same three phases (identical arithmetic, so the same
+//    stops).  With w_k = T_k alpha_k it uses
+//    dC/dtau_k = T_{k+1} c_k - sum_{j>k} w_j c_j, the suffix sum being
+//    C_final - (prefix through k), so it needs no division by (1 - alpha) and
+//    no reverse traversal.  Phase 2 records, for every actor interval reached,
+//    the prefix state at its entry; phase 3 then replays every reached actor
+//    interval with gradients from that state.  Gradients of records visited in
+//    lockstep are reduced across the warp before the atomics.
+//  * Tiles with more than NTA actors handle the extra actors with a per-lane
+//    walk of the actor's sub-list (correct, but divergent).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,8 +45,9 @@ namespace dv {
 
 namespace {
 
-constexpr int BATCH = DV_BLOCK;
-constexpr int GSTRIDE = 12;  // per-record gradient slots: 8 densities, 3 colour, 1 pad
+constexpr int CT_THREADS = 128;  // half a tile per CTA
+constexpr int GSTRIDE = 12;      // per-record gradient slots: 8 densities, 3 colour, 1 pad
+constexpr int NTA = 4;           // tile actors with lockstep partials
 
 struct Pix {
     float C0, C1, C2, D, T;
@@ -48,26 +57,27 @@ struct Pix {
 };
 
 struct Bwd {
-    // upstream gradient, forward results, running prefix sums
+    // upstream gradient and the forward's results
     float g0, g1, g2, gD, gA;
     float Cf0, Cf1, Cf2, Df, Tend;
-    float P0, P1, P2, PD;
-    uint32_t nmax;
 };
 
 struct ActInt {
-    int o;
+    int o;  // octree index (-1: none)
+    int q;  // slot in the tile's actor list
     float a, b;
 };
 
+// exponential-linear activation: x above 1.1, 1.1 exp(x/1.1 - 1) below (C1 at 1.1); the
+// exponential goes to the SFU (__expf), whose relative error here is ~1e-6
 __device__ __forceinline__ float act_fn(float x, int act) {
     if (act == DV_ACT_IDENTITY) return x;
-    return x > 1.1f ? x : 1.1f * expf(fmaf(x, 0.90909090909090909f, -1.0f));
+    return x > 1.1f ? x : 1.1f * __expf(fmaf(x, 0.90909090909090909f, -1.0f));
 }
 
 __device__ __forceinline__ float act_grad(float x, int act) {
     if (act == DV_ACT_IDENTITY) return 1.0f;
-    return x > 1.1f ? 1.0f : expf(fmaf(x, 0.90909090909090909f, -1.0f));
+    return x > 1.1f ? 1.0f : __expf(fmaf(x, 0.90909090909090909f, -1.0f));
 }
 
 __device__ __forceinline__ void rotate(const float* A, const float* x, float* y) {
@@ -109,9 +119,9 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(
 // optical depth of the segment [t0, t1] through one voxel; optionally d tau / d dens[c]
 template <bool GRAD>
 __device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, const float* o, const float* d, float t0,
-                                         float t1, int K, int act, float* dtd) {
-    const float h = (t1 - t0) / (float)K;
-    const float is = 1.0f / g.w;
+                                         float t1, int K, float inv_k, int act, float* dtd) {
+    const float h = (t1 - t0) * inv_k;
+    const float is = __fdividef(1.0f, g.w);
     float tau = 0.0f;
     if (GRAD) {
 #pragma unroll
@@ -142,24 +152,25 @@ __device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, const f
     return tau * h;
 }
 
-// Composites one segment; in the backward also adds this segment's gradient
-// into acc[0..10] (8 densities, 3 colour channels).
-template <bool BWD>
-__device__ __forceinline__ void add_segment(Pix& ps, Bwd& bw, const FrameParams& fp, float4 g, float4 da, float4 db,
-                                            float4 col, const float* o, const float* d, float t0, float t1,
-                                            float* acc) {
+// Composites one segment (with the stop test when STOP); with GRAD also adds
+// this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
+template <bool GRAD, bool STOP>
+__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const FrameParams& fp, float4 g, float4 da,
+                                            float4 db, float4 col, const float* o, const float* d, float t0,
+                                            float t1, float* acc) {
     float dtd[8];
-    const float tau = seg_tau<BWD>(g, da, db, o, d, t0, t1, fp.K, fp.activation, dtd);
-    const float alpha = -expm1f(-tau);
+    const float tau = seg_tau<GRAD>(g, da, db, o, d, t0, t1, fp.K, fp.inv_k, fp.activation, dtd);
+    const float e = __expf(-tau);  // transmittance of the segment
+    const float alpha = 1.0f - e;
     const float w = ps.T * alpha;
     const float mid = 0.5f * (t0 + t1);
     ps.C0 = fmaf(w, col.x, ps.C0);
     ps.C1 = fmaf(w, col.y, ps.C1);
     ps.C2 = fmaf(w, col.z, ps.C2);
     ps.D = fmaf(w, mid, ps.D);
-    ps.T = ps.T * (1.0f - alpha);
+    ps.T = ps.T * e;
     ps.n += 1;
-    if (BWD) {
+    if (GRAD) {
         const float Tn = ps.T;
         float gt = bw.gA * bw.Tend;
         gt = fmaf(bw.g0, fmaf(Tn, col.x, -(bw.Cf0 - ps.C0)), gt);
@@ -171,10 +182,8 @@ __device__ __forceinline__ void add_segment(Pix& ps, Bwd& bw, const FrameParams&
         acc[8] = fmaf(bw.g0, w, acc[8]);
         acc[9] = fmaf(bw.g1, w, acc[9]);
         acc[10] = fmaf(bw.g2, w, acc[10]);
-        if (ps.n >= bw.nmax) ps.done = true;
-    } else {
-        if (ps.T < fp.eps_stop) ps.done = true;
     }
+    if (STOP && ps.T < fp.eps_stop) ps.done = true;
 }
 
 // next actor interval ahead of tau_cur (first-entered box owns overlaps)
@@ -182,6 +191,7 @@ __device__ __forceinline__ ActInt next_interval(const FrameParams& fp, const int
                                                 float tau_cur) {
     ActInt r;
     r.o = -1;
+    r.q = -1;
     r.a = INFINITY;
     r.b = 0.0f;
     for (int q = 0; q < n_ta; ++q) {
@@ -197,6 +207,7 @@ __device__ __forceinline__ ActInt next_interval(const FrameParams& fp, const int
         if (!(b > a) || !(b > tau_cur)) continue;
         if (a < r.a) {
             r.o = tact[q];
+            r.q = q;
             r.a = a;
             r.b = b;
         }
@@ -205,7 +216,6 @@ __device__ __forceinline__ ActInt next_interval(const FrameParams& fp, const int
     return r;
 }
 
-template <bool BWD>
 __device__ __forceinline__ void atomic_grad(float* grad_rec, uint32_t r, const float* acc) {
     float* gp = grad_rec + (size_t)r * GSTRIDE;
 #pragma unroll
@@ -213,11 +223,61 @@ __device__ __forceinline__ void atomic_grad(float* grad_rec, uint32_t r, const f
         if (acc[c] != 0.0f) atomicAdd(gp + c, acc[c]);
 }
 
-// walk one actor's sub-list of the tile, clipped to its interval
-template <bool BWD>
-__device__ __noinline__ void walk_actor(Pix& ps, Bwd& bw, const FrameParams& fp, const ActInt& it,
-                                        const uint32_t* __restrict__ pval, const VoxRec* __restrict__ rec,
-                                        uint32_t q0, uint32_t q1, const float* dc, float* grad_rec) {
+// Sum of acc[0..10] over the warp, transposed: each butterfly level keeps half of
+// the values and exchanges the other half, so 16 shuffles reduce all 11 values
+// (instead of 5 per value).  Afterwards even lanes hold the totals, value index
+// ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1) for lane l, and each of
+// the 11 lanes owning a real value adds it to the record's gradient slot.
+__device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
+    const int lane = threadIdx.x & 31;
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = c < 11 ? acc[c] : 0.0f;
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float send = up ? v[i] : v[i + 8];
+            const float keep = up ? v[i + 8] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float send = up ? v[i] : v[i + 4];
+            const float keep = up ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float send = up ? v[i] : v[i + 2];
+            const float keep = up ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    if (!(lane & 1) && idx < 11 && v[0] != 0.0f) atomicAdd(gp + idx, v[0]);
+}
+
+// Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
+// NTA lockstep slots).
+template <bool GRAD>
+__device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const FrameParams& fp, const ActInt& it,
+                                             const uint32_t* __restrict__ pval, const uint8_t* __restrict__ pmask,
+                                             uint32_t wbit, const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
+                                             const float* dc, float* grad_rec) {
     const OctParams& P = fp.oc[it.o];
     float d[3], inv[3];
     rotate(P.A, dc, d);
@@ -226,6 +286,7 @@ __device__ __noinline__ void walk_actor(Pix& ps, Bwd& bw, const FrameParams& fp,
     inv[2] = 1.0f / d[2];
     const float o[3] = {P.o_loc[0], P.o_loc[1], P.o_loc[2]};
     for (uint32_t q = q0; q < q1 && !ps.done; ++q) {
+        if (!(__ldg(pmask + q) & wbit)) continue;
         ps.tests += 1;
         const uint32_t r = __ldg(pval + q);
         const float4* R = rec[r].v;
@@ -238,17 +299,89 @@ __device__ __noinline__ void walk_actor(Pix& ps, Bwd& bw, const FrameParams& fp,
         float acc[11];
 #pragma unroll
         for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
-        add_segment<BWD>(ps, bw, fp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), o, d, t0, t1, acc);
-        if (BWD) atomic_grad<BWD>(grad_rec, r, acc);
+        add_segment<GRAD, true>(ps, bw, fp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), o, d, t0, t1, acc);
+        if (GRAD) atomic_grad(grad_rec, r, acc);
     }
 }
 
+// Warp-lockstep walk of octree o's sub-list [q0, q1): every lane with `act`
+// composites the segments inside its interval [a, b] into st (STOP: with the
+// stop test).  With GRAD the per-record gradients are reduced across the warp.
+template <bool GRAD, bool STOP>
+__device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const FrameParams& fp, int o, float a, float b,
+                                             bool act, const uint32_t* __restrict__ pval,
+                                             const uint8_t* __restrict__ pmask, uint32_t wbit,
+                                             const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
+                                             const float* dc, float* grad_rec) {
+    const OctParams& P = fp.oc[o];
+    float d[3], inv[3];
+    rotate(P.A, dc, d);
+    inv[0] = 1.0f / d[0];
+    inv[1] = 1.0f / d[1];
+    inv[2] = 1.0f / d[2];
+    const float ol[3] = {P.o_loc[0], P.o_loc[1], P.o_loc[2]};
+    uint32_t r_nx = q0 < q1 ? __ldg(pval + q0) : 0u;
+    uint32_t m_nx = q0 < q1 ? __ldg(pmask + q0) : 0u;
+    for (uint32_t q = q0; q < q1; ++q) {
+        if (!__any_sync(0xffffffffu, act && !st.done)) break;
+        const uint32_t r = r_nx;
+        const uint32_t m = m_nx;
+        if (q + 1 < q1) {
+            r_nx = __ldg(pval + q + 1);
+            m_nx = __ldg(pmask + q + 1);
+        }
+        if (!(m & wbit)) continue;  // the voxel misses this warp's 8x4 block
+        const float4* R = rec[r].v;
+        const float4 g = __ldg(R);
+        float acc[11];
+        if (GRAD) {
+#pragma unroll
+            for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
+        }
+        bool hit = false;
+        if (act && !st.done) {
+            st.tests += 1;
+            float t0, t1;
+            if (slab_cube(ol, inv, g, t0, t1)) {
+                t0 = fmaxf(t0, a);
+                t1 = fminf(t1, b);
+                if (t1 > t0) {
+                    add_segment<GRAD, STOP>(st, bw, fp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), ol, d, t0, t1,
+                                            acc);
+                    hit = true;
+                }
+            }
+        }
+        if (GRAD) {
+            const unsigned any = __ballot_sync(0xffffffffu, hit);
+            if (any) warp_reduce_add(acc, grad_rec + (size_t)r * GSTRIDE);
+        }
+    }
+}
+
+// 16-byte asynchronous global -> shared copy (L2 only), and its group fences
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// per-lane actor bookkeeping in shared memory, slot q < NTA:
+//   s_iv[q][0/1][lane]  = the lane's owned interval [a, b) of that actor (a > b: none)
+//   s_st[q][0..4][lane] = phase 1: partial (C0, C1, C2, D, T); phase 2 overwrites it with the
+//                         state at the interval's entry (C0, C1, C2, D, T) when it is replayed
+//   s_st[q][5][lane]    = phase 1: partial segment count; phase 2: 0 not reached,
+//                         1 partial applied, 2 stop inside (replay)
+
 template <bool BWD>
-__global__ void __launch_bounds__(DV_BLOCK) k_composite(const __grid_constant__ FrameParams fp,
+__global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __grid_constant__ FrameParams fp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
+                                                        const uint8_t* __restrict__ pmask,
                                                         const uint2* __restrict__ tile_range,
                                                         const uint32_t* __restrict__ vis_start,
+                                                        const uint32_t* __restrict__ tile_order,
                                                         float* __restrict__ out_rgb, float* __restrict__ out_depth,
                                                         float* __restrict__ out_alpha, uint32_t* __restrict__ n_seg,
                                                         float* __restrict__ t_final, const float* __restrict__ g_rgb,
@@ -256,13 +389,17 @@ __global__ void __launch_bounds__(DV_BLOCK) k_composite(const __grid_constant__ 
                                                         const float* __restrict__ g_alpha,
                                                         float* __restrict__ grad_rec,
                                                         unsigned long long* __restrict__ work) {
-    __shared__ float4 s_rec[BATCH][4];
-    __shared__ uint32_t s_r[BATCH];
+    __shared__ float4 s_rec[2][CT_THREADS][4];
+    __shared__ uint32_t s_r[2][CT_THREADS];
+    __shared__ uint8_t s_m[2][CT_THREADS];
     __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];
     __shared__ int16_t s_act[DV_MAX_OCTREES];
+    __shared__ float s_iv[NTA][2][CT_THREADS];
+    __shared__ float s_st[NTA][6][CT_THREADS];
     __shared__ int s_nact;
 
-    const int tile = blockIdx.x;
+    const int tile = (int)tile_order[blockIdx.x >> 1];
+    const int half = blockIdx.x & 1;
     const int tx = tile % fp.tiles_x, ty = tile / fp.tiles_x;
     const uint2 rg = tile_range[tile];
     const int tid = threadIdx.x;
@@ -289,8 +426,10 @@ __global__ void __launch_bounds__(DV_BLOCK) k_composite(const __grid_constant__ 
     }
     __syncthreads();
 
-    const int u = tx * DV_TILE + (tid & (DV_TILE - 1));
-    const int v = ty * DV_TILE + (tid >> 4);
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t wbit = 1u << ((half * 2 + (warp >> 1)) * 2 + (warp & 1));  // this warp's 8x4 block
+    const int u = tx * DV_TILE + (warp & 1) * 8 + (lane & 7);
+    const int v = ty * DV_TILE + half * 8 + (warp >> 1) * 4 + (lane >> 3);
     const bool valid = u < fp.W && v < fp.H;
     const int64_t pix = (int64_t)v * fp.W + u;
 
@@ -319,25 +458,73 @@ __global__ void __launch_bounds__(DV_BLOCK) k_composite(const __grid_constant__ 
     ps.boxes = 0;
     ps.done = !valid;
     Bwd bw;
-    if (BWD) {
-        if (valid) {
-            bw.g0 = g_rgb ? g_rgb[pix * 3 + 0] : 0.0f;
-            bw.g1 = g_rgb ? g_rgb[pix * 3 + 1] : 0.0f;
-            bw.g2 = g_rgb ? g_rgb[pix * 3 + 2] : 0.0f;
-            bw.gD = g_depth ? g_depth[pix] : 0.0f;
-            bw.gA = g_alpha ? g_alpha[pix] : 0.0f;
-            bw.Cf0 = out_rgb[pix * 3 + 0];
-            bw.Cf1 = out_rgb[pix * 3 + 1];
-            bw.Cf2 = out_rgb[pix * 3 + 2];
-            bw.Df = out_depth[pix];
-            bw.Tend = t_final[pix];
-            bw.nmax = n_seg[pix];
-            if (bw.nmax == 0) ps.done = true;
-        } else {
-            bw.nmax = 0;
-        }
+    if (BWD && valid) {
+        bw.g0 = g_rgb ? g_rgb[pix * 3 + 0] : 0.0f;
+        bw.g1 = g_rgb ? g_rgb[pix * 3 + 1] : 0.0f;
+        bw.g2 = g_rgb ? g_rgb[pix * 3 + 2] : 0.0f;
+        bw.gD = g_depth ? g_depth[pix] : 0.0f;
+        bw.gA = g_alpha ? g_alpha[pix] : 0.0f;
+        bw.Cf0 = out_rgb[pix * 3 + 0];
+        bw.Cf1 = out_rgb[pix * 3 + 1];
+        bw.Cf2 = out_rgb[pix * 3 + 2];
+        bw.Df = out_depth[pix];
+        bw.Tend = t_final[pix];
+    } else {
+        bw.g0 = bw.g1 = bw.g2 = bw.gD = bw.gA = 0.0f;
+        bw.Cf0 = bw.Cf1 = bw.Cf2 = bw.Df = bw.Tend = 0.0f;
     }
     const int n_ta = s_nact;
+    const int n_lock = n_ta < NTA ? n_ta : NTA;
+
+    // ---- owned actor intervals of this ray (lockstep slots) ----
+    for (int q = 0; q < n_lock; ++q) {
+        s_iv[q][0][tid] = INFINITY;
+        s_iv[q][1][tid] = -INFINITY;
+        s_st[q][5][tid] = 0.0f;
+    }
+    if (valid && n_ta > 0) {
+        float tau = fp.near_;
+        for (int guard = 0; guard < n_ta; ++guard) {
+            const ActInt it = next_interval(fp, s_act, n_ta, dc, tau);
+            ps.boxes += n_ta;
+            if (it.o < 0) break;
+            if (it.q < NTA) {
+                s_iv[it.q][0][tid] = it.a;
+                s_iv[it.q][1][tid] = it.b;
+            }
+            tau = it.b;
+        }
+    }
+
+    // ---- phase 1: partial composite of every lockstep actor interval ----
+    for (int q = 0; q < n_lock; ++q) {
+        const float a = s_iv[q][0][tid], b = s_iv[q][1][tid];
+        const bool act = valid && b > a;
+        if (!__any_sync(0xffffffffu, act)) continue;
+        Pix pt;
+        pt.C0 = pt.C1 = pt.C2 = pt.D = 0.0f;
+        pt.T = 1.0f;
+        pt.n = 0;
+        pt.tests = 0;
+        pt.boxes = 0;
+        pt.done = false;
+        const int o = s_act[q];
+        // a lane whose own transmittance already falls below eps_stop will stop inside this
+        // actor whatever T it enters with (T <= 1), so its partial may stop there too
+        walk_actor_warp<false, true>(pt, bw, fp, o, a, b, act, pval, pmask, wbit, rec, s_sub[o], s_sub[o + 1], dc,
+                                     nullptr);
+        ps.tests += pt.tests;
+        if (act) {
+            s_st[q][0][tid] = pt.C0;
+            s_st[q][1][tid] = pt.C1;
+            s_st[q][2][tid] = pt.C2;
+            s_st[q][3][tid] = pt.D;
+            s_st[q][4][tid] = pt.T;
+            s_st[q][5][tid] = __int_as_float((int)pt.n);
+        }
+    }
+
+    // ---- phase 2: background walk, applying actor partials in order ----
     float tau_cur = fp.near_;
     ActInt nxt;
     nxt.o = -1;
@@ -345,79 +532,162 @@ __global__ void __launch_bounds__(DV_BLOCK) k_composite(const __grid_constant__ 
         nxt = next_interval(fp, s_act, n_ta, dc, tau_cur);
         ps.boxes += n_ta;
     }
+    // enters actor interval `it`: apply its partial, or stop inside it, or walk it per lane
+    auto enter_actor = [&](const ActInt& it) {
+        if (it.q < NTA) {
+            const int q = it.q;
+            const float pC0 = s_st[q][0][tid], pC1 = s_st[q][1][tid], pC2 = s_st[q][2][tid];
+            const float pD = s_st[q][3][tid], pT = s_st[q][4][tid];
+            const uint32_t pn = (uint32_t)__float_as_int(s_st[q][5][tid]);
+            const bool stop_inside = ps.T * pT < fp.eps_stop;
+            if (BWD || stop_inside) {
+                s_st[q][0][tid] = ps.C0;
+                s_st[q][1][tid] = ps.C1;
+                s_st[q][2][tid] = ps.C2;
+                s_st[q][3][tid] = ps.D;
+                s_st[q][4][tid] = ps.T;
+            }
+            s_st[q][5][tid] = stop_inside ? 2.0f : 1.0f;
+            if (stop_inside) {
+                ps.done = true;
+            } else {
+                ps.C0 = fmaf(ps.T, pC0, ps.C0);
+                ps.C1 = fmaf(ps.T, pC1, ps.C1);
+                ps.C2 = fmaf(ps.T, pC2, ps.C2);
+                ps.D = fmaf(ps.T, pD, ps.D);
+                ps.T = ps.T * pT;
+                ps.n += pn;
+            }
+        } else {
+            walk_actor_lane<BWD>(ps, bw, fp, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc, grad_rec);
+        }
+    };
 
     const uint32_t bg0 = s_sub[0], bg1 = s_sub[1];
-    for (uint32_t base = bg0; base < bg1; base += BATCH) {
-        const uint32_t cnt = min((uint32_t)BATCH, bg1 - base);
-        if ((uint32_t)tid < cnt) {
-            const uint32_t r = __ldg(pval + base + tid);
+    const uint32_t n_batch = (bg1 - bg0 + CT_THREADS - 1) / CT_THREADS;
+    uint32_t r_ahead = 0, m_ahead = 0;
+    if (n_batch > 0) {
+        const uint32_t q0 = bg0 + tid;
+        if (q0 < bg1) {
+            const uint32_t r = __ldg(pval + q0);
             const float4* R = rec[r].v;
-            s_rec[tid][0] = __ldg(R);
-            s_rec[tid][1] = __ldg(R + 1);
-            s_rec[tid][2] = __ldg(R + 2);
-            s_rec[tid][3] = __ldg(R + 3);
-            s_r[tid] = r;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cp_async16(&s_rec[0][tid][k], R + k);
+            s_r[0][tid] = r;
+            s_m[0][tid] = __ldg(pmask + q0);
         }
+        cp_async_commit();
+        const uint32_t q1 = bg0 + CT_THREADS + tid;
+        if (q1 < bg1) {
+            r_ahead = __ldg(pval + q1);
+            m_ahead = __ldg(pmask + q1);
+        }
+    }
+    for (uint32_t bi = 0; bi < n_batch; ++bi) {
+        const int slot = bi & 1;
+        {
+            const uint32_t q1 = bg0 + (bi + 1) * CT_THREADS + tid;
+            if (q1 < bg1) {
+                const float4* R = rec[r_ahead].v;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async16(&s_rec[slot ^ 1][tid][k], R + k);
+                s_r[slot ^ 1][tid] = r_ahead;
+                s_m[slot ^ 1][tid] = (uint8_t)m_ahead;
+            }
+            cp_async_commit();
+            const uint32_t q2 = bg0 + (bi + 2) * CT_THREADS + tid;
+            if (q2 < bg1) {
+                r_ahead = __ldg(pval + q2);
+                m_ahead = __ldg(pmask + q2);
+            }
+        }
+        cp_async_wait_one();  // batch bi has landed (only batch bi+1 may still be in flight)
         __syncthreads();
+        const uint32_t cnt = min((uint32_t)CT_THREADS, bg1 - bg0 - bi * CT_THREADS);
         for (uint32_t j = 0; j < cnt; ++j) {
-            if (!BWD && ps.done) break;
+            if (__all_sync(0xffffffffu, ps.done)) break;
+            if (!(s_m[slot][j] & wbit)) continue;  // the voxel misses this warp's 8x4 block
             float acc[11];
             if (BWD) {
 #pragma unroll
                 for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
             }
             bool contributed = false;
-            const float4 g = s_rec[j][0];
+            const float4 g = s_rec[slot][j][0];
             float t_in, t_out;
             if (!ps.done) ps.tests += 1;
             if (!ps.done && slab_cube(ob, ib, g, t_in, t_out)) {
                 t_in = fmaxf(t_in, fp.near_);
                 t_out = fminf(t_out, fp.far_);
                 if (t_out > t_in) {
-                    const float4 da = s_rec[j][1], dd = s_rec[j][2], col = s_rec[j][3];
+                    const float4 da = s_rec[slot][j][1], dd = s_rec[slot][j][2], col = s_rec[slot][j][3];
                     float cur = fmaxf(t_in, tau_cur);
                     while (nxt.o >= 0 && nxt.a < t_out && !ps.done) {
                         if (nxt.a > cur) {
-                            add_segment<BWD>(ps, bw, fp, g, da, dd, col, ob, db_, cur, nxt.a, acc);
+                            add_segment<BWD, true>(ps, bw, fp, g, da, dd, col, ob, db_, cur, nxt.a, acc);
                             contributed = true;
                             if (ps.done) break;
                         }
-                        walk_actor<BWD>(ps, bw, fp, nxt, pval, rec, s_sub[nxt.o], s_sub[nxt.o + 1], dc, grad_rec);
+                        enter_actor(nxt);
                         tau_cur = nxt.b;
                         cur = fmaxf(cur, nxt.b);
                         nxt = next_interval(fp, s_act, n_ta, dc, tau_cur);
                         ps.boxes += n_ta;
                     }
                     if (!ps.done && t_out > cur) {
-                        add_segment<BWD>(ps, bw, fp, g, da, dd, col, ob, db_, cur, t_out, acc);
+                        add_segment<BWD, true>(ps, bw, fp, g, da, dd, col, ob, db_, cur, t_out, acc);
                         contributed = true;
                     }
                 }
             }
             if (BWD) {
-                // all lanes visit record j together: reduce across the warp, one atomic per value
+                // every lane visits record j of the batch together: reduce across the warp
                 const unsigned any = __ballot_sync(0xffffffffu, contributed);
-                if (any) {
-#pragma unroll
-                    for (int c = 0; c < 11; ++c) {
-                        float x = acc[c];
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-                        acc[c] = x;
-                    }
-                    if ((tid & 31) == 0) atomic_grad<BWD>(grad_rec, s_r[j], acc);
-                }
+                if (any) warp_reduce_add(acc, grad_rec + (size_t)s_r[slot][j] * GSTRIDE);
             }
         }
+        // every warp is done with this slot before batch bi+2 is copied into it
         if (__syncthreads_count(!ps.done) == 0) break;
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the loop (early exit)
     // actor intervals behind the last background hit
     while (nxt.o >= 0 && !ps.done) {
-        walk_actor<BWD>(ps, bw, fp, nxt, pval, rec, s_sub[nxt.o], s_sub[nxt.o + 1], dc, grad_rec);
+        enter_actor(nxt);
         tau_cur = nxt.b;
         nxt = next_interval(fp, s_act, n_ta, dc, tau_cur);
         ps.boxes += n_ta;
     }
+
+    // ---- phase 3: actor intervals replayed from their entry state ----
+    //   forward: only those where the ray stops; backward: every one reached (gradients)
+    for (int q = 0; q < n_lock; ++q) {
+        const int status = valid ? (int)s_st[q][5][tid] : 0;
+        const bool act = BWD ? status >= 1 : status == 2;
+        if (!__any_sync(0xffffffffu, act)) continue;
+        Pix pt;
+        pt.C0 = act ? s_st[q][0][tid] : 0.0f;
+        pt.C1 = act ? s_st[q][1][tid] : 0.0f;
+        pt.C2 = act ? s_st[q][2][tid] : 0.0f;
+        pt.D = act ? s_st[q][3][tid] : 0.0f;
+        pt.T = act ? s_st[q][4][tid] : 1.0f;
+        pt.n = 0;
+        pt.tests = 0;
+        pt.boxes = 0;
+        pt.done = false;
+        const int o = s_act[q];
+        walk_actor_warp<BWD, true>(pt, bw, fp, o, s_iv[q][0][tid], s_iv[q][1][tid], act, pval, pmask, wbit, rec,
+                                   s_sub[o], s_sub[o + 1], dc, grad_rec);
+        ps.tests += pt.tests;
+        if (!BWD && act) {
+            ps.C0 = pt.C0;
+            ps.C1 = pt.C1;
+            ps.C2 = pt.C2;
+            ps.D = pt.D;
+            ps.T = pt.T;
+            ps.n += pt.n;
+        }
+    }
+
     if (!BWD && work) {
         unsigned long long t = ps.tests, b = ps.boxes, n = ps.n;
 #pragma unroll
@@ -426,7 +696,7 @@ __global__ void __launch_bounds__(DV_BLOCK) k_composite(const __grid_constant__ 
             b += __shfl_down_sync(0xffffffffu, b, off);
             n += __shfl_down_sync(0xffffffffu, n, off);
         }
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(work + 0, t);
             atomicAdd(work + 1, b);
             atomicAdd(work + 2, n);
@@ -540,24 +810,27 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
 }  // namespace
 
 cudaError_t launch_composite_fwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint2* tile_range, const uint32_t* vis_start, float* rgb, float* depth,
-                                 float* alpha, uint32_t* n_seg, float* t_final, unsigned long long* work,
-                                 cudaStream_t s) {
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
+                                 float* rgb, float* depth, float* alpha, uint32_t* n_seg, float* t_final,
+                                 unsigned long long* work, cudaStream_t s) {
     const int n_tiles = fp.tiles_x * fp.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
-    k_composite<false><<<n_tiles, DV_BLOCK, 0, s>>>(fp, rec, pair_val, tile_range, vis_start, rgb, depth, alpha,
-                                                    n_seg, t_final, nullptr, nullptr, nullptr, nullptr, work);
+    k_composite<false><<<2 * n_tiles, CT_THREADS, 0, s>>>(fp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb,
+                                                          depth, alpha, n_seg, t_final, nullptr, nullptr, nullptr,
+                                                          nullptr, work);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_composite_bwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint2* tile_range, const uint32_t* vis_start, const float* rgb,
-                                 const float* depth, const uint32_t* n_seg, const float* t_final, const float* g_rgb,
-                                 const float* g_depth, const float* g_alpha, float* grad_rec, cudaStream_t s) {
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
+                                 const float* rgb, const float* depth, const uint32_t* n_seg, const float* t_final,
+                                 const float* g_rgb, const float* g_depth, const float* g_alpha, float* grad_rec,
+                                 cudaStream_t s) {
     const int n_tiles = fp.tiles_x * fp.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
-    k_composite<true><<<n_tiles, DV_BLOCK, 0, s>>>(fp, rec, pair_val, tile_range, vis_start, const_cast<float*>(rgb),
+    k_composite<true><<<2 * n_tiles, CT_THREADS, 0, s>>>(fp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order,
+                                                   const_cast<float*>(rgb),
                                                    const_cast<float*>(depth), nullptr, const_cast<uint32_t*>(n_seg),
                                                    const_cast<float*>(t_final), g_rgb, g_depth, g_alpha, grad_rec,
                                                    nullptr);

@@ -36,6 +36,7 @@ struct FrameParams {
     float near_, far_;
     float z_clip;        // camera-frame depth below which no ray sample can lie (near * min unit dz)
     int32_t K;
+    float inv_k;         // 1 / K
     float eps_stop;
     int32_t activation;
     int32_t n_oct;
@@ -120,16 +121,22 @@ cudaError_t launch_records(const FrameParams& fp, const uint32_t* sorted_g, int6
 cudaError_t launch_vis_start(const uint64_t* sorted_key, int64_t n_vis, int oct_shift, int n_oct,
                              uint32_t* vis_start, cudaStream_t s);
 cudaError_t launch_emit(const FrameParams& fp, const uint64_t* off, const uint64_t* rect_sorted, int64_t n_vis,
-                        uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s);
+                        int64_t n_pairs, uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s);
+cudaError_t launch_pair_mask(const FrameParams& fp, const uint32_t* pair_key, const uint32_t* pair_val,
+                             const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* pair_key, int64_t n_pairs, uint2* tile_range, int n_tiles, cudaStream_t s);
 cudaError_t launch_composite_fwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint2* tile_range, const uint32_t* vis_start, float* rgb, float* depth,
-                                 float* alpha, uint32_t* n_seg, float* t_final, unsigned long long* work,
-                                 cudaStream_t s);
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
+                                 float* rgb, float* depth, float* alpha, uint32_t* n_seg, float* t_final,
+                                 unsigned long long* work, cudaStream_t s);
 cudaError_t launch_composite_bwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint2* tile_range, const uint32_t* vis_start, const float* rgb,
-                                 const float* depth, const uint32_t* n_seg, const float* t_final, const float* g_rgb,
-                                 const float* g_depth, const float* g_alpha, float* grad_rec, cudaStream_t s);
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
+                                 const float* rgb, const float* depth, const uint32_t* n_seg, const float* t_final,
+                                 const float* g_rgb, const float* g_depth, const float* g_alpha, float* grad_rec,
+                                 cudaStream_t s);
+// tiles ordered by decreasing pair-list length (log2 buckets); scratch: 64 words
+cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* scratch64, uint32_t* order,
+                              cudaStream_t s);
 cudaError_t launch_sh_bwd(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
                           const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s);
 }  // namespace dv

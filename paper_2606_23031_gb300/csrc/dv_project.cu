@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ FramePa
     const uint32_t tx0 = pu0 >> 4, tx1 = pu1 >> 4, ty0 = pv0 >> 4, ty1 = pv1 >> 4;
     cnt[g] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
     vis[g] = 1;
-    rect[g] = (uint64_t)tx0 | ((uint64_t)tx1 << 16) | ((uint64_t)ty0 << 32) | ((uint64_t)ty1 << 48);
+    // pixel rectangle (tiles are its pixels >> 4)
+    rect[g] = (uint64_t)pu0 | ((uint64_t)pu1 << 16) | ((uint64_t)pv0 << 32) | ((uint64_t)pv1 << 48);
     // depth-order key (see the file comment)
     uint64_t bsp = 0;
     const int Lk = fp.Lkey;
@@ -257,19 +258,48 @@ __global__ void k_vis_start(const uint64_t* __restrict__ key, int64_t n_vis, int
         for (int q = o + 1; q <= n_oct; ++q) vis_start[q] = (uint32_t)n_vis;
 }
 
+// one thread per (tile, voxel) pair: the pair's voxel is the last record whose first
+// pair offset is <= the pair index (binary search), its tile the matching cell of
+// the voxel's tile rectangle (row-major), so every thread writes exactly one pair
 __global__ void k_emit(int tiles_x, const uint64_t* __restrict__ off, const uint64_t* __restrict__ rect_sorted,
-                       int64_t n_vis, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_vis) return;
-    uint64_t p = off[r];
-    const uint64_t rc = rect_sorted[r];
-    const uint32_t tx0 = rc & 0xffff, tx1 = (rc >> 16) & 0xffff, ty0 = (rc >> 32) & 0xffff, ty1 = rc >> 48;
-    for (uint32_t ty = ty0; ty <= ty1; ++ty)
-        for (uint32_t tx = tx0; tx <= tx1; ++tx) {
-            pkey[p] = ty * (uint32_t)tiles_x + tx;
-            pval[p] = (uint32_t)r;
-            ++p;
-        }
+                       int64_t n_vis, int64_t n_pairs, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    int64_t lo = 0, hi = n_vis - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= (uint64_t)p)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const uint64_t rc = __ldg(rect_sorted + lo);
+    const uint32_t tx0 = (rc & 0xffff) >> 4, tx1 = ((rc >> 16) & 0xffff) >> 4, ty0 = ((rc >> 32) & 0xffff) >> 4;
+    const uint32_t w = tx1 - tx0 + 1;
+    const uint32_t k = (uint32_t)((uint64_t)p - __ldg(off + lo));
+    pkey[p] = (ty0 + k / w) * (uint32_t)tiles_x + tx0 + k % w;
+    pval[p] = (uint32_t)lo;
+}
+
+// For every sorted pair: which of the tile's eight 8x4-pixel blocks (bit sy*2+sx for
+// the block at x in [8 sx, 8 sx + 8), y in [4 sy, 4 sy + 4)) the voxel's pixel
+// rectangle touches; a warp rendering a block skips the pairs without its bit.
+__global__ void k_pair_mask(int tiles_x, const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ pval,
+                            const uint64_t* __restrict__ rect_sorted, int64_t n_pairs, uint8_t* __restrict__ mask) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const uint32_t t = pkey[p];
+    const uint64_t rc = __ldg(rect_sorted + pval[p]);
+    const int x0 = (int)(t % (uint32_t)tiles_x) * DV_TILE, y0 = (int)(t / (uint32_t)tiles_x) * DV_TILE;
+    const int u0 = (int)(rc & 0xffff) - x0, u1 = (int)((rc >> 16) & 0xffff) - x0;
+    const int v0 = (int)((rc >> 32) & 0xffff) - y0, v1 = (int)(rc >> 48) - y0;
+    uint32_t m = 0;
+#pragma unroll
+    for (int sy = 0; sy < 4; ++sy)
+#pragma unroll
+        for (int sx = 0; sx < 2; ++sx)
+            if (u0 <= 8 * sx + 7 && u1 >= 8 * sx && v0 <= 4 * sy + 3 && v1 >= 4 * sy) m |= 1u << (sy * 2 + sx);
+    mask[p] = (uint8_t)m;
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ key, int64_t n, uint2* __restrict__ range) {
@@ -280,9 +310,64 @@ __global__ void k_ranges(const uint32_t* __restrict__ key, int64_t n, uint2* __r
     if (i == n - 1 || key[i + 1] != t) range[t].y = (uint32_t)(i + 1);
 }
 
+// Heaviest tiles first: counting sort of tiles by floor(log2(list length + 1)),
+// descending, so the longest CTAs start early and the short ones fill in behind
+// them.  The order inside a bucket does not matter (tiles are independent).
+__device__ __forceinline__ int tile_bucket(uint2 r) { return 31 - __clz((int)(r.y - r.x) + 1); }
+
+__global__ void k_tile_count(const uint2* __restrict__ range, int n_tiles, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) atomicAdd(&h[tile_bucket(range[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_tile_offsets(uint32_t* __restrict__ cnt_off) {
+    // cnt_off[0..31] counts -> cnt_off[32..63] start of each bucket, heaviest bucket first
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 31; b >= 0; --b) {
+            cnt_off[32 + b] = run;
+            run += cnt_off[b];
+        }
+    }
+}
+
+__global__ void k_tile_scatter(const uint2* __restrict__ range, int n_tiles, uint32_t* __restrict__ off,
+                               uint32_t* __restrict__ order) {
+    // block-local ranks first, then one global reservation per (block, bucket)
+    __shared__ uint32_t h[32], base[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = t < n_tiles ? tile_bucket(range[t]) : -1;
+    const uint32_t rank = b >= 0 ? atomicAdd(&h[b], 1u) : 0u;
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&off[threadIdx.x], h[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) order[base[b] + rank] = (uint32_t)t;
+}
+
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
+
+cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* scratch64, uint32_t* order,
+                              cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(scratch64, 0, 64 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_tile_count<<<nblk(n_tiles, 256), 256, 0, s>>>(tile_range, n_tiles, scratch64);
+    count_launches(1);
+    k_tile_offsets<<<1, 32, 0, s>>>(scratch64);
+    count_launches(1);
+    k_tile_scatter<<<nblk(n_tiles, 256), 256, 0, s>>>(tile_range, n_tiles, scratch64 + 32, order);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_project(const FrameParams& fp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
                            uint32_t* flags, cudaStream_t s) {
@@ -318,9 +403,17 @@ cudaError_t launch_vis_start(const uint64_t* sorted_key, int64_t n_vis, int oct_
 }
 
 cudaError_t launch_emit(const FrameParams& fp, const uint64_t* off, const uint64_t* rect_sorted, int64_t n_vis,
-                        uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s) {
-    if (n_vis <= 0) return cudaSuccess;
-    k_emit<<<nblk(n_vis, 256), 256, 0, s>>>(fp.tiles_x, off, rect_sorted, n_vis, pair_key, pair_val);
+                        int64_t n_pairs, uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s) {
+    if (n_vis <= 0 || n_pairs <= 0) return cudaSuccess;
+    k_emit<<<nblk(n_pairs, 256), 256, 0, s>>>(fp.tiles_x, off, rect_sorted, n_vis, n_pairs, pair_key, pair_val);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_mask(const FrameParams& fp, const uint32_t* pair_key, const uint32_t* pair_val,
+                             const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, cudaStream_t s) {
+    if (n_pairs <= 0) return cudaSuccess;
+    k_pair_mask<<<nblk(n_pairs, 256), 256, 0, s>>>(fp.tiles_x, pair_key, pair_val, rect_sorted, n_pairs, mask);
     count_launches(1);
     return cudaGetLastError();
 }

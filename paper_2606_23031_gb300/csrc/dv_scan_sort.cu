@@ -133,21 +133,20 @@ cudaError_t scan_impl(const Tin* in, Tout* out, int64_t n, Tout* total_dev, Aren
 // ---------------------------------------------------------------------------
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_MAX_ROUNDS = 16;  // keys per thread per pass, chosen per sort (see radix_impl)
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_RADIX = 256;
 
 template <typename K>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__ keys, int64_t n, int shift,
                                                             uint32_t mask, uint32_t* __restrict__ hist,
-                                                            int64_t nblocks) {
+                                                            int64_t nblocks, int rounds) {
     __shared__ uint32_t h[RS_RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = (int64_t)blockIdx.x * RS_THREADS * rounds;
 #pragma unroll 4
-    for (int r = 0; r < RS_ROUNDS; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
         if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & mask], 1u);
     }
@@ -160,16 +159,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
                                                                const uint32_t* __restrict__ vals, int64_t n,
                                                                int shift, uint32_t mask,
                                                                const uint32_t* __restrict__ offs, int64_t nblocks,
-                                                               K* __restrict__ okeys, uint32_t* __restrict__ ovals) {
+                                                               K* __restrict__ okeys, uint32_t* __restrict__ ovals,
+                                                               int rounds) {
     __shared__ uint32_t run[RS_RADIX];       // next free slot per digit (global index)
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     run[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
     for (int w = 0; w < RS_WARPS; ++w) wcnt[w][threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = (int64_t)blockIdx.x * RS_THREADS * rounds;
     const unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < RS_ROUNDS; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
         bool ok = i < n;
         K key = ok ? keys[i] : K(0);
@@ -203,7 +203,11 @@ template <typename K>
 cudaError_t radix_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits, Arena& ar,
                        cudaStream_t s) {
     if (n <= 1 || n_bits <= 0) return cudaSuccess;
-    int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+    // keys per block: as many as possible while still giving every SM two blocks
+    int rounds = RS_MAX_ROUNDS;
+    while (rounds > 1 && (n + (int64_t)RS_THREADS * rounds - 1) / ((int64_t)RS_THREADS * rounds) < 304) rounds >>= 1;
+    const int64_t tile = (int64_t)RS_THREADS * rounds;
+    int64_t nblocks = (n + tile - 1) / tile;
     uint32_t* hist = ar.alloc<uint32_t>((size_t)(nblocks * RS_RADIX));
     uint32_t* offs = ar.alloc<uint32_t>((size_t)(nblocks * RS_RADIX));
     if (!hist || !offs) return ar.err;
@@ -214,12 +218,12 @@ cudaError_t radix_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_al
     for (int shift = 0; shift < n_bits; shift += 8) {
         int bits = n_bits - shift < 8 ? n_bits - shift : 8;
         uint32_t mask = (1u << bits) - 1u;
-        k_radix_hist<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, n, shift, mask, hist, nblocks);
+        k_radix_hist<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, n, shift, mask, hist, nblocks, rounds);
         count_launches(1);
         cudaError_t e = scan_impl<uint32_t, uint32_t>(hist, offs, nblocks * RS_RADIX, nullptr, ar, s);
         if (e != cudaSuccess) return e;
         k_radix_scatter<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, src_v, n, shift, mask, offs, nblocks,
-                                                                     dst_k, dst_v);
+                                                                     dst_k, dst_v, rounds);
         count_launches(1);
         K* tk = src_k;
         src_k = dst_k;
