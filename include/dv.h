@@ -59,6 +59,7 @@ enum { DV_ROLE_BG = 0, DV_ROLE_ACTOR = 1 };
 enum { DV_ACT_EXPLIN = 0, DV_ACT_IDENTITY = 1 };
 
 #define DV_MAX_OCTREES 128   /* background + up to 127 actors per call */
+#define DV_MAX_VIEWS 64      /* views (cameras / requests) per render call */
 #define DV_MAX_LEVEL 16      /* deepest leaf level accepted */
 #define DV_MAX_IMAGE 16384   /* maximum W and H */
 #define DV_MAX_SH_DEGREE 3
@@ -96,6 +97,13 @@ typedef struct {
     dv_pose cam_to_world;   /* camera pose */
     float near_, far_;      /* ray distance range, 0 < near < far */
 } dv_camera;
+
+/* One view of a batched render: a camera and the poses of every octree for it
+ * (its own timestamp).  `poses` is a host array [n_oct] read during the call. */
+typedef struct {
+    dv_camera camera;
+    const dv_pose* poses;
+} dv_view;
 
 typedef struct {
     int32_t K;              /* midpoint samples per voxel segment, 1..16 */
@@ -138,6 +146,17 @@ dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_p
                     void* stream);
 
 /*
+ * Batched render of independent views (same method as dv_render): every view
+ * has its own camera and its own octree poses (e.g. requests at different
+ * timestamps), and all views go through one launch per stage, with the tiles of
+ * every view scheduled together.  Up to DV_MAX_VIEWS views; outputs are
+ * concatenated in view order as for dv_render; `saved` covers all views.
+ */
+dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_view* views, int32_t n_view,
+                          const dv_opts* opts, float* rgb, float* depth, float* alpha, dv_state** saved,
+                          void* stream);
+
+/*
  * Backward of dv_render (gradients flow through every voxel segment, Sec. 3.4).
  * Given dL/dRGB [sum H*W][3], dL/ddepth and dL/dalpha [sum H*W] (device; any of
  * the three may be NULL = zero), ADDS dL/d dens into d_dens[i] ([n_vox][8]) and
@@ -152,16 +171,18 @@ dv_status dv_render_backward(dv_ctx* ctx, dv_state* state, const float* d_rgb, c
 /* Releases a saved state (stream-ordered on the stream of its render call). */
 void dv_state_free(dv_state* state);
 
-/* Sizes of a saved state, per camera `cam`: visible voxels, (tile, voxel)
- * pairs, tiles.  Returns DV_ERR_INVALID_ARG for a bad index. */
-dv_status dv_state_stats(const dv_state* state, int32_t cam, int64_t* n_visible, int64_t* n_pairs,
+/* Sizes of a saved state: visible voxels, (tile, voxel) pairs and tiles of view
+ * `view`, or of the whole call for view = -1 (per-view figures synchronise the
+ * state's stream).  Returns DV_ERR_INVALID_ARG for a bad index. */
+dv_status dv_state_stats(const dv_state* state, int32_t view, int64_t* n_visible, int64_t* n_pairs,
                          int64_t* n_tiles);
 
-/* Work done by the forward compositing of camera `cam` of a saved state:
- * voxel slab tests (pixel x list entry examined before the ray stopped),
- * actor clip-box tests, and composited segments.  Synchronises the state's
- * stream.  These are the algorithmic units behind the compositing roofline. */
-dv_status dv_state_work(const dv_state* state, int32_t cam, uint64_t* tests, uint64_t* box_tests,
+/* Work done by the forward compositing of a saved state, over all its views
+ * (`view` must be -1, or 0 for a single-view state): voxel slab tests (pixel x
+ * list entry examined), actor clip-box tests, and composited segments.
+ * Synchronises the state's stream.  These are the algorithmic units behind the
+ * compositing roofline. */
+dv_status dv_state_work(const dv_state* state, int32_t view, uint64_t* tests, uint64_t* box_tests,
                         uint64_t* segments);
 
 /* Number of kernel launches this library has issued in this process (all
@@ -175,10 +196,10 @@ long long dv_launch_count(int32_t reset);
  * nodes, in a real-time loop that may not take an allocator lock, or with the
  * device memory fully committed to another allocator).  Same arguments,
  * results and accumulation semantics as dv_render_backward.  Its scratch is a
- * file-scope device array sized for 131072 visible voxels per camera (6 MiB,
- * held by every GPU that loads the library until exit); a state with a camera
- * above that limit fails with DV_ERR_CAPACITY before any work is enqueued.
- * All calls on a device share that array and clear it per camera before use:
+ * file-scope device array sized for 131072 visible voxels per render call,
+ * summed over its views (6 MiB, held by every GPU that loads the library until
+ * exit); a larger state fails with DV_ERR_CAPACITY before any work is enqueued.
+ * All calls on a device share that array and clear the part they use first:
  * calls whose GPU work overlaps (unordered streams) race on it.  The first call
  * on a device looks up the array's address; make it before any stream capture.
  */

@@ -93,6 +93,10 @@ class dv_camera(C.Structure):
                 ("cy", C.c_float), ("cam_to_world", dv_pose), ("near_", C.c_float), ("far_", C.c_float)]
 
 
+class dv_view(C.Structure):
+    _fields_ = [("camera", dv_camera), ("poses", C.c_void_p)]
+
+
 class dv_opts(C.Structure):
     _fields_ = [("K", C.c_int32), ("eps_stop", C.c_float), ("activation", C.c_int32), ("reserved", C.c_int32)]
 
@@ -123,6 +127,10 @@ def load(path: str | None = None):
                               C.c_int32, C.POINTER(dv_opts), C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(C.c_void_p), C.c_void_p]
     lib.dv_render.restype = C.c_int
+    lib.dv_render_views.argtypes = [C.c_void_p, C.POINTER(dv_octree), C.c_int32, C.POINTER(dv_view), C.c_int32,
+                                    C.POINTER(dv_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p),
+                                    C.c_void_p]
+    lib.dv_render_views.restype = C.c_int
     lib.dv_render_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]
     lib.dv_render_backward.restype = C.c_int
@@ -295,14 +303,15 @@ class State:
     def __init__(self, ctx: Context, handle, n_cam: int, keep):
         self.ctx, self.handle, self.n_cam, self.keep = ctx, handle, n_cam, keep
 
-    def stats(self, cam=0):
+    def stats(self, view=-1):
+        """Sizes of view ``view`` (-1: the whole call)."""
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
-        self.ctx.check(load().dv_state_stats(self.handle, cam, C.byref(a), C.byref(b), C.byref(c)))
+        self.ctx.check(load().dv_state_stats(self.handle, view, C.byref(a), C.byref(b), C.byref(c)))
         return {"n_visible": a.value, "n_pairs": b.value, "n_tiles": c.value}
 
-    def work(self, cam=0):
+    def work(self, view=-1):
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
-        self.ctx.check(load().dv_state_work(self.handle, cam, C.byref(a), C.byref(b), C.byref(c)))
+        self.ctx.check(load().dv_state_work(self.handle, view, C.byref(a), C.byref(b), C.byref(c)))
         return {"tests": a.value, "box_tests": b.value, "segments": c.value}
 
     def free(self):
@@ -346,6 +355,41 @@ def dv_render(octrees, poses, cams, opts=None, *, ctx: Context | None = None, sa
                            _stream_ptr(stream))
     ctx.check(status)
     state = State(ctx, st, len(cams), (octrees, dens, sh, rgb, depth, alpha)) if save_state else None
+    return rgb, depth, alpha, state
+
+
+def dv_render_views(octrees, views, opts=None, *, ctx: Context | None = None, save_state=False, out=None,
+                    dens=None, sh=None, stream=None):
+    """Batched render of independent views, each a (camera, per-octree poses) pair; one launch per
+    stage for all of them.  Returns (rgb, depth, alpha, state) with the images concatenated in view order."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = len(octrees)
+    oct_arr = (dv_octree * n)(*[o.struct(None if dens is None else dens[i], None if sh is None else sh[i])
+                                for i, o in enumerate(octrees)])
+    pose_arrs = [(dv_pose * n)(*[make_pose(p) for p in poses]) for _, poses in views]
+    varr = (dv_view * max(len(views), 1))()
+    for i, ((cam, _), pa) in enumerate(zip(views, pose_arrs)):
+        varr[i].camera = make_camera(cam)
+        varr[i].poses = C.cast(pa, C.c_void_p)
+    opts = opts or make_opts()
+    P = sum(int(c.W) * int(c.H) for c, _ in views)
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        rgb = torch.empty((P, 3), device=dev, dtype=torch.float32)
+        depth = torch.empty((P,), device=dev, dtype=torch.float32)
+        alpha = torch.empty((P,), device=dev, dtype=torch.float32)
+    else:
+        rgb, depth, alpha = out
+    st = C.c_void_p()
+    status = lib.dv_render_views(ctx.handle, oct_arr, n, varr, len(views), C.byref(opts),
+                                 C.c_void_p(rgb.data_ptr() if P else None),
+                                 C.c_void_p(depth.data_ptr() if P else None),
+                                 C.c_void_p(alpha.data_ptr() if P else None), C.byref(st) if save_state else None,
+                                 _stream_ptr(stream))
+    ctx.check(status)
+    state = State(ctx, st, len(views), (octrees, dens, sh, rgb, depth, alpha)) if save_state else None
     return rgb, depth, alpha, state
 
 
@@ -433,7 +477,7 @@ def render(octrees, poses, cams, opts=None, dens=None, sh=None):
     return _RenderFn.apply((octrees, poses, cams, opts or make_opts()), *dens, *sh)
 
 
-STATIC_MAX_VISIBLE = 1 << 17
+STATIC_MAX_VISIBLE = 1 << 17  # visible voxels per render call, summed over its views
 
 
 def dv_render_backward_static(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_dens=None, d_sh=None,

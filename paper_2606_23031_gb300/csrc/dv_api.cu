@@ -52,9 +52,13 @@ struct dv_ctx {
 
 namespace {
 
-struct CamState {
-    std::unique_ptr<FrameParams> fp;
-    int64_t n_vis = 0, n_pairs = 0, n_tiles = 0, pix_offset = 0;
+// device buffers of one render call (all views), kept for the backward
+struct BatchState {
+    BatchParams bp{};
+    int64_t n_vis = 0, n_pairs = 0, n_pix = 0;
+    ViewParams* d_views = nullptr;
+    OctParams* d_octs = nullptr;
+    std::vector<ViewParams> h_views;
     VoxRec* rec = nullptr;
     uint32_t* sorted_g = nullptr;
     uint32_t* pval = nullptr;
@@ -74,7 +78,7 @@ struct CamState {
 struct dv_state {
     dv_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
-    std::vector<CamState> cams;
+    BatchState b;
     std::vector<void*> owned;
 };
 
@@ -188,7 +192,7 @@ bool rotation_ok(const float* Rf) {
 }
 
 // conservative tile rectangle of an actor clip box (camera frame points, near-plane clipped)
-void box_rect(const FrameParams& fp, const M3& Mc, const double* mc, const float* h, int16_t* rect) {
+void box_rect(const ViewParams& fp, const M3& Mc, const double* mc, const float* h, int16_t* rect) {
     double P[8][3];
     for (int c = 0; c < 8; ++c) {
         double q[3] = {(c & 1) ? h[0] : -h[0], (c & 2) ? h[1] : -h[1], (c & 4) ? h[2] : -h[2]};
@@ -240,39 +244,32 @@ void box_rect(const FrameParams& fp, const M3& Mc, const double* mc, const float
     rect[3] = (int16_t)(pv1 / DV_TILE);
 }
 
-dv_status make_params(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pose* poses, const dv_camera& cam,
-                      const dv_opts& opt, FrameParams& fp) {
-    memset(&fp, 0, sizeof(fp));
-    fp.W = cam.W;
-    fp.H = cam.H;
-    fp.tiles_x = (cam.W + DV_TILE - 1) / DV_TILE;
-    fp.tiles_y = (cam.H + DV_TILE - 1) / DV_TILE;
-    fp.fx = cam.fx;
-    fp.fy = cam.fy;
-    fp.cx = cam.cx;
-    fp.cy = cam.cy;
-    fp.near_ = cam.near_;
-    fp.far_ = cam.far_;
-    fp.K = opt.K;
-    fp.inv_k = 1.0f / (float)opt.K;
-    fp.eps_stop = opt.eps_stop;
-    fp.activation = opt.activation;
-    fp.n_oct = n_oct;
+// constants of one view: ViewParams plus one OctParams per octree
+void make_view(const dv_octree* oct, int n_oct, const dv_pose* poses, const dv_camera& cam, int Lkey,
+               ViewParams& vp, OctParams* P) {
+    memset(&vp, 0, sizeof(vp));
+    vp.W = cam.W;
+    vp.H = cam.H;
+    vp.tiles_x = (cam.W + DV_TILE - 1) / DV_TILE;
+    vp.tiles_y = (cam.H + DV_TILE - 1) / DV_TILE;
+    vp.fx = cam.fx;
+    vp.fy = cam.fy;
+    vp.cx = cam.cx;
+    vp.cy = cam.cy;
+    vp.near_ = cam.near_;
+    vp.far_ = cam.far_;
     // smallest unit-direction z over the image: samples at distance >= near have z >= near * that
     double xm = std::fmax(std::fabs(0.5 - (double)cam.cx), std::fabs((double)cam.W - 0.5 - (double)cam.cx)) /
                 (double)cam.fx;
     double ym = std::fmax(std::fabs(0.5 - (double)cam.cy), std::fabs((double)cam.H - 0.5 - (double)cam.cy)) /
                 (double)cam.fy;
-    fp.z_clip = (float)(0.999 * (double)cam.near_ / std::sqrt(1.0 + xm * xm + ym * ym));
-    int Lkey = 0;
-    for (int i = 0; i < n_oct; ++i) Lkey = std::max(Lkey, (int)oct[i].max_level);
-    fp.Lkey = Lkey;
-    fp.oct_shift = 3 * Lkey;
+    vp.z_clip = (float)(0.999 * (double)cam.near_ / std::sqrt(1.0 + xm * xm + ym * ym));
     M3 Rc = load_R(cam.cam_to_world.R);
     double tc[3] = {cam.cam_to_world.t[0], cam.cam_to_world.t[1], cam.cam_to_world.t[2]};
     int64_t off = 0;
     for (int i = 0; i < n_oct; ++i) {
-        OctParams& P = fp.oc[i];
+        OctParams& Q = P[i];
+        memset(&Q, 0, sizeof(Q));
         M3 Ri = load_R(poses[i].R);
         double ti[3] = {poses[i].t[0], poses[i].t[1], poses[i].t[2]};
         M3 A = mul(tr(Ri), Rc);
@@ -282,50 +279,51 @@ dv_status make_params(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pos
         mv(tr(Rc), dt, mc);
         mv(tr(Ri), ndt, ol);
         for (int k = 0; k < 9; ++k) {
-            P.A[k] = (float)A.a[k];
-            P.M[k] = (float)Mc.a[k];
+            Q.A[k] = (float)A.a[k];
+            Q.M[k] = (float)Mc.a[k];
         }
         for (int k = 0; k < 3; ++k) {
-            P.m[k] = (float)mc[k];
-            P.o_loc[k] = (float)ol[k];
-            P.clip_half[k] = oct[i].clip_half[k];
-            P.root_min[k] = (float)(oct[i].center[k] - 0.5 * oct[i].root_size);
+            Q.m[k] = (float)mc[k];
+            Q.o_loc[k] = (float)ol[k];
+            Q.clip_half[k] = oct[i].clip_half[k];
+            Q.root_min[k] = (float)(oct[i].center[k] - 0.5 * oct[i].root_size);
         }
-        P.root_size = (float)oct[i].root_size;
-        P.role = oct[i].role;
-        P.sh_degree = oct[i].sh_degree;
-        P.max_level = oct[i].max_level;
+        Q.root_size = (float)oct[i].root_size;
+        Q.role = oct[i].role;
+        Q.sh_degree = oct[i].sh_degree;
+        Q.max_level = oct[i].max_level;
         for (int k = 0; k < 3; ++k) {
-            double rel = ((double)P.o_loc[k] - (double)P.root_min[k]) / (double)P.root_size;
+            double rel = ((double)Q.o_loc[k] - (double)Q.root_min[k]) / (double)Q.root_size;
             double q = std::floor(2.0 * rel * std::ldexp(1.0, Lkey));
             q = std::fmax(std::fmin(q, 1e15), -1e15);
-            P.O2[k] = (int64_t)q;
+            Q.O2[k] = (int64_t)q;
         }
-        P.vox_offset = off;
-        P.n_vox = oct[i].n_vox;
-        P.key = oct[i].key;
-        P.dens = oct[i].dens;
-        P.sh = oct[i].sh;
+        Q.vox_offset = off;
+        Q.n_vox = oct[i].n_vox;
+        Q.key = oct[i].key;
+        Q.dens = oct[i].dens;
+        Q.sh = oct[i].sh;
         off += oct[i].n_vox;
         if (oct[i].role == DV_ROLE_ACTOR) {
-            box_rect(fp, Mc, mc, oct[i].clip_half, P.rect);
+            box_rect(vp, Mc, mc, oct[i].clip_half, Q.rect);
         } else {
-            P.rect[0] = 1;
-            P.rect[2] = 0;
-            P.rect[1] = 1;
-            P.rect[3] = 0;
+            Q.rect[0] = 1;
+            Q.rect[2] = 0;
+            Q.rect[1] = 1;
+            Q.rect[3] = 0;
         }
     }
-    fp.n_vox_total = off;
-    (void)ctx;
-    return DV_OK;
 }
 
-dv_status validate(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* poses, const dv_camera* cams,
-                   int32_t n_cam, const dv_opts* opts) {
-    if (!oct || !poses || n_oct < 1) return fail(ctx, DV_ERR_INVALID_ARG, "need at least the background octree");
+int bits_for(int64_t n) {
+    int b = 0;
+    while (((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+dv_status validate_octrees(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_opts* opts) {
+    if (!oct || n_oct < 1) return fail(ctx, DV_ERR_INVALID_ARG, "need at least the background octree");
     if (n_oct > DV_MAX_OCTREES) return fail(ctx, DV_ERR_CAPACITY, "too many octrees (max 128)");
-    if (n_cam < 0 || (n_cam > 0 && !cams)) return fail(ctx, DV_ERR_INVALID_ARG, "bad camera array");
     if (!opts) return fail(ctx, DV_ERR_INVALID_ARG, "opts is NULL");
     if (opts->K < 1 || opts->K > 16) return fail(ctx, DV_ERR_INVALID_ARG, "K must be in 1..16");
     if (!(opts->eps_stop >= 0.0f) || !std::isfinite(opts->eps_stop))
@@ -350,37 +348,30 @@ dv_status validate(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_po
             if (o.role == DV_ROLE_ACTOR && !(o.clip_half[k] >= 0.0f && std::isfinite(o.clip_half[k])))
                 return fail(ctx, DV_ERR_INVALID_ARG, "bad clip box");
         }
-        if (!rotation_ok(poses[i].R)) return fail(ctx, DV_ERR_INVALID_POSE, "octree pose is not a rotation");
-        for (int k = 0; k < 3; ++k)
-            if (!std::isfinite(poses[i].t[k])) return fail(ctx, DV_ERR_INVALID_POSE, "non-finite translation");
         total += o.n_vox;
     }
-    int oct_bits = 0;
-    while ((1 << oct_bits) < n_oct) ++oct_bits;
-    int Lkey = 0;
-    for (int i = 0; i < n_oct; ++i) Lkey = std::max(Lkey, (int)oct[i].max_level);
-    if (3 * Lkey + oct_bits > 64) return fail(ctx, DV_ERR_CAPACITY, "depth key does not fit 64 bits");
     if (total >= (int64_t)1 << 31) return fail(ctx, DV_ERR_CAPACITY, "more than 2^31 voxels in one call");
-    for (int c = 0; c < n_cam; ++c) {
-        const dv_camera& cm = cams[c];
-        if (cm.W < 0 || cm.H < 0 || cm.W > DV_MAX_IMAGE || cm.H > DV_MAX_IMAGE)
-            return fail(ctx, DV_ERR_INVALID_ARG, "image size out of range");
-        if (!(cm.fx > 0.0f) || !(cm.fy > 0.0f) || !std::isfinite(cm.fx) || !std::isfinite(cm.fy) ||
-            !std::isfinite(cm.cx) || !std::isfinite(cm.cy))
-            return fail(ctx, DV_ERR_INVALID_ARG, "bad intrinsics");
-        if (!(cm.near_ > 0.0f) || !(cm.far_ > cm.near_) || !std::isfinite(cm.far_))
-            return fail(ctx, DV_ERR_INVALID_ARG, "need 0 < near < far");
-        if (!rotation_ok(cm.cam_to_world.R)) return fail(ctx, DV_ERR_INVALID_POSE, "camera pose is not a rotation");
-        for (int k = 0; k < 3; ++k)
-            if (!std::isfinite(cm.cam_to_world.t[k])) return fail(ctx, DV_ERR_INVALID_POSE, "non-finite camera");
-    }
     return DV_OK;
 }
 
-int bits_for(int64_t n) {
-    int b = 0;
-    while (((int64_t)1 << b) < n) ++b;
-    return b;
+dv_status validate_view(dv_ctx* ctx, const dv_camera& cm, const dv_pose* poses, int n_oct) {
+    if (!poses) return fail(ctx, DV_ERR_INVALID_ARG, "NULL pose array");
+    for (int i = 0; i < n_oct; ++i) {
+        if (!rotation_ok(poses[i].R)) return fail(ctx, DV_ERR_INVALID_POSE, "octree pose is not a rotation");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(poses[i].t[k])) return fail(ctx, DV_ERR_INVALID_POSE, "non-finite translation");
+    }
+    if (cm.W < 0 || cm.H < 0 || cm.W > DV_MAX_IMAGE || cm.H > DV_MAX_IMAGE)
+        return fail(ctx, DV_ERR_INVALID_ARG, "image size out of range");
+    if (!(cm.fx > 0.0f) || !(cm.fy > 0.0f) || !std::isfinite(cm.fx) || !std::isfinite(cm.fy) ||
+        !std::isfinite(cm.cx) || !std::isfinite(cm.cy))
+        return fail(ctx, DV_ERR_INVALID_ARG, "bad intrinsics");
+    if (!(cm.near_ > 0.0f) || !(cm.far_ > cm.near_) || !std::isfinite(cm.far_))
+        return fail(ctx, DV_ERR_INVALID_ARG, "need 0 < near < far");
+    if (!rotation_ok(cm.cam_to_world.R)) return fail(ctx, DV_ERR_INVALID_POSE, "camera pose is not a rotation");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(cm.cam_to_world.t[k])) return fail(ctx, DV_ERR_INVALID_POSE, "non-finite camera");
+    return DV_OK;
 }
 
 template <typename T>
@@ -394,36 +385,80 @@ T* pool_alloc(dv_ctx* ctx, cudaStream_t s, size_t count, std::vector<void*>& own
     return (T*)p;
 }
 
-// one camera's forward; state buffers go to `st` (always, freed by the caller when not saved)
-dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_state* st, float* rgb,
-                        float* depth, float* alpha, cudaStream_t s) {
+// The forward of one render call over all its views.  State buffers go to `st`
+// (freed by the caller when no state is wanted).
+dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pose* const* view_poses,
+                       const dv_camera* cams, int n_view, const dv_opts& opt, dv_state* st, float* rgb, float* depth,
+                       float* alpha, cudaStream_t s) {
     using namespace dv;
-    const FrameParams& fp = fp_in;
+    BatchState& B = st->b;
+    BatchParams& bp = B.bp;
+    memset(&bp, 0, sizeof(bp));
+    bp.n_view = n_view;
+    bp.n_oct = n_oct;
+    bp.K = opt.K;
+    bp.inv_k = 1.0f / (float)opt.K;
+    bp.eps_stop = opt.eps_stop;
+    bp.activation = opt.activation;
+    int Lkey = 0;
+    for (int i = 0; i < n_oct; ++i) Lkey = std::max(Lkey, (int)oct[i].max_level);
+    bp.Lkey = Lkey;
+    bp.oct_shift = 3 * Lkey;
+    bp.view_shift = bp.oct_shift + bits_for(n_oct);
+    int64_t off = 0;
+    for (int i = 0; i < n_oct; ++i) {
+        bp.vox_offset[i] = off;
+        off += oct[i].n_vox;
+    }
+    for (int i = n_oct; i <= DV_MAX_OCTREES; ++i) bp.vox_offset[i] = off;
+    bp.n_vox = off;
+    // per-view constants
+    std::vector<OctParams> h_octs((size_t)n_view * n_oct);
+    B.h_views.resize(n_view);
+    int64_t tiles = 0, pix = 0;
+    for (int v = 0; v < n_view; ++v) {
+        make_view(oct, n_oct, view_poses[v], cams[v], Lkey, B.h_views[v], &h_octs[(size_t)v * n_oct]);
+        B.h_views[v].tile_base = (int32_t)tiles;
+        B.h_views[v].pix_base = pix;
+        bp.tile_base[v] = (int32_t)tiles;
+        tiles += (int64_t)B.h_views[v].tiles_x * B.h_views[v].tiles_y;
+        pix += (int64_t)cams[v].W * cams[v].H;
+    }
+    for (int v = n_view; v <= DV_MAX_VIEWS; ++v) bp.tile_base[v] = (int32_t)tiles;
+    if (tiles >= ((int64_t)1 << 31)) return fail(ctx, DV_ERR_CAPACITY, "too many tiles in one call");
+    bp.n_tiles = (int32_t)tiles;
+    B.n_pix = pix;
+    B.rgb = rgb;
+    B.depth = depth;
     cudaError_t e = cudaSuccess;
+    std::vector<void*>& own = st->owned;
+    B.d_views = pool_alloc<ViewParams>(ctx, s, (size_t)n_view, own, e);
+    B.d_octs = pool_alloc<OctParams>(ctx, s, h_octs.size(), own, e);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B.d_views, B.h_views.data(), sizeof(ViewParams) * n_view, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B.d_octs, h_octs.data(), sizeof(OctParams) * h_octs.size(), cudaMemcpyHostToDevice, s);
+    bp.views = B.d_views;
+    bp.octs = B.d_octs;
+    const int64_t NT = bp.n_vox * n_view;
+    if (NT >= ((int64_t)1 << 32)) return fail(ctx, DV_ERR_CAPACITY, "views x voxels exceeds 2^32");
+    B.n_seg = pool_alloc<uint32_t>(ctx, s, (size_t)pix, own, e);
+    B.t_final = pool_alloc<float>(ctx, s, (size_t)pix, own, e);
+    B.range = pool_alloc<uint2>(ctx, s, (size_t)tiles, own, e);
+    B.vis_start = pool_alloc<uint32_t>(ctx, s, (size_t)n_view * n_oct + 1, own, e);
+    B.tile_order = pool_alloc<uint32_t>(ctx, s, (size_t)tiles, own, e);
+    B.work = pool_alloc<unsigned long long>(ctx, s, 4, own, e);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.work, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate state");
+
     Arena ar;
     ar.pool = ctx->pool;
     ar.stream = s;
-    const int64_t Vt = fp.n_vox_total;
-    const int64_t npix = (int64_t)fp.W * fp.H;
-    const int64_t n_tiles = (int64_t)fp.tiles_x * fp.tiles_y;
-    cs.n_tiles = n_tiles;
-    cs.rgb = rgb;
-    cs.depth = depth;
-    std::vector<void*>& own = st->owned;
-    cs.n_seg = pool_alloc<uint32_t>(ctx, s, (size_t)npix, own, e);
-    cs.t_final = pool_alloc<float>(ctx, s, (size_t)npix, own, e);
-    cs.range = pool_alloc<uint2>(ctx, s, (size_t)n_tiles, own, e);
-    cs.vis_start = pool_alloc<uint32_t>(ctx, s, (size_t)fp.n_oct + 1, own, e);
-    cs.tile_order = pool_alloc<uint32_t>(ctx, s, (size_t)n_tiles, own, e);
-    cs.work = pool_alloc<unsigned long long>(ctx, s, 4, own, e);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cs.work, 0, 4 * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate state");
-
-    uint32_t* cnt = ar.alloc<uint32_t>((size_t)Vt);
-    uint64_t* rect = ar.alloc<uint64_t>((size_t)Vt);
-    uint64_t* skey = ar.alloc<uint64_t>((size_t)Vt);
-    uint32_t* vis = ar.alloc<uint32_t>((size_t)Vt);
-    uint32_t* pos = ar.alloc<uint32_t>((size_t)Vt);
+    uint32_t* cnt = ar.alloc<uint32_t>((size_t)NT);
+    uint64_t* rect = ar.alloc<uint64_t>((size_t)NT);
+    uint64_t* skey = ar.alloc<uint64_t>((size_t)NT);
+    uint32_t* vis = ar.alloc<uint32_t>((size_t)NT);
+    uint32_t* pos = ar.alloc<uint32_t>((size_t)NT);
     if (ar.err != cudaSuccess) {
         ar.release();
         return cuda_fail(ctx, ar.err, "allocate scratch");
@@ -434,12 +469,12 @@ dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_
     e = cudaMemsetAsync(ctx->d_scalars, 0, 3 * sizeof(uint64_t), s);
     {
         Prof p(ctx, KP_PROJECT, s);
-        if (e == cudaSuccess) e = launch_project(fp, cnt, rect, skey, vis, d_flags, s);
+        if (e == cudaSuccess) e = launch_project(bp, cnt, rect, skey, vis, d_flags, s);
     }
     {
         Prof p(ctx, KP_SCAN, s);
-        if (e == cudaSuccess) e = scan_u32_to_u32(vis, pos, Vt, (uint32_t*)d_nvis, ar, s);
-        if (e == cudaSuccess) e = scan_u32_to_u64(cnt, nullptr, Vt, d_npairs, ar, s);
+        if (e == cudaSuccess) e = scan_u32_to_u32(vis, pos, NT, (uint32_t*)d_nvis, ar, s);
+        if (e == cudaSuccess) e = scan_u32_to_u64(cnt, nullptr, NT, d_npairs, ar, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_scalars, ctx->d_scalars, 3 * sizeof(uint64_t),
                                               cudaMemcpyDeviceToHost, s);
@@ -458,49 +493,48 @@ dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_
     }
     if (P >= ((int64_t)1 << 32) - 1) {
         ar.release();
-        return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 (tile, voxel) pairs for one camera");
+        return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 (tile, voxel) pairs in one call");
     }
-    cs.n_vis = n_vis;
-    cs.n_pairs = P;
-    // depth-order sort of the visible voxels
+    B.n_vis = n_vis;
+    B.n_pairs = P;
+    // depth-order sort of the visible (view, voxel)s
     uint64_t* k0 = ar.alloc<uint64_t>((size_t)n_vis);
     uint64_t* k1 = ar.alloc<uint64_t>((size_t)n_vis);
     uint32_t* g1 = ar.alloc<uint32_t>((size_t)n_vis);
-    cs.sorted_g = pool_alloc<uint32_t>(ctx, s, (size_t)n_vis, own, e);
-    uint32_t* g0 = cs.sorted_g;
+    B.sorted_g = pool_alloc<uint32_t>(ctx, s, (size_t)n_vis, own, e);
+    uint32_t* g0 = B.sorted_g;
     if (ar.err != cudaSuccess || e != cudaSuccess) {
         ar.release();
         return cuda_fail(ctx, ar.err != cudaSuccess ? ar.err : e, "allocate sort");
     }
     {
         Prof p(ctx, KP_COMPACT, s);
-        e = launch_compact(vis, pos, skey, Vt, k0, g0, s);
+        e = launch_compact(vis, pos, skey, NT, k0, g0, s);
     }
     uint64_t* kk = k0;
     uint32_t* gg = g0;
     {
         Prof p(ctx, KP_SORT_VOX, s);
-        if (e == cudaSuccess)
-            e = radix_sort_u64(kk, gg, k1, g1, n_vis, fp.oct_shift + bits_for(fp.n_oct), ar, s);
+        if (e == cudaSuccess) e = radix_sort_u64(kk, gg, k1, g1, n_vis, bp.view_shift + bits_for(n_view), ar, s);
     }
-    if (e == cudaSuccess && gg != cs.sorted_g)
-        e = cudaMemcpyAsync(cs.sorted_g, gg, sizeof(uint32_t) * (size_t)n_vis, cudaMemcpyDeviceToDevice, s);
-    cs.rec = pool_alloc<VoxRec>(ctx, s, (size_t)n_vis, own, e);
+    if (e == cudaSuccess && gg != B.sorted_g)
+        e = cudaMemcpyAsync(B.sorted_g, gg, sizeof(uint32_t) * (size_t)n_vis, cudaMemcpyDeviceToDevice, s);
+    B.rec = pool_alloc<VoxRec>(ctx, s, (size_t)n_vis, own, e);
     uint32_t* cnt_sorted = ar.alloc<uint32_t>((size_t)n_vis);
     uint64_t* rect_sorted = ar.alloc<uint64_t>((size_t)n_vis);
-    uint64_t* off = ar.alloc<uint64_t>((size_t)n_vis);
+    uint64_t* off_pairs = ar.alloc<uint64_t>((size_t)n_vis);
     if (ar.err != cudaSuccess || e != cudaSuccess) {
         ar.release();
         return cuda_fail(ctx, ar.err != cudaSuccess ? ar.err : e, "sort voxels");
     }
     {
         Prof p(ctx, KP_RECORDS, s);
-        e = launch_records(fp, cs.sorted_g, n_vis, cnt, rect, cs.rec, cnt_sorted, rect_sorted, s);
-        if (e == cudaSuccess) e = launch_vis_start(kk, n_vis, fp.oct_shift, fp.n_oct, cs.vis_start, s);
+        e = launch_records(bp, B.sorted_g, n_vis, cnt, rect, B.rec, cnt_sorted, rect_sorted, s);
+        if (e == cudaSuccess) e = launch_vis_start(bp, kk, n_vis, B.vis_start, s);
     }
     {
         Prof p(ctx, KP_SCAN, s);
-        if (e == cudaSuccess) e = scan_u32_to_u64(cnt_sorted, off, n_vis, nullptr, ar, s);
+        if (e == cudaSuccess) e = scan_u32_to_u64(cnt_sorted, off_pairs, n_vis, nullptr, ar, s);
     }
     // pairs
     uint32_t* pk0 = ar.alloc<uint32_t>((size_t)P);
@@ -513,33 +547,51 @@ dv_status render_camera(dv_ctx* ctx, const FrameParams& fp_in, CamState& cs, dv_
     }
     {
         Prof p(ctx, KP_EMIT, s);
-        e = launch_emit(fp, off, rect_sorted, n_vis, P, pk0, pv0, s);
+        e = launch_emit(bp, off_pairs, rect_sorted, B.sorted_g, n_vis, P, pk0, pv0, s);
     }
     uint32_t* pk = pk0;
     uint32_t* pv = pv0;
     {
         Prof p(ctx, KP_SORT_PAIRS, s);
-        if (e == cudaSuccess) e = radix_sort_u32(pk, pv, pk1, pv1, P, bits_for(n_tiles), ar, s);
+        if (e == cudaSuccess) e = radix_sort_u32(pk, pv, pk1, pv1, P, bits_for(tiles), ar, s);
     }
     if (e == cudaSuccess && pv != pv0)
         e = cudaMemcpyAsync(pv0, pv, sizeof(uint32_t) * (size_t)P, cudaMemcpyDeviceToDevice, s);
-    cs.pval = pv0;
-    cs.pmask = pool_alloc<uint8_t>(ctx, s, (size_t)P, own, e);
+    B.pval = pv0;
+    B.pmask = pool_alloc<uint8_t>(ctx, s, (size_t)P, own, e);
     {
         Prof p(ctx, KP_RANGES, s);
-        if (e == cudaSuccess) e = launch_pair_mask(fp, pk, cs.pval, rect_sorted, P, cs.pmask, s);
-        if (e == cudaSuccess) e = launch_ranges(pk, P, cs.range, (int)n_tiles, s);
+        if (e == cudaSuccess) e = launch_pair_mask(bp, pk, B.pval, rect_sorted, P, B.pmask, s);
+        if (e == cudaSuccess) e = launch_ranges(pk, P, B.range, (int)tiles, s);
         uint32_t* tscr = ar.alloc<uint32_t>(64);
-        if (e == cudaSuccess) e = tscr ? launch_tile_order(cs.range, (int)n_tiles, tscr, cs.tile_order, s) : ar.err;
+        if (e == cudaSuccess) e = tscr ? launch_tile_order(B.range, (int)tiles, tscr, B.tile_order, s) : ar.err;
     }
     {
         Prof p(ctx, KP_FWD, s);
         if (e == cudaSuccess)
-            e = launch_composite_fwd(fp, cs.rec, cs.pval, cs.pmask, cs.range, cs.vis_start, cs.tile_order, rgb, depth, alpha,
-                                     cs.n_seg, cs.t_final, cs.work, s);
+            e = launch_composite_fwd(bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, rgb, depth,
+                                     alpha, B.n_seg, B.t_final, B.work, s);
     }
     ar.release();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render");
+    return DV_OK;
+}
+
+dv_status backward_batch(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth, const float* d_alpha,
+                         float* const* d_dens, float* const* d_sh, float* grad, cudaStream_t s) {
+    BatchState& B = st->b;
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * 12 * (size_t)B.n_vis, s);
+    {
+        Prof p(ctx, KP_BWD, s);
+        if (e == cudaSuccess)
+            e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, B.rgb,
+                                         B.depth, B.t_final, d_rgb, d_depth, d_alpha, grad, s);
+    }
+    {
+        Prof p(ctx, KP_SHBWD, s);
+        if (e == cudaSuccess) e = dv::launch_sh_bwd(B.bp, B.sorted_g, B.n_vis, B.rec, grad, d_dens, d_sh, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "backward");
     return DV_OK;
 }
 
@@ -606,16 +658,26 @@ void dv_destroy(dv_ctx* ctx) {
 
 const char* dv_last_error(const dv_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
-dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* poses, const dv_camera* cams,
-                    int32_t n_cam, const dv_opts* opts, float* rgb, float* depth, float* alpha, dv_state** saved,
-                    void* stream) {
+static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* const* view_poses,
+                               const dv_camera* cams, int32_t n_view, const dv_opts* opts, float* rgb, float* depth,
+                               float* alpha, dv_state** saved, void* stream) {
     if (!ctx) return DV_ERR_INVALID_ARG;
     ctx->err.clear();
     if (saved) *saved = nullptr;
-    dv_status vs = validate(ctx, oct, n_oct, poses, cams, n_cam, opts);
+    dv_status vs = validate_octrees(ctx, oct, n_oct, opts);
     if (vs != DV_OK) return vs;
+    if (n_view < 0 || (n_view > 0 && (!cams || !view_poses))) return fail(ctx, DV_ERR_INVALID_ARG, "bad view array");
+    if (n_view > DV_MAX_VIEWS) return fail(ctx, DV_ERR_CAPACITY, "too many views in one call (max 64)");
     int64_t total_pix = 0;
-    for (int c = 0; c < n_cam; ++c) total_pix += (int64_t)cams[c].W * cams[c].H;
+    for (int v = 0; v < n_view; ++v) {
+        vs = validate_view(ctx, cams[v], view_poses[v], n_oct);
+        if (vs != DV_OK) return vs;
+        total_pix += (int64_t)cams[v].W * cams[v].H;
+    }
+    int Lkey = 0;
+    for (int i = 0; i < n_oct; ++i) Lkey = std::max(Lkey, (int)oct[i].max_level);
+    if (3 * Lkey + bits_for(n_oct) + bits_for(n_view) > 64)
+        return fail(ctx, DV_ERR_CAPACITY, "depth key does not fit 64 bits");
     if (total_pix > 0 && (!rgb || !depth || !alpha)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL output buffer");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -623,23 +685,12 @@ dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_p
     if (!st) return fail(ctx, DV_ERR_NOMEM, "host allocation");
     st->ctx = ctx;
     st->stream = s;
-    st->cams.resize(n_cam);
-    int64_t pix_off = 0;
-    for (int c = 0; c < n_cam; ++c) {
-        CamState& cs = st->cams[c];
-        cs.fp.reset(new (std::nothrow) FrameParams());
-        if (!cs.fp) {
-            free_state(st.release());
-            return fail(ctx, DV_ERR_NOMEM, "host allocation");
-        }
-        make_params(ctx, oct, n_oct, poses, cams[c], *opts, *cs.fp);
-        cs.pix_offset = pix_off;
-        dv_status rs = render_camera(ctx, *cs.fp, cs, st.get(), rgb + pix_off * 3, depth + pix_off, alpha + pix_off, s);
+    if (n_view > 0) {
+        dv_status rs = render_batch(ctx, oct, n_oct, view_poses, cams, n_view, *opts, st.get(), rgb, depth, alpha, s);
         if (rs != DV_OK) {
             free_state(st.release());
             return rs;
         }
-        pix_off += (int64_t)cams[c].W * cams[c].H;
     }
     if (saved)
         *saved = st.release();
@@ -648,63 +699,98 @@ dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_p
     return DV_OK;
 }
 
+dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* poses, const dv_camera* cams,
+                    int32_t n_cam, const dv_opts* opts, float* rgb, float* depth, float* alpha, dv_state** saved,
+                    void* stream) {
+    if (n_cam < 0 || n_cam > DV_MAX_VIEWS) {
+        if (ctx) ctx->err = "camera count out of range (0..64)";
+        return n_cam < 0 ? DV_ERR_INVALID_ARG : DV_ERR_CAPACITY;
+    }
+    std::vector<const dv_pose*> vp((size_t)std::max(n_cam, 1), poses);
+    return render_common(ctx, oct, n_oct, vp.data(), cams, n_cam, opts, rgb, depth, alpha, saved, stream);
+}
+
+dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_view* views, int32_t n_view,
+                          const dv_opts* opts, float* rgb, float* depth, float* alpha, dv_state** saved,
+                          void* stream) {
+    if (n_view < 0 || n_view > DV_MAX_VIEWS || (n_view > 0 && !views)) {
+        if (ctx) ctx->err = "view count out of range (0..64) or NULL views";
+        return n_view > DV_MAX_VIEWS ? DV_ERR_CAPACITY : DV_ERR_INVALID_ARG;
+    }
+    std::vector<const dv_pose*> vp((size_t)std::max(n_view, 1), nullptr);
+    std::vector<dv_camera> cams((size_t)std::max(n_view, 1));
+    for (int v = 0; v < n_view; ++v) {
+        vp[v] = views[v].poses;
+        cams[v] = views[v].camera;
+    }
+    return render_common(ctx, oct, n_oct, vp.data(), cams.data(), n_view, opts, rgb, depth, alpha, saved, stream);
+}
+
 dv_status dv_render_backward(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
                              const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream) {
     if (!ctx || !st) return DV_ERR_INVALID_ARG;
     ctx->err.clear();
     if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
+    if (st->b.n_vis == 0) return DV_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    for (auto& cs : st->cams) {
-        const FrameParams& fp = *cs.fp;
-        if (cs.n_vis == 0) continue;
-        dv::Arena ar;
-        ar.pool = ctx->pool;
-        ar.stream = s;
-        float* grad = ar.alloc<float>((size_t)cs.n_vis * 12);
-        if (!grad) {
-            ar.release();
-            return cuda_fail(ctx, ar.err, "allocate gradient scratch");
-        }
-        cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * 12 * (size_t)cs.n_vis, s);
-        const int64_t po = cs.pix_offset;
-        {
-            Prof p(ctx, KP_BWD, s);
-            if (e == cudaSuccess)
-                e = dv::launch_composite_bwd(fp, cs.rec, cs.pval, cs.pmask, cs.range, cs.vis_start, cs.tile_order, cs.rgb,
-                                             cs.depth, cs.n_seg, cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
-                                             d_depth ? d_depth + po : nullptr, d_alpha ? d_alpha + po : nullptr,
-                                             grad, s);
-        }
-        {
-            Prof p(ctx, KP_SHBWD, s);
-            if (e == cudaSuccess) e = dv::launch_sh_bwd(fp, cs.sorted_g, cs.n_vis, cs.rec, grad, d_dens, d_sh, s);
-        }
+    dv::Arena ar;
+    ar.pool = ctx->pool;
+    ar.stream = s;
+    float* grad = ar.alloc<float>((size_t)st->b.n_vis * 12);
+    if (!grad) {
         ar.release();
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "backward");
+        return cuda_fail(ctx, ar.err, "allocate gradient scratch");
     }
-    return DV_OK;
+    dv_status r = backward_batch(ctx, st, d_rgb, d_depth, d_alpha, d_dens, d_sh, grad, s);
+    ar.release();
+    return r;
 }
 
 void dv_state_free(dv_state* st) { free_state(st); }
 
-dv_status dv_state_stats(const dv_state* st, int32_t cam, int64_t* n_visible, int64_t* n_pairs, int64_t* n_tiles) {
-    if (!st || cam < 0 || cam >= (int32_t)st->cams.size()) return DV_ERR_INVALID_ARG;
-    const CamState& cs = st->cams[cam];
-    if (n_visible) *n_visible = cs.n_vis;
-    if (n_pairs) *n_pairs = cs.n_pairs;
-    if (n_tiles) *n_tiles = cs.n_tiles;
+dv_status dv_state_stats(const dv_state* st, int32_t view, int64_t* n_visible, int64_t* n_pairs, int64_t* n_tiles) {
+    if (!st) return DV_ERR_INVALID_ARG;
+    const BatchState& B = st->b;
+    if (view == -1 || (view == 0 && B.bp.n_view == 1)) {
+        if (n_visible) *n_visible = B.n_vis;
+        if (n_pairs) *n_pairs = B.n_pairs;
+        if (n_tiles) *n_tiles = B.bp.n_tiles;
+        return DV_OK;
+    }
+    if (view < 0 || view >= B.bp.n_view) return DV_ERR_INVALID_ARG;
+    DeviceGuard g(st->ctx->device);
+    const int n_oct = B.bp.n_oct;
+    uint32_t vs[2] = {0, 0};
+    const int t0 = B.bp.tile_base[view], t1 = B.bp.tile_base[view + 1];
+    cudaError_t e = cudaMemcpyAsync(&vs[0], B.vis_start + (size_t)view * n_oct, 4, cudaMemcpyDeviceToHost, st->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&vs[1], B.vis_start + (size_t)(view + 1) * n_oct, 4, cudaMemcpyDeviceToHost, st->stream);
+    // pairs of the view: from the first tile's start to the last tile's end (tiles are contiguous per view)
+    std::vector<uint2> rg((size_t)(t1 - t0));
+    if (e == cudaSuccess && t1 > t0)
+        e = cudaMemcpyAsync(rg.data(), B.range + t0, sizeof(uint2) * rg.size(), cudaMemcpyDeviceToHost, st->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) return DV_ERR_CUDA;
+    int64_t np = 0;
+    for (const uint2& x : rg) np += (int64_t)x.y - (int64_t)x.x;
+    if (n_visible) *n_visible = (int64_t)vs[1] - (int64_t)vs[0];
+    if (n_pairs) *n_pairs = np;
+    if (n_tiles) *n_tiles = t1 - t0;
     return DV_OK;
 }
 
-dv_status dv_state_work(const dv_state* st, int32_t cam, uint64_t* tests, uint64_t* box_tests, uint64_t* segments) {
-    if (!st || cam < 0 || cam >= (int32_t)st->cams.size()) return DV_ERR_INVALID_ARG;
-    const CamState& cs = st->cams[cam];
+dv_status dv_state_work(const dv_state* st, int32_t view, uint64_t* tests, uint64_t* box_tests, uint64_t* segments) {
+    if (!st) return DV_ERR_INVALID_ARG;
+    const BatchState& B = st->b;
+    if (!(view == -1 || (view == 0 && B.bp.n_view == 1))) return DV_ERR_INVALID_ARG;
     unsigned long long h[4] = {0, 0, 0, 0};
-    DeviceGuard g(st->ctx->device);
-    if (cudaMemcpyAsync(h, cs.work, sizeof(h), cudaMemcpyDeviceToHost, st->stream) != cudaSuccess ||
-        cudaStreamSynchronize(st->stream) != cudaSuccess)
-        return DV_ERR_CUDA;
+    if (B.work) {
+        DeviceGuard g(st->ctx->device);
+        if (cudaMemcpyAsync(h, B.work, sizeof(h), cudaMemcpyDeviceToHost, st->stream) != cudaSuccess ||
+            cudaStreamSynchronize(st->stream) != cudaSuccess)
+            return DV_ERR_CUDA;
+    }
     if (tests) *tests = h[0];
     if (box_tests) *box_tests = h[1];
     if (segments) *segments = h[2];
@@ -763,11 +849,11 @@ dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, doub
 // no pool allocation, no library routine that allocates).
 //
 // Limits and sharing rules:
-//  * at most DV_STATIC_MAX_VISIBLE visible voxels per camera (12 floats each,
-//    6 MiB in total); a larger camera is rejected with DV_ERR_CAPACITY before
-//    any work is enqueued;
+//  * at most DV_STATIC_MAX_VISIBLE visible voxels per render call, summed over
+//    its views (12 floats each, 6 MiB in total); a larger call is rejected
+//    with DV_ERR_CAPACITY before any work is enqueued;
 //  * every GPU that loads this library holds the array until the process exits;
-//  * all calls on a device share the one array: each camera's slice is cleared
+//  * all calls on a device share the one array: the slice a call uses is cleared
 //    (cudaMemsetAsync) before use, but two calls whose work overlaps on the GPU
 //    (different streams, no ordering between them) race on it and corrupt each
 //    other's gradients -- order such calls on one stream or with events;
@@ -809,26 +895,14 @@ extern "C" dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* st, const 
     if (!ctx || !st) return DV_ERR_INVALID_ARG;
     ctx->err.clear();
     if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
-    for (const auto& cs : st->cams)
-        if (cs.n_vis > DV_STATIC_MAX_VISIBLE)
-            return fail(ctx, DV_ERR_CAPACITY,
-                        "dv_render_backward_static: a camera has " + std::to_string(cs.n_vis) +
-                            " visible voxels, above the static limit of " + std::to_string(DV_STATIC_MAX_VISIBLE));
+    if (st->b.n_vis > DV_STATIC_MAX_VISIBLE)
+        return fail(ctx, DV_ERR_CAPACITY,
+                    "dv_render_backward_static: the render call has " + std::to_string(st->b.n_vis) +
+                        " visible voxels, above the static limit of " + std::to_string(DV_STATIC_MAX_VISIBLE));
+    if (st->b.n_vis == 0) return DV_OK;
     DeviceGuard g(ctx->device);
     float* grad = nullptr;
     cudaError_t e = static_grad_ptr(ctx->device, &grad);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(static gradient scratch)");
-    cudaStream_t s = (cudaStream_t)stream;
-    for (auto& cs : st->cams) {
-        if (cs.n_vis == 0) continue;
-        const int64_t po = cs.pix_offset;
-        e = cudaMemsetAsync(grad, 0, sizeof(float) * 12 * (size_t)cs.n_vis, s);
-        if (e == cudaSuccess)
-            e = dv::launch_composite_bwd(*cs.fp, cs.rec, cs.pval, cs.pmask, cs.range, cs.vis_start, cs.tile_order, cs.rgb,
-                                         cs.depth, cs.n_seg, cs.t_final, d_rgb ? d_rgb + po * 3 : nullptr,
-                                         d_depth ? d_depth + po : nullptr, d_alpha ? d_alpha + po : nullptr, grad, s);
-        if (e == cudaSuccess) e = dv::launch_sh_bwd(*cs.fp, cs.sorted_g, cs.n_vis, cs.rec, grad, d_dens, d_sh, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "dv_render_backward_static");
-    }
-    return DV_OK;
+    return backward_batch(ctx, st, d_rgb, d_depth, d_alpha, d_dens, d_sh, grad, (cudaStream_t)stream);
 }

@@ -155,11 +155,11 @@ __device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, const f
 // Composites one segment (with the stop test when STOP); with GRAD also adds
 // this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
 template <bool GRAD, bool STOP>
-__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const FrameParams& fp, float4 g, float4 da,
+__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchParams& bp, float4 g, float4 da,
                                             float4 db, float4 col, const float* o, const float* d, float t0,
                                             float t1, float* acc) {
     float dtd[8];
-    const float tau = seg_tau<GRAD>(g, da, db, o, d, t0, t1, fp.K, fp.inv_k, fp.activation, dtd);
+    const float tau = seg_tau<GRAD>(g, da, db, o, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
     const float e = __expf(-tau);  // transmittance of the segment
     const float alpha = 1.0f - e;
     const float w = ps.T * alpha;
@@ -183,27 +183,27 @@ __device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const FrameP
         acc[9] = fmaf(bw.g1, w, acc[9]);
         acc[10] = fmaf(bw.g2, w, acc[10]);
     }
-    if (STOP && ps.T < fp.eps_stop) ps.done = true;
+    if (STOP && ps.T < bp.eps_stop) ps.done = true;
 }
 
 // next actor interval ahead of tau_cur (first-entered box owns overlaps)
-__device__ __forceinline__ ActInt next_interval(const FrameParams& fp, const int16_t* tact, int n_ta, const float* dc,
-                                                float tau_cur) {
+__device__ __forceinline__ ActInt next_interval(const OctParams* __restrict__ vo, float t_near, float t_far,
+                                                const int16_t* tact, int n_ta, const float* dc, float tau_cur) {
     ActInt r;
     r.o = -1;
     r.q = -1;
     r.a = INFINITY;
     r.b = 0.0f;
     for (int q = 0; q < n_ta; ++q) {
-        const OctParams& P = fp.oc[tact[q]];
+        const OctParams& P = vo[tact[q]];
         float d[3], inv[3], a, b;
         rotate(P.A, dc, d);
         inv[0] = 1.0f / d[0];
         inv[1] = 1.0f / d[1];
         inv[2] = 1.0f / d[2];
         if (!slab_box(P.o_loc, inv, P.clip_half, a, b)) continue;
-        a = fmaxf(a, fp.near_);
-        b = fminf(b, fp.far_);
+        a = fmaxf(a, t_near);
+        b = fminf(b, t_far);
         if (!(b > a) || !(b > tau_cur)) continue;
         if (a < r.a) {
             r.o = tact[q];
@@ -274,11 +274,12 @@ __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
 // Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
 // NTA lockstep slots).
 template <bool GRAD>
-__device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const FrameParams& fp, const ActInt& it,
+__device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const BatchParams& bp,
+                                             const OctParams* __restrict__ vo, const ActInt& it,
                                              const uint32_t* __restrict__ pval, const uint8_t* __restrict__ pmask,
                                              uint32_t wbit, const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
                                              const float* dc, float* grad_rec) {
-    const OctParams& P = fp.oc[it.o];
+    const OctParams& P = vo[it.o];
     float d[3], inv[3];
     rotate(P.A, dc, d);
     inv[0] = 1.0f / d[0];
@@ -299,7 +300,7 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Frame
         float acc[11];
 #pragma unroll
         for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
-        add_segment<GRAD, true>(ps, bw, fp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), o, d, t0, t1, acc);
+        add_segment<GRAD, true>(ps, bw, bp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), o, d, t0, t1, acc);
         if (GRAD) atomic_grad(grad_rec, r, acc);
     }
 }
@@ -308,12 +309,13 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Frame
 // composites the segments inside its interval [a, b] into st (STOP: with the
 // stop test).  With GRAD the per-record gradients are reduced across the warp.
 template <bool GRAD, bool STOP>
-__device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const FrameParams& fp, int o, float a, float b,
+__device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const BatchParams& bp,
+                                             const OctParams* __restrict__ vo, int o, float a, float b,
                                              bool act, const uint32_t* __restrict__ pval,
                                              const uint8_t* __restrict__ pmask, uint32_t wbit,
                                              const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
                                              const float* dc, float* grad_rec) {
-    const OctParams& P = fp.oc[o];
+    const OctParams& P = vo[o];
     float d[3], inv[3];
     rotate(P.A, dc, d);
     inv[0] = 1.0f / d[0];
@@ -346,7 +348,7 @@ __device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const Frame
                 t0 = fmaxf(t0, a);
                 t1 = fminf(t1, b);
                 if (t1 > t0) {
-                    add_segment<GRAD, STOP>(st, bw, fp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), ol, d, t0, t1,
+                    add_segment<GRAD, STOP>(st, bw, bp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), ol, d, t0, t1,
                                             acc);
                     hit = true;
                 }
@@ -375,7 +377,7 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 //                         1 partial applied, 2 stop inside (replay)
 
 template <bool BWD>
-__global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __grid_constant__ FrameParams fp,
+__global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __grid_constant__ BatchParams bp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
                                                         const uint8_t* __restrict__ pmask,
@@ -398,13 +400,30 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
     __shared__ float s_st[NTA][6][CT_THREADS];
     __shared__ int s_nact;
 
-    const int tile = (int)tile_order[blockIdx.x >> 1];
+    const int gtile = (int)tile_order[blockIdx.x >> 1];
     const int half = blockIdx.x & 1;
-    const int tx = tile % fp.tiles_x, ty = tile / fp.tiles_x;
-    const uint2 rg = tile_range[tile];
+    int view = 0;
+    {
+        int lo = 0, hi = bp.n_view - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bp.tile_base[mid] <= gtile)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        view = lo;
+    }
+    const ViewParams& fp = bp.views[view];
+    const OctParams* __restrict__ vo = bp.octs + view * bp.n_oct;
+    const int tiles_x = fp.tiles_x, W = fp.W, H = fp.H;
+    const float t_near = fp.near_, t_far = fp.far_;
+    const int tile = gtile - bp.tile_base[view];
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const uint2 rg = tile_range[gtile];
     const int tid = threadIdx.x;
-    if (tid <= fp.n_oct) {
-        const uint32_t key = vis_start[tid];
+    if (tid <= bp.n_oct) {
+        const uint32_t key = vis_start[view * bp.n_oct + tid];
         uint32_t lo = rg.x, hi = rg.y;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -417,8 +436,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
     }
     if (tid == 0) {
         int n = 0;
-        for (int o = 1; o < fp.n_oct; ++o) {
-            const OctParams& P = fp.oc[o];
+        for (int o = 1; o < bp.n_oct; ++o) {
+            const OctParams& P = vo[o];
             if (P.role == DV_ROLE_ACTOR && P.rect[0] <= tx && tx <= P.rect[2] && P.rect[1] <= ty && ty <= P.rect[3])
                 s_act[n++] = (int16_t)o;
         }
@@ -430,8 +449,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
     const uint32_t wbit = 1u << ((half * 2 + (warp >> 1)) * 2 + (warp & 1));  // this warp's 8x4 block
     const int u = tx * DV_TILE + (warp & 1) * 8 + (lane & 7);
     const int v = ty * DV_TILE + half * 8 + (warp >> 1) * 4 + (lane >> 3);
-    const bool valid = u < fp.W && v < fp.H;
-    const int64_t pix = (int64_t)v * fp.W + u;
+    const bool valid = u < W && v < H;
+    const int64_t pix = fp.pix_base + (int64_t)v * W + u;
 
     float dc[3];
     {
@@ -442,7 +461,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
         dc[1] = y * in;
         dc[2] = in;
     }
-    const OctParams& B = fp.oc[0];
+    const OctParams& B = vo[0];
     float db_[3], ib[3];
     rotate(B.A, dc, db_);
     ib[0] = 1.0f / db_[0];
@@ -483,9 +502,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
         s_st[q][5][tid] = 0.0f;
     }
     if (valid && n_ta > 0) {
-        float tau = fp.near_;
+        float tau = t_near;
         for (int guard = 0; guard < n_ta; ++guard) {
-            const ActInt it = next_interval(fp, s_act, n_ta, dc, tau);
+            const ActInt it = next_interval(vo, t_near, t_far, s_act, n_ta, dc, tau);
             ps.boxes += n_ta;
             if (it.o < 0) break;
             if (it.q < NTA) {
@@ -511,7 +530,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
         const int o = s_act[q];
         // a lane whose own transmittance already falls below eps_stop will stop inside this
         // actor whatever T it enters with (T <= 1), so its partial may stop there too
-        walk_actor_warp<false, true>(pt, bw, fp, o, a, b, act, pval, pmask, wbit, rec, s_sub[o], s_sub[o + 1], dc,
+        walk_actor_warp<false, true>(pt, bw, bp, vo, o, a, b, act, pval, pmask, wbit, rec, s_sub[o], s_sub[o + 1], dc,
                                      nullptr);
         ps.tests += pt.tests;
         if (act) {
@@ -525,11 +544,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
     }
 
     // ---- phase 2: background walk, applying actor partials in order ----
-    float tau_cur = fp.near_;
+    float tau_cur = t_near;
     ActInt nxt;
     nxt.o = -1;
     if (valid && n_ta > 0) {
-        nxt = next_interval(fp, s_act, n_ta, dc, tau_cur);
+        nxt = next_interval(vo, t_near, t_far, s_act, n_ta, dc, tau_cur);
         ps.boxes += n_ta;
     }
     // enters actor interval `it`: apply its partial, or stop inside it, or walk it per lane
@@ -539,7 +558,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
             const float pC0 = s_st[q][0][tid], pC1 = s_st[q][1][tid], pC2 = s_st[q][2][tid];
             const float pD = s_st[q][3][tid], pT = s_st[q][4][tid];
             const uint32_t pn = (uint32_t)__float_as_int(s_st[q][5][tid]);
-            const bool stop_inside = ps.T * pT < fp.eps_stop;
+            const bool stop_inside = ps.T * pT < bp.eps_stop;
             if (BWD || stop_inside) {
                 s_st[q][0][tid] = ps.C0;
                 s_st[q][1][tid] = ps.C1;
@@ -559,7 +578,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
                 ps.n += pn;
             }
         } else {
-            walk_actor_lane<BWD>(ps, bw, fp, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc, grad_rec);
+            walk_actor_lane<BWD>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc, grad_rec);
         }
     };
 
@@ -617,25 +636,25 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
             float t_in, t_out;
             if (!ps.done) ps.tests += 1;
             if (!ps.done && slab_cube(ob, ib, g, t_in, t_out)) {
-                t_in = fmaxf(t_in, fp.near_);
-                t_out = fminf(t_out, fp.far_);
+                t_in = fmaxf(t_in, t_near);
+                t_out = fminf(t_out, t_far);
                 if (t_out > t_in) {
                     const float4 da = s_rec[slot][j][1], dd = s_rec[slot][j][2], col = s_rec[slot][j][3];
                     float cur = fmaxf(t_in, tau_cur);
                     while (nxt.o >= 0 && nxt.a < t_out && !ps.done) {
                         if (nxt.a > cur) {
-                            add_segment<BWD, true>(ps, bw, fp, g, da, dd, col, ob, db_, cur, nxt.a, acc);
+                            add_segment<BWD, true>(ps, bw, bp, g, da, dd, col, ob, db_, cur, nxt.a, acc);
                             contributed = true;
                             if (ps.done) break;
                         }
                         enter_actor(nxt);
                         tau_cur = nxt.b;
                         cur = fmaxf(cur, nxt.b);
-                        nxt = next_interval(fp, s_act, n_ta, dc, tau_cur);
+                        nxt = next_interval(vo, t_near, t_far, s_act, n_ta, dc, tau_cur);
                         ps.boxes += n_ta;
                     }
                     if (!ps.done && t_out > cur) {
-                        add_segment<BWD, true>(ps, bw, fp, g, da, dd, col, ob, db_, cur, t_out, acc);
+                        add_segment<BWD, true>(ps, bw, bp, g, da, dd, col, ob, db_, cur, t_out, acc);
                         contributed = true;
                     }
                 }
@@ -654,7 +673,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
     while (nxt.o >= 0 && !ps.done) {
         enter_actor(nxt);
         tau_cur = nxt.b;
-        nxt = next_interval(fp, s_act, n_ta, dc, tau_cur);
+        nxt = next_interval(vo, t_near, t_far, s_act, n_ta, dc, tau_cur);
         ps.boxes += n_ta;
     }
 
@@ -675,7 +694,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
         pt.boxes = 0;
         pt.done = false;
         const int o = s_act[q];
-        walk_actor_warp<BWD, true>(pt, bw, fp, o, s_iv[q][0][tid], s_iv[q][1][tid], act, pval, pmask, wbit, rec,
+        walk_actor_warp<BWD, true>(pt, bw, bp, vo, o, s_iv[q][0][tid], s_iv[q][1][tid], act, pval, pmask, wbit, rec,
                                    s_sub[o], s_sub[o + 1], dc, grad_rec);
         ps.tests += pt.tests;
         if (!BWD && act) {
@@ -741,18 +760,10 @@ __device__ __forceinline__ void sh_basis_f(int deg, float x, float y, float z, f
     b[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
 }
 
-struct ShBwdOct {
-    float o_loc[3];
-    int32_t sh_degree;
-    int64_t vox_offset;
-    const float* sh;
-    float* d_dens;
-    float* d_sh;
-};
-
 struct ShBwdParams {
-    int32_t n_oct;
-    ShBwdOct oc[DV_MAX_OCTREES];
+    BatchParams bp;
+    float* d_dens[DV_MAX_OCTREES];
+    float* d_sh[DV_MAX_OCTREES];
 };
 
 __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdParams sp,
@@ -760,25 +771,32 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
                                                 const VoxRec* __restrict__ rec, const float* __restrict__ grad_rec) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
+    const BatchParams& bp = sp.bp;
     const uint32_t gidx = sorted_g[r];
-    int lo = 0, hi = sp.n_oct - 1;
+    const int view = (int)(gidx / (uint64_t)bp.n_vox);
+    const int64_t gv = (int64_t)gidx - (int64_t)view * bp.n_vox;
+    int lo = 0, hi = bp.n_oct - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (sp.oc[mid].vox_offset <= (int64_t)gidx)
+        if (bp.vox_offset[mid] <= gv)
             lo = mid;
         else
             hi = mid - 1;
     }
-    const ShBwdOct& P = sp.oc[lo];
-    const int64_t v = (int64_t)gidx - P.vox_offset;
+    const OctParams& P = bp.octs[view * bp.n_oct + lo];
+    const int64_t v = gv - bp.vox_offset[lo];
     const float* gr = grad_rec + (size_t)r * GSTRIDE;
-    if (P.d_dens) {
-        float* dd = P.d_dens + v * 8;
+    float* d_dens = sp.d_dens[lo];
+    float* d_sh = sp.d_sh[lo];
+    // several views may touch the same voxel: accumulate with atomics
+    if (d_dens) {
+        float* dd = d_dens + v * 8;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) dd[c] += gr[c];
+        for (int c = 0; c < 8; ++c)
+            if (gr[c] != 0.0f) atomicAdd(dd + c, gr[c]);
     }
     const float gc0 = gr[8], gc1 = gr[9], gc2 = gr[10];
-    if (!P.d_sh || (gc0 == 0.0f && gc1 == 0.0f && gc2 == 0.0f)) return;
+    if (!d_sh || (gc0 == 0.0f && gc1 == 0.0f && gc2 == 0.0f)) return;
     const float4 g = rec[r].v[0];
     float gx = g.x + 0.5f * g.w - P.o_loc[0];
     float gy = g.y + 0.5f * g.w - P.o_loc[1];
@@ -799,61 +817,51 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
         c2 = fmaf(b[q], shv[q * 3 + 2], c2);
     }
     const float m0 = c0 > 0.0f ? gc0 : 0.0f, m1 = c1 > 0.0f ? gc1 : 0.0f, m2 = c2 > 0.0f ? gc2 : 0.0f;
-    float* ds = P.d_sh + v * nsh * 3;
+    float* ds = d_sh + v * nsh * 3;
     for (int q = 0; q < nsh; ++q) {
-        ds[q * 3 + 0] += b[q] * m0;
-        ds[q * 3 + 1] += b[q] * m1;
-        ds[q * 3 + 2] += b[q] * m2;
+        if (m0 != 0.0f) atomicAdd(ds + q * 3 + 0, b[q] * m0);
+        if (m1 != 0.0f) atomicAdd(ds + q * 3 + 1, b[q] * m1);
+        if (m2 != 0.0f) atomicAdd(ds + q * 3 + 2, b[q] * m2);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_composite_fwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
-                                 float* rgb, float* depth, float* alpha, uint32_t* n_seg, float* t_final,
-                                 unsigned long long* work, cudaStream_t s) {
-    const int n_tiles = fp.tiles_x * fp.tiles_y;
-    if (n_tiles <= 0) return cudaSuccess;
-    k_composite<false><<<2 * n_tiles, CT_THREADS, 0, s>>>(fp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb,
-                                                          depth, alpha, n_seg, t_final, nullptr, nullptr, nullptr,
-                                                          nullptr, work);
+cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
+                                 const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
+                                 float* t_final, unsigned long long* work, cudaStream_t s) {
+    if (bp.n_tiles <= 0) return cudaSuccess;
+    k_composite<false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range, vis_start,
+                                                             tile_order, rgb, depth, alpha, n_seg, t_final, nullptr,
+                                                             nullptr, nullptr, nullptr, work);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_bwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
-                                 const float* rgb, const float* depth, const uint32_t* n_seg, const float* t_final,
-                                 const float* g_rgb, const float* g_depth, const float* g_alpha, float* grad_rec,
-                                 cudaStream_t s) {
-    const int n_tiles = fp.tiles_x * fp.tiles_y;
-    if (n_tiles <= 0) return cudaSuccess;
-    k_composite<true><<<2 * n_tiles, CT_THREADS, 0, s>>>(fp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order,
-                                                   const_cast<float*>(rgb),
-                                                   const_cast<float*>(depth), nullptr, const_cast<uint32_t*>(n_seg),
-                                                   const_cast<float*>(t_final), g_rgb, g_depth, g_alpha, grad_rec,
-                                                   nullptr);
+cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
+                                 const uint32_t* tile_order, const float* rgb, const float* depth,
+                                 const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
+                                 float* grad_rec, cudaStream_t s) {
+    if (bp.n_tiles <= 0) return cudaSuccess;
+    k_composite<true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range, vis_start,
+                                                            tile_order, const_cast<float*>(rgb),
+                                                            const_cast<float*>(depth), nullptr, nullptr,
+                                                            const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+                                                            grad_rec, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sh_bwd(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
+cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
                           const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s) {
     if (n_vis <= 0) return cudaSuccess;
     ShBwdParams sp;
-    sp.n_oct = fp.n_oct;
-    for (int o = 0; o < fp.n_oct; ++o) {
-        const OctParams& P = fp.oc[o];
-        ShBwdOct& q = sp.oc[o];
-        q.o_loc[0] = P.o_loc[0];
-        q.o_loc[1] = P.o_loc[1];
-        q.o_loc[2] = P.o_loc[2];
-        q.sh_degree = P.sh_degree;
-        q.vox_offset = P.vox_offset;
-        q.sh = P.sh;
-        q.d_dens = d_dens ? d_dens[o] : nullptr;
-        q.d_sh = d_sh ? d_sh[o] : nullptr;
+    sp.bp = bp;
+    for (int o = 0; o < DV_MAX_OCTREES; ++o) {
+        sp.d_dens[o] = (d_dens && o < bp.n_oct) ? d_dens[o] : nullptr;
+        sp.d_sh[o] = (d_sh && o < bp.n_oct) ? d_sh[o] : nullptr;
     }
     k_sh_bwd<<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(sp, sorted_g, n_vis, rec, grad_rec);
     count_launches(1);

@@ -7,9 +7,8 @@
 #include "dv.h"
 
 #define DV_TILE 16
-#define DV_BLOCK 256  // one thread per pixel of a 16x16 tile
 
-// Per (camera, octree) constants, computed on the host in double and rounded once.
+// Per (view, octree) constants, computed on the host in double and rounded once.
 struct OctParams {
     float A[9];          // unit camera-frame ray direction -> octree-local direction (R_i^T R_c)
     float M[9];          // octree-local point -> camera frame, rotation (R_c^T R_i)
@@ -21,38 +20,50 @@ struct OctParams {
     int32_t role;
     int32_t sh_degree;
     int32_t max_level;
-    int16_t rect[4];     // actor clip box tile rectangle [tx0, ty0, tx1, ty1] (tx0 > tx1: off screen)
+    int16_t rect[4];     // actor clip box tile rectangle [tx0, ty0, tx1, ty1] in the view (tx0 > tx1: off screen)
     int64_t O2[3];       // floor(2 * (o_loc - root_min) / root * 2^Lkey): BSP side tests in integers
-    int64_t vox_offset;  // first global voxel index of this octree
+    int64_t vox_offset;  // first voxel index of this octree within a view
     int64_t n_vox;
     const uint64_t* key;
     const float* dens;
     const float* sh;
 };
 
-struct FrameParams {
+// Per view (one camera of one render request).
+struct ViewParams {
     int32_t W, H, tiles_x, tiles_y;
     float fx, fy, cx, cy;
     float near_, far_;
     float z_clip;        // camera-frame depth below which no ray sample can lie (near * min unit dz)
+    int32_t tile_base;   // first global tile index of this view
+    int64_t pix_base;    // first pixel of this view in the concatenated outputs
+};
+
+// Shared by every kernel of a render call (passed by value).
+struct BatchParams {
+    int32_t n_view, n_oct;
     int32_t K;
     float inv_k;         // 1 / K
     float eps_stop;
     int32_t activation;
-    int32_t n_oct;
     int32_t Lkey;        // BSP key depth (max level over the octrees)
     int32_t oct_shift;   // 3 * Lkey
-    int64_t n_vox_total;
-    OctParams oc[DV_MAX_OCTREES];
+    int32_t view_shift;  // oct_shift + bits(n_oct)
+    int32_t n_tiles;     // over all views
+    int64_t n_vox;       // voxels of one view (all octrees)
+    int64_t vox_offset[DV_MAX_OCTREES + 1];
+    int32_t tile_base[DV_MAX_VIEWS + 1];
+    const ViewParams* views;  // device [n_view]
+    const OctParams* octs;    // device [n_view][n_oct]
 };
 
-static_assert(sizeof(FrameParams) < 31000, "FrameParams must fit the kernel parameter space");
+static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
 
-// 64-byte per-voxel render record, one per visible voxel in depth-sort order.
+// 64-byte per-voxel render record, one per visible (view, voxel) in depth-key order.
 //   v[0] = (min.x, min.y, min.z, size)   local frame
 //   v[1] = dens[0..3]
 //   v[2] = dens[4..7]
-//   v[3] = (r, g, b, bits(local voxel index))
+//   v[3] = (r, g, b, unused)
 struct __align__(16) VoxRec {
     float4 v[4];
 };
@@ -65,20 +76,7 @@ void count_launches(long long n);
 // error flags written by kernels (bitmask in device memory)
 #define DV_FLAG_BAD_LEVEL 1u
 
-// host-side launchers (defined in the .cu files)
 namespace dv {
-
-struct Arena;  // stream-ordered scratch allocations of one call
-
-cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
-                            cudaStream_t s);
-cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, Arena& ar,
-                            cudaStream_t s);
-// LSD radix sort of (key, value) pairs on bits [0, n_bits). Returns the buffers holding the result.
-cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s);
-cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s);
 
 struct Arena {
     cudaMemPool_t pool;
@@ -107,36 +105,46 @@ struct Arena {
     }
 };
 
-}  // namespace dv
+cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
+                            cudaStream_t s);
+cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, Arena& ar,
+                            cudaStream_t s);
+// LSD radix sort of (key, value) pairs on bits [0, n_bits). Returns the buffers holding the result.
+cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int n_bits, Arena& ar, cudaStream_t s);
+cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int n_bits, Arena& ar, cudaStream_t s);
 
-// kernel launchers, one per .cu file
-namespace dv {
-cudaError_t launch_project(const FrameParams& fp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
+// kernel launchers (one thread per (view, voxel) unless stated)
+cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
                            uint32_t* flags, cudaStream_t s);
 cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
                            uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
-cudaError_t launch_records(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
+cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
                            const uint64_t* rect, VoxRec* rec, uint32_t* cnt_sorted, uint64_t* rect_sorted,
                            cudaStream_t s);
-cudaError_t launch_vis_start(const uint64_t* sorted_key, int64_t n_vis, int oct_shift, int n_oct,
-                             uint32_t* vis_start, cudaStream_t s);
-cudaError_t launch_emit(const FrameParams& fp, const uint64_t* off, const uint64_t* rect_sorted, int64_t n_vis,
-                        int64_t n_pairs, uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s);
-cudaError_t launch_pair_mask(const FrameParams& fp, const uint32_t* pair_key, const uint32_t* pair_val,
+// start of every (view, octree) group in depth-key order: vis_start[n_view * n_oct + 1]
+cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, int64_t n_vis, uint32_t* vis_start,
+                             cudaStream_t s);
+cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64_t* rect_sorted,
+                        const uint32_t* sorted_g, int64_t n_vis, int64_t n_pairs, uint32_t* pair_key,
+                        uint32_t* pair_val, cudaStream_t s);
+cudaError_t launch_pair_mask(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
                              const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* pair_key, int64_t n_pairs, uint2* tile_range, int n_tiles, cudaStream_t s);
-cudaError_t launch_composite_fwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
-                                 float* rgb, float* depth, float* alpha, uint32_t* n_seg, float* t_final,
-                                 unsigned long long* work, cudaStream_t s);
-cudaError_t launch_composite_bwd(const FrameParams& fp, const VoxRec* rec, const uint32_t* pair_val,
-                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
-                                 const float* rgb, const float* depth, const uint32_t* n_seg, const float* t_final,
-                                 const float* g_rgb, const float* g_depth, const float* g_alpha, float* grad_rec,
-                                 cudaStream_t s);
 // tiles ordered by decreasing pair-list length (log2 buckets); scratch: 64 words
 cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* scratch64, uint32_t* order,
                               cudaStream_t s);
-cudaError_t launch_sh_bwd(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
+cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
+                                 const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
+                                 float* t_final, unsigned long long* work, cudaStream_t s);
+cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
+                                 const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
+                                 const uint32_t* tile_order, const float* rgb, const float* depth,
+                                 const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
+                                 float* grad_rec, cudaStream_t s);
+cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
                           const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s);
+
 }  // namespace dv

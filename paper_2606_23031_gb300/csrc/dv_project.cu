@@ -1,6 +1,9 @@
 // Per-voxel projection, visibility compaction, render records and tile binning.
 //
-// project  (one thread per voxel of every octree): leaf geometry from its key,
+// All kernels run over every view of a render call at once (a view is one camera
+// of one request, with its own actor poses); tiles are numbered globally.
+//
+// project  (one thread per (view, voxel) of every octree): leaf geometry from its key,
 //          the 8 corners placed in the camera frame by the composed pose
 //          (local -> world -> camera, Sec. 3.2), near/far culling, a conservative
 //          screen rectangle of the box (clipped against the near plane) turned
@@ -20,8 +23,8 @@
 // path with each child bit flipped when o lies on the positive side of that
 // node's plane, so sorting keys ascending yields that order.  The side tests
 // are exact integer comparisons of 2*(o - root_min)/root*2^L against the
-// node-centre lattice coordinates.  The octree index sits above the path bits,
-// so one sort groups each octree's voxels and orders them front to back.
+// node-centre lattice coordinates.  The view and octree indices sit above the
+// path bits, so one sort groups each (view, octree) and orders it front to back.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,11 +36,11 @@ namespace {
 
 constexpr uint64_t M19 = (1ull << 19) - 1;
 
-__device__ __forceinline__ int find_octree(const FrameParams& fp, int64_t g) {
-    int lo = 0, hi = fp.n_oct - 1;
+__device__ __forceinline__ int find_octree(const BatchParams& bp, int64_t g) {
+    int lo = 0, hi = bp.n_oct - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (fp.oc[mid].vox_offset <= g)
+        if (bp.vox_offset[mid] <= g)
             lo = mid;
         else
             hi = mid - 1;
@@ -65,7 +68,7 @@ __device__ __forceinline__ Leaf decode_leaf(const OctParams& P, uint64_t key) {
     return L;
 }
 
-__device__ __forceinline__ void proj_point(const FrameParams& fp, float x, float y, float z, float& u0, float& u1,
+__device__ __forceinline__ void proj_point(const ViewParams& fp, float x, float y, float z, float& u0, float& u1,
                                            float& v0, float& v1) {
     float iz = 1.0f / z;
     float u = fmaf(fp.fx * x, iz, fp.cx);
@@ -76,14 +79,17 @@ __device__ __forceinline__ void proj_point(const FrameParams& fp, float x, float
     v1 = fmaxf(v1, v);
 }
 
-__global__ void __launch_bounds__(256) k_project(const __grid_constant__ FrameParams fp, uint32_t* __restrict__ cnt,
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParams bp, uint32_t* __restrict__ cnt,
                                                  uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
                                                  uint32_t* __restrict__ vis, uint32_t* __restrict__ flags) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= fp.n_vox_total) return;
-    const int o = find_octree(fp, g);
-    const OctParams& P = fp.oc[o];
-    const int64_t v = g - P.vox_offset;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // view * n_vox + voxel
+    if (g >= bp.n_vox * bp.n_view) return;
+    const int view = (int)(g / bp.n_vox);
+    const int64_t gv = g - (int64_t)view * bp.n_vox;
+    const int o = find_octree(bp, gv);
+    const ViewParams& fp = bp.views[view];
+    const OctParams& P = bp.octs[view * bp.n_oct + o];
+    const int64_t v = gv - bp.vox_offset[o];
     const uint64_t key = P.key[v];
     cnt[g] = 0;
     vis[g] = 0;
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ FramePa
     rect[g] = (uint64_t)pu0 | ((uint64_t)pu1 << 16) | ((uint64_t)pv0 << 32) | ((uint64_t)pv1 << 48);
     // depth-order key (see the file comment)
     uint64_t bsp = 0;
-    const int Lk = fp.Lkey;
+    const int Lk = bp.Lkey;
     for (int l = 0; l < L.level; ++l) {
         const int sh = L.level - 1 - l;
         const uint32_t bi = (L.i >> sh) & 1u, bj = (L.j >> sh) & 1u, bk = (L.k >> sh) & 1u;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ FramePa
         bsp = (bsp << 3) | (fi << 2) | (fj << 1) | fk;
     }
     bsp <<= 3 * (Lk - L.level);
-    skey[g] = ((uint64_t)o << fp.oct_shift) | bsp;
+    skey[g] = ((uint64_t)view << bp.view_shift) | ((uint64_t)o << bp.oct_shift) | bsp;
 }
 
 __global__ void k_compact(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ pos,
@@ -204,7 +210,7 @@ __device__ __forceinline__ void sh_eval_basis(int deg, float x, float y, float z
     b[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
 }
 
-__global__ void __launch_bounds__(256) k_records(const __grid_constant__ FrameParams fp,
+__global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchParams bp,
                                                  const uint32_t* __restrict__ sorted_g, int64_t n_vis,
                                                  const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ rect,
                                                  VoxRec* __restrict__ rec, uint32_t* __restrict__ cnt_sorted,
@@ -212,9 +218,11 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ FramePa
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
     const uint32_t g = sorted_g[r];
-    const int o = find_octree(fp, g);
-    const OctParams& P = fp.oc[o];
-    const int64_t v = (int64_t)g - P.vox_offset;
+    const int view = (int)(g / bp.n_vox);
+    const int64_t gv = (int64_t)g - (int64_t)view * bp.n_vox;
+    const int o = find_octree(bp, gv);
+    const OctParams& P = bp.octs[view * bp.n_oct + o];
+    const int64_t v = gv - bp.vox_offset[o];
     const Leaf L = decode_leaf(P, P.key[v]);
     const float4* d4 = reinterpret_cast<const float4*>(P.dens + v * 8);
     const float4 da = __ldg(d4), db = __ldg(d4 + 1);
@@ -241,27 +249,35 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ FramePa
     R.v[0] = make_float4(L.mn[0], L.mn[1], L.mn[2], L.s);
     R.v[1] = da;
     R.v[2] = db;
-    R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), __int_as_float((int)v));
+    R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
     rec[r] = R;
     cnt_sorted[r] = cnt[g];
     rect_sorted[r] = rect[g];
 }
 
-__global__ void k_vis_start(const uint64_t* __restrict__ key, int64_t n_vis, int shift, int n_oct,
+// (view, octree) group of a depth key: view * n_oct + octree
+__device__ __forceinline__ int key_group(const BatchParams& bp, uint64_t k) {
+    const int view = (int)(k >> bp.view_shift);
+    const int o = (int)((k >> bp.oct_shift) & ((1ull << (bp.view_shift - bp.oct_shift)) - 1));
+    return view * bp.n_oct + o;
+}
+
+__global__ void k_vis_start(const __grid_constant__ BatchParams bp, const uint64_t* __restrict__ key, int64_t n_vis,
                             uint32_t* __restrict__ vis_start) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
-    const int o = (int)(key[r] >> shift);
-    const int prev = r > 0 ? (int)(key[r - 1] >> shift) : -1;
-    for (int q = prev + 1; q <= o; ++q) vis_start[q] = (uint32_t)r;
+    const int grp = key_group(bp, key[r]);
+    const int prev = r > 0 ? key_group(bp, key[r - 1]) : -1;
+    for (int q = prev + 1; q <= grp; ++q) vis_start[q] = (uint32_t)r;
     if (r == n_vis - 1)
-        for (int q = o + 1; q <= n_oct; ++q) vis_start[q] = (uint32_t)n_vis;
+        for (int q = grp + 1; q <= bp.n_view * bp.n_oct; ++q) vis_start[q] = (uint32_t)n_vis;
 }
 
 // one thread per (tile, voxel) pair: the pair's voxel is the last record whose first
 // pair offset is <= the pair index (binary search), its tile the matching cell of
 // the voxel's tile rectangle (row-major), so every thread writes exactly one pair
-__global__ void k_emit(int tiles_x, const uint64_t* __restrict__ off, const uint64_t* __restrict__ rect_sorted,
+__global__ void k_emit(const __grid_constant__ BatchParams bp, const uint64_t* __restrict__ off,
+                       const uint64_t* __restrict__ rect_sorted, const uint32_t* __restrict__ sorted_g,
                        int64_t n_vis, int64_t n_pairs, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
@@ -277,18 +293,35 @@ __global__ void k_emit(int tiles_x, const uint64_t* __restrict__ off, const uint
     const uint32_t tx0 = (rc & 0xffff) >> 4, tx1 = ((rc >> 16) & 0xffff) >> 4, ty0 = ((rc >> 32) & 0xffff) >> 4;
     const uint32_t w = tx1 - tx0 + 1;
     const uint32_t k = (uint32_t)((uint64_t)p - __ldg(off + lo));
-    pkey[p] = (ty0 + k / w) * (uint32_t)tiles_x + tx0 + k % w;
+    const int view = (int)(__ldg(sorted_g + lo) / (uint64_t)bp.n_vox);
+    const uint32_t tiles_x = (uint32_t)bp.views[view].tiles_x;
+    pkey[p] = (uint32_t)bp.tile_base[view] + (ty0 + k / w) * tiles_x + tx0 + k % w;
     pval[p] = (uint32_t)lo;
 }
 
 // For every sorted pair: which of the tile's eight 8x4-pixel blocks (bit sy*2+sx for
 // the block at x in [8 sx, 8 sx + 8), y in [4 sy, 4 sy + 4)) the voxel's pixel
 // rectangle touches; a warp rendering a block skips the pairs without its bit.
-__global__ void k_pair_mask(int tiles_x, const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ pval,
-                            const uint64_t* __restrict__ rect_sorted, int64_t n_pairs, uint8_t* __restrict__ mask) {
+__device__ __forceinline__ int view_of_tile(const BatchParams& bp, int t) {
+    int lo = 0, hi = bp.n_view - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bp.tile_base[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32_t* __restrict__ pkey,
+                            const uint32_t* __restrict__ pval, const uint64_t* __restrict__ rect_sorted,
+                            int64_t n_pairs, uint8_t* __restrict__ mask) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
-    const uint32_t t = pkey[p];
+    const int view = view_of_tile(bp, (int)pkey[p]);
+    const uint32_t t = pkey[p] - (uint32_t)bp.tile_base[view];
+    const uint32_t tiles_x = (uint32_t)bp.views[view].tiles_x;
     const uint64_t rc = __ldg(rect_sorted + pval[p]);
     const int x0 = (int)(t % (uint32_t)tiles_x) * DV_TILE, y0 = (int)(t / (uint32_t)tiles_x) * DV_TILE;
     const int u0 = (int)(rc & 0xffff) - x0, u1 = (int)((rc >> 16) & 0xffff) - x0;
@@ -369,10 +402,11 @@ cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* sc
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const FrameParams& fp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
+cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
                            uint32_t* flags, cudaStream_t s) {
-    if (fp.n_vox_total <= 0) return cudaSuccess;
-    k_project<<<nblk(fp.n_vox_total, 256), 256, 0, s>>>(fp, cnt, rect, skey, vis, flags);
+    const int64_t n = bp.n_vox * bp.n_view;
+    if (n <= 0) return cudaSuccess;
+    k_project<<<nblk(n, 256), 256, 0, s>>>(bp, cnt, rect, skey, vis, flags);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -385,35 +419,36 @@ cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint6
     return cudaGetLastError();
 }
 
-cudaError_t launch_records(const FrameParams& fp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
+cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
                            const uint64_t* rect, VoxRec* rec, uint32_t* cnt_sorted, uint64_t* rect_sorted,
                            cudaStream_t s) {
     if (n_vis <= 0) return cudaSuccess;
-    k_records<<<nblk(n_vis, 256), 256, 0, s>>>(fp, sorted_g, n_vis, cnt, rect, rec, cnt_sorted, rect_sorted);
+    k_records<<<nblk(n_vis, 256), 256, 0, s>>>(bp, sorted_g, n_vis, cnt, rect, rec, cnt_sorted, rect_sorted);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_vis_start(const uint64_t* sorted_key, int64_t n_vis, int oct_shift, int n_oct,
-                             uint32_t* vis_start, cudaStream_t s) {
-    if (n_vis <= 0) return cudaMemsetAsync(vis_start, 0, sizeof(uint32_t) * (n_oct + 1), s);
-    k_vis_start<<<nblk(n_vis, 256), 256, 0, s>>>(sorted_key, n_vis, oct_shift, n_oct, vis_start);
+cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, int64_t n_vis, uint32_t* vis_start,
+                             cudaStream_t s) {
+    if (n_vis <= 0) return cudaMemsetAsync(vis_start, 0, sizeof(uint32_t) * (bp.n_view * bp.n_oct + 1), s);
+    k_vis_start<<<nblk(n_vis, 256), 256, 0, s>>>(bp, sorted_key, n_vis, vis_start);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const FrameParams& fp, const uint64_t* off, const uint64_t* rect_sorted, int64_t n_vis,
-                        int64_t n_pairs, uint32_t* pair_key, uint32_t* pair_val, cudaStream_t s) {
+cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64_t* rect_sorted,
+                        const uint32_t* sorted_g, int64_t n_vis, int64_t n_pairs, uint32_t* pair_key,
+                        uint32_t* pair_val, cudaStream_t s) {
     if (n_vis <= 0 || n_pairs <= 0) return cudaSuccess;
-    k_emit<<<nblk(n_pairs, 256), 256, 0, s>>>(fp.tiles_x, off, rect_sorted, n_vis, n_pairs, pair_key, pair_val);
+    k_emit<<<nblk(n_pairs, 256), 256, 0, s>>>(bp, off, rect_sorted, sorted_g, n_vis, n_pairs, pair_key, pair_val);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_mask(const FrameParams& fp, const uint32_t* pair_key, const uint32_t* pair_val,
+cudaError_t launch_pair_mask(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
                              const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, cudaStream_t s) {
     if (n_pairs <= 0) return cudaSuccess;
-    k_pair_mask<<<nblk(n_pairs, 256), 256, 0, s>>>(fp.tiles_x, pair_key, pair_val, rect_sorted, n_pairs, mask);
+    k_pair_mask<<<nblk(n_pairs, 256), 256, 0, s>>>(bp, pair_key, pair_val, rect_sorted, n_pairs, mask);
     count_launches(1);
     return cudaGetLastError();
 }
