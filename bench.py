@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate and path")
+    p.add_argument("--serve-rates", default="200,500,1000,2000")
     return p.parse_args()
 
 
@@ -234,6 +237,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
     return 0
 
+
+
+# ---------------------------------------------------------------------------
+# serving: continuous batching vs one request per launch (cfg 4 workload)
+# ---------------------------------------------------------------------------
+
+SERVE_WORKLOAD = ("config-2 background (500k leaves) + 20 actors x 20k leaves resident; Poisson requests, camera at "
+                  "u ~ U(0,1) on a 100 m straight track, timestamp ~ U(0,10) s setting all 20 actor poses, "
+                  "resolution uniform over {480x270, 960x540, 1920x1080}")
+
+
+def serve_once(dv, ds, scene, reqs, mode, opts):
+    import numpy as np
+    import torch
+    import synth
+    if mode == "plain":
+        cfg = dict(max_views=1, n_workers=1)
+    else:
+        cfg = dict(max_views=16, n_workers=2)
+    srv = dv.Server(ds, max_batch_pixels=16 * 1920 * 1080, max_inflight_pixels=24 * 1920 * 1080, opts=opts, **cfg)
+    pools = {}
+    users = {}
+
+    def out_for(cam, k):
+        key = (cam.W, cam.H)
+        pool = pools.setdefault(key, [])
+        slot = k % 48
+        while len(pool) <= slot:
+            n = cam.W * cam.H
+            pool.append((torch.empty((n, 3), device="cuda"), torch.empty((n,), device="cuda"),
+                         torch.empty((n,), device="cuda")))
+        prev = users.get((key, slot))
+        if prev is not None:
+            srv.wait(prev, 600000.0)          # the buffer's previous request must be done
+        return pool[slot], (key, slot)
+
+    # warm-up (contexts, pools, first launches)
+    warm = [srv.submit(c.camera, synth.request_poses(scene, c.t), out_for(c.camera, i)[0])
+            for i, c in enumerate(reqs[:8])]
+    for t in warm:
+        srv.wait(t, 600000.0)
+        srv.release(t)
+    users.clear()
+    tickets, lags, pixels = [], [], 0
+    t0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        buf, key = out_for(r.camera, k)
+        lag = time.perf_counter() - t0 - r.arrival_s
+        t = srv.submit(r.camera, synth.request_poses(scene, r.t), buf)
+        users[key] = t
+        tickets.append(t)
+        lags.append(lag)
+        pixels += r.camera.W * r.camera.H
+    lat = []
+    for t, lag in zip(tickets, lags):
+        lat.append(srv.wait(t, 600000.0) + 1e3 * lag)
+    t_end = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "mpix_s": pixels / t_end / 1e6, "requests": len(reqs),
+            "batches": st["batches"], "max_batch": st["max_batch"]}
+
+
+def serving_bench(args, dv, opts):
+    import synth
+    scene = synth.config4(args.seed)
+    ds = [dv.DeviceOctree.from_host(o) for o in scene.octrees]
+    rows = []
+    for rate in [float(x) for x in args.serve_rates.split(",") if x]:
+        n = max(16, int(rate * args.serve_seconds))
+        reqs = synth.request_stream(n, rate, args.seed + int(rate))
+        row = {"rate_hz": rate}
+        for mode in ("plain", "batched"):
+            row[mode] = serve_once(dv, ds, scene, reqs, mode, opts)
+        rows.append(row)
+        log("serving", rate, row)
+    return {"workload": SERVE_WORKLOAD, "plain": "max_views=1, 1 worker (one request per launch)",
+            "batched": "max_views=16, 2 workers, continuous batching", "latency": "arrival -> outputs written",
+            "rates": rows}
 
 # ---------------------------------------------------------------------------
 # our arm
@@ -414,6 +501,10 @@ def run_ours(args):
                 "frac": d["frac"], "traffic": load_traffic(dom), "kernel": dom,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_bench(args, dv, opts)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, cam, args.cpu_seconds, args.seed)
@@ -427,6 +518,7 @@ def run_ours(args):
                            "visible_voxels": stats["n_visible"], "pairs": stats["n_pairs"]},
                 "fwd": {"value": value_fwd, "unit": "Mpix/s", "ms_per_step": ms_fwd},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "serving": serving,
                 "gpu_launches_per_step": launches / max(args.steps, 1), "wall_s_timed": wall,
                 "work": work, "kernels": kernels}
         print(json.dumps(line), flush=True)

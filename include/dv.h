@@ -215,6 +215,49 @@ dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* state, const float* d
 dv_status dv_profile_enable(dv_ctx* ctx, int32_t on);
 dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, double* ms, int64_t* launches);
 
+/* ------------------------------------------------------------------------
+ * Serving loop: continuous batching of render requests (no counterpart in the
+ * paper; it keeps the scene resident and renders requests as they arrive).
+ *
+ * A request is a camera plus the pose of every octree at the request's
+ * timestamp, with caller-owned device output buffers (rgb [H*W][3], depth and
+ * alpha [H*W]) that must stay valid until the request is done.  Worker threads,
+ * each with its own CUDA stream, take the queued requests in arrival order up
+ * to the admission limits below and render each group as one batch of views
+ * (dv_render_views); requests arriving meanwhile join the next batch a worker
+ * forms, and the batches of different workers overlap on the GPU.  Results are
+ * identical to rendering each request alone.
+ * ------------------------------------------------------------------------ */
+typedef struct dv_server dv_server;
+
+typedef struct {
+    int32_t max_views;           /* requests per batch, 1..DV_MAX_VIEWS (1 = one request per launch) */
+    int32_t n_workers;           /* batches in flight at once, each on its own stream, 1..8 */
+    int64_t max_batch_pixels;    /* pixels per batch (a larger single request still runs, alone) */
+    int64_t max_inflight_pixels; /* pixels rendering at once over all workers: the device-memory budget */
+    dv_opts opts;
+} dv_serve_config;
+
+/* Starts a server on `device` over the octrees oct[n_oct] (device buffers
+ * borrowed for the server's lifetime; the dv_octree structs are copied). */
+dv_status dv_serve_create(dv_server** srv, int32_t device, const dv_octree* oct, int32_t n_oct,
+                          const dv_serve_config* cfg);
+/* Queues one request (poses: host array [n_oct], copied); returns its ticket. */
+dv_status dv_serve_submit(dv_server* srv, const dv_camera* cam, const dv_pose* poses, float* rgb, float* depth,
+                          float* alpha, int64_t* ticket);
+/* Non-blocking: *done = 1 once the outputs are written; then *latency_ms is the
+ * time from submit to completion and the return value the request's status. */
+dv_status dv_serve_poll(dv_server* srv, int64_t ticket, int32_t* done, double* latency_ms);
+/* Waits at most timeout_ms for the request; DV_ERR_TIMEOUT if it is not done. */
+dv_status dv_serve_wait(dv_server* srv, int64_t ticket, double timeout_ms, double* latency_ms);
+/* Forgets a finished request (its ticket becomes invalid). */
+dv_status dv_serve_release(dv_server* srv, int64_t ticket);
+/* Batches run, requests rendered, largest batch so far. */
+dv_status dv_serve_stats(dv_server* srv, int64_t* batches, int64_t* views, int64_t* max_batch);
+const char* dv_serve_last_error(const dv_server* srv);
+/* Finishes every queued request, stops the workers and frees the server. */
+void dv_serve_destroy(dv_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

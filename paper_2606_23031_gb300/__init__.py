@@ -23,7 +23,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libdv.so")
-SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu"]
+SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV_ERR_TIMEOUT, DV_ERR_NOMEM = range(7)
@@ -101,6 +101,11 @@ class dv_opts(C.Structure):
     _fields_ = [("K", C.c_int32), ("eps_stop", C.c_float), ("activation", C.c_int32), ("reserved", C.c_int32)]
 
 
+class dv_serve_config(C.Structure):
+    _fields_ = [("max_views", C.c_int32), ("n_workers", C.c_int32), ("max_batch_pixels", C.c_int64),
+                ("max_inflight_pixels", C.c_int64), ("opts", dv_opts)]
+
+
 _lib = None
 
 
@@ -144,6 +149,24 @@ def load(path: str | None = None):
     lib.dv_state_work.restype = C.c_int
     lib.dv_launch_count.argtypes = [C.c_int32]
     lib.dv_launch_count.restype = C.c_longlong
+    lib.dv_serve_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(dv_octree), C.c_int32,
+                                    C.POINTER(dv_serve_config)]
+    lib.dv_serve_create.restype = C.c_int
+    lib.dv_serve_submit.argtypes = [C.c_void_p, C.POINTER(dv_camera), C.POINTER(dv_pose), C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_int64)]
+    lib.dv_serve_submit.restype = C.c_int
+    lib.dv_serve_poll.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    lib.dv_serve_poll.restype = C.c_int
+    lib.dv_serve_wait.argtypes = [C.c_void_p, C.c_int64, C.c_double, C.POINTER(C.c_double)]
+    lib.dv_serve_wait.restype = C.c_int
+    lib.dv_serve_release.argtypes = [C.c_void_p, C.c_int64]
+    lib.dv_serve_release.restype = C.c_int
+    lib.dv_serve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.dv_serve_stats.restype = C.c_int
+    lib.dv_serve_last_error.argtypes = [C.c_void_p]
+    lib.dv_serve_last_error.restype = C.c_char_p
+    lib.dv_serve_destroy.argtypes = [C.c_void_p]
+    lib.dv_serve_destroy.restype = None
     lib.dv_profile_enable.argtypes = [C.c_void_p, C.c_int32]
     lib.dv_profile_enable.restype = C.c_int
     lib.dv_profile_read.argtypes = [C.c_void_p, C.POINTER(C.c_char_p), C.c_int32, C.POINTER(C.c_double),
@@ -498,3 +521,75 @@ def dv_render_backward_static(state: State, d_rgb=None, d_depth=None, d_alpha=No
     ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
     status = fn(state.ctx.handle, state.handle, ptr(d_rgb), ptr(d_depth), ptr(d_alpha), pd, ps, _stream_ptr(stream))
     state.ctx.check(status)
+
+
+class Server:
+    """Continuous-batching render server over resident octrees (``dv_serve_*``).
+
+    ``submit`` queues a request (camera, per-octree poses, device output tensors) and returns a
+    ticket; ``wait`` blocks at most ``timeout_ms``; results are written into the given tensors."""
+
+    def __init__(self, octrees, max_views=16, n_workers=2, max_batch_pixels=8 * 1920 * 1080,
+                 max_inflight_pixels=16 * 1920 * 1080, opts=None, device=None):
+        import torch
+        lib = load()
+        self.octrees = octrees  # keep the device buffers alive
+        self.n_oct = len(octrees)
+        arr = (dv_octree * self.n_oct)(*[o.struct() for o in octrees])
+        cfg = dv_serve_config()
+        cfg.max_views, cfg.n_workers = int(max_views), int(n_workers)
+        cfg.max_batch_pixels, cfg.max_inflight_pixels = int(max_batch_pixels), int(max_inflight_pixels)
+        cfg.opts = opts or make_opts()
+        h = C.c_void_p()
+        dev = torch.cuda.current_device() if device is None else device
+        st = lib.dv_serve_create(C.byref(h), int(dev), arr, self.n_oct, C.byref(cfg))
+        if st != DV_OK:
+            raise DVError(st, "dv_serve_create failed")
+        self.handle = h
+        self.keep = {}
+
+    def _check(self, st):
+        if st != DV_OK:
+            raise DVError(st, load().dv_serve_last_error(self.handle).decode())
+
+    def submit(self, cam, poses, out):
+        rgb, depth, alpha = out
+        c = make_camera(cam)
+        pa = (dv_pose * self.n_oct)(*[make_pose(p) for p in poses])
+        t = C.c_int64()
+        self._check(load().dv_serve_submit(self.handle, C.byref(c), pa, C.c_void_p(rgb.data_ptr()),
+                                           C.c_void_p(depth.data_ptr()), C.c_void_p(alpha.data_ptr()), C.byref(t)))
+        self.keep[t.value] = out
+        return t.value
+
+    def poll(self, ticket):
+        d = C.c_int32()
+        lat = C.c_double()
+        self._check(load().dv_serve_poll(self.handle, int(ticket), C.byref(d), C.byref(lat)))
+        return (lat.value if d.value else None)
+
+    def wait(self, ticket, timeout_ms=60000.0):
+        lat = C.c_double()
+        self._check(load().dv_serve_wait(self.handle, int(ticket), float(timeout_ms), C.byref(lat)))
+        return lat.value
+
+    def release(self, ticket):
+        self._check(load().dv_serve_release(self.handle, int(ticket)))
+        self.keep.pop(ticket, None)
+
+    def stats(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(load().dv_serve_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)))
+        return {"batches": a.value, "requests": b.value, "max_batch": c.value}
+
+    def close(self):
+        if self.handle:
+            load().dv_serve_destroy(self.handle)
+            self.handle = None
+            self.keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

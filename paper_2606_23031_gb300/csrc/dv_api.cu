@@ -69,8 +69,6 @@ struct BatchState {
     uint32_t* n_seg = nullptr;
     float* t_final = nullptr;
     unsigned long long* work = nullptr;  // [tests, box tests, segments] of the forward
-    float* rgb = nullptr;
-    float* depth = nullptr;
 };
 
 }  // namespace
@@ -388,8 +386,8 @@ T* pool_alloc(dv_ctx* ctx, cudaStream_t s, size_t count, std::vector<void*>& own
 // The forward of one render call over all its views.  State buffers go to `st`
 // (freed by the caller when no state is wanted).
 dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pose* const* view_poses,
-                       const dv_camera* cams, int n_view, const dv_opts& opt, dv_state* st, float* rgb, float* depth,
-                       float* alpha, cudaStream_t s) {
+                       const dv_camera* cams, int n_view, const dv_opts& opt, dv_state* st, float* const* rgbs,
+                       float* const* depths, float* const* alphas, cudaStream_t s) {
     using namespace dv;
     BatchState& B = st->b;
     BatchParams& bp = B.bp;
@@ -420,6 +418,9 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         make_view(oct, n_oct, view_poses[v], cams[v], Lkey, B.h_views[v], &h_octs[(size_t)v * n_oct]);
         B.h_views[v].tile_base = (int32_t)tiles;
         B.h_views[v].pix_base = pix;
+        B.h_views[v].rgb = rgbs[v];
+        B.h_views[v].depth = depths[v];
+        B.h_views[v].alpha = alphas[v];
         bp.tile_base[v] = (int32_t)tiles;
         tiles += (int64_t)B.h_views[v].tiles_x * B.h_views[v].tiles_y;
         pix += (int64_t)cams[v].W * cams[v].H;
@@ -428,8 +429,6 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     if (tiles >= ((int64_t)1 << 31)) return fail(ctx, DV_ERR_CAPACITY, "too many tiles in one call");
     bp.n_tiles = (int32_t)tiles;
     B.n_pix = pix;
-    B.rgb = rgb;
-    B.depth = depth;
     cudaError_t e = cudaSuccess;
     std::vector<void*>& own = st->owned;
     B.d_views = pool_alloc<ViewParams>(ctx, s, (size_t)n_view, own, e);
@@ -569,8 +568,8 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     {
         Prof p(ctx, KP_FWD, s);
         if (e == cudaSuccess)
-            e = launch_composite_fwd(bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, rgb, depth,
-                                     alpha, B.n_seg, B.t_final, B.work, s);
+            e = launch_composite_fwd(bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, nullptr,
+                                     nullptr, nullptr, B.n_seg, B.t_final, B.work, s);
     }
     ar.release();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render");
@@ -584,8 +583,8 @@ dv_status backward_batch(dv_ctx* ctx, dv_state* st, const float* d_rgb, const fl
     {
         Prof p(ctx, KP_BWD, s);
         if (e == cudaSuccess)
-            e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, B.rgb,
-                                         B.depth, B.t_final, d_rgb, d_depth, d_alpha, grad, s);
+            e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, nullptr,
+                                         nullptr, B.t_final, d_rgb, d_depth, d_alpha, grad, s);
     }
     {
         Prof p(ctx, KP_SHBWD, s);
@@ -660,7 +659,8 @@ const char* dv_last_error(const dv_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* const* view_poses,
                                const dv_camera* cams, int32_t n_view, const dv_opts* opts, float* rgb, float* depth,
-                               float* alpha, dv_state** saved, void* stream) {
+                               float* alpha, float* const* rgbs, float* const* depths, float* const* alphas,
+                               dv_state** saved, void* stream) {
     if (!ctx) return DV_ERR_INVALID_ARG;
     ctx->err.clear();
     if (saved) *saved = nullptr;
@@ -678,7 +678,24 @@ static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct,
     for (int i = 0; i < n_oct; ++i) Lkey = std::max(Lkey, (int)oct[i].max_level);
     if (3 * Lkey + bits_for(n_oct) + bits_for(n_view) > 64)
         return fail(ctx, DV_ERR_CAPACITY, "depth key does not fit 64 bits");
-    if (total_pix > 0 && (!rgb || !depth || !alpha)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL output buffer");
+    // per-view output pointers: given, or carved from the concatenated buffers
+    std::vector<float*> vr((size_t)std::max(n_view, 1)), vd(vr.size()), va(vr.size());
+    int64_t pb = 0;
+    for (int v = 0; v < n_view; ++v) {
+        const int64_t n = (int64_t)cams[v].W * cams[v].H;
+        if (rgbs) {
+            vr[v] = rgbs[v];
+            vd[v] = depths ? depths[v] : nullptr;
+            va[v] = alphas ? alphas[v] : nullptr;
+        } else {
+            vr[v] = rgb ? rgb + pb * 3 : nullptr;
+            vd[v] = depth ? depth + pb : nullptr;
+            va[v] = alpha ? alpha + pb : nullptr;
+        }
+        if (n > 0 && (!vr[v] || !vd[v] || !va[v])) return fail(ctx, DV_ERR_INVALID_ARG, "NULL output buffer");
+        pb += n;
+    }
+    (void)total_pix;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     std::unique_ptr<dv_state> st(new (std::nothrow) dv_state());
@@ -686,7 +703,8 @@ static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct,
     st->ctx = ctx;
     st->stream = s;
     if (n_view > 0) {
-        dv_status rs = render_batch(ctx, oct, n_oct, view_poses, cams, n_view, *opts, st.get(), rgb, depth, alpha, s);
+        dv_status rs = render_batch(ctx, oct, n_oct, view_poses, cams, n_view, *opts, st.get(), vr.data(), vd.data(),
+                                    va.data(), s);
         if (rs != DV_OK) {
             free_state(st.release());
             return rs;
@@ -707,7 +725,8 @@ dv_status dv_render(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_p
         return n_cam < 0 ? DV_ERR_INVALID_ARG : DV_ERR_CAPACITY;
     }
     std::vector<const dv_pose*> vp((size_t)std::max(n_cam, 1), poses);
-    return render_common(ctx, oct, n_oct, vp.data(), cams, n_cam, opts, rgb, depth, alpha, saved, stream);
+    return render_common(ctx, oct, n_oct, vp.data(), cams, n_cam, opts, rgb, depth, alpha, nullptr, nullptr, nullptr,
+                         saved, stream);
 }
 
 dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_view* views, int32_t n_view,
@@ -723,7 +742,8 @@ dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, cons
         vp[v] = views[v].poses;
         cams[v] = views[v].camera;
     }
-    return render_common(ctx, oct, n_oct, vp.data(), cams.data(), n_view, opts, rgb, depth, alpha, saved, stream);
+    return render_common(ctx, oct, n_oct, vp.data(), cams.data(), n_view, opts, rgb, depth, alpha, nullptr, nullptr,
+                         nullptr, saved, stream);
 }
 
 dv_status dv_render_backward(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
@@ -835,6 +855,22 @@ dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, doub
 }
 
 }  // extern "C"
+
+namespace dv {
+// Render of views whose outputs live in separate buffers (used by the serving loop).
+dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
+                            const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,
+                            void* stream) {
+    std::vector<const dv_pose*> vp((size_t)std::max(n_view, 1), nullptr);
+    std::vector<dv_camera> cams((size_t)std::max(n_view, 1));
+    for (int v = 0; v < n_view; ++v) {
+        vp[v] = views[v].poses;
+        cams[v] = views[v].camera;
+    }
+    return render_common(ctx, oct, n_oct, vp.data(), cams.data(), n_view, opts, nullptr, nullptr, nullptr, rgbs, depths,
+                         alphas, nullptr, stream);
+}
+}  // namespace dv
 
 // ---------------------------------------------------------------------------
 // Backward without any allocation.

@@ -450,7 +450,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
     const int u = tx * DV_TILE + (warp & 1) * 8 + (lane & 7);
     const int v = ty * DV_TILE + half * 8 + (warp >> 1) * 4 + (lane >> 3);
     const bool valid = u < W && v < H;
-    const int64_t pix = fp.pix_base + (int64_t)v * W + u;
+    const int64_t lpix = (int64_t)v * W + u;       // pixel within the view's own images
+    const int64_t pix = fp.pix_base + lpix;        // pixel within the call's per-pixel arrays
 
     float dc[3];
     {
@@ -483,10 +484,10 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
         bw.g2 = g_rgb ? g_rgb[pix * 3 + 2] : 0.0f;
         bw.gD = g_depth ? g_depth[pix] : 0.0f;
         bw.gA = g_alpha ? g_alpha[pix] : 0.0f;
-        bw.Cf0 = out_rgb[pix * 3 + 0];
-        bw.Cf1 = out_rgb[pix * 3 + 1];
-        bw.Cf2 = out_rgb[pix * 3 + 2];
-        bw.Df = out_depth[pix];
+        bw.Cf0 = fp.rgb[lpix * 3 + 0];
+        bw.Cf1 = fp.rgb[lpix * 3 + 1];
+        bw.Cf2 = fp.rgb[lpix * 3 + 2];
+        bw.Df = fp.depth[lpix];
         bw.Tend = t_final[pix];
     } else {
         bw.g0 = bw.g1 = bw.g2 = bw.gD = bw.gA = 0.0f;
@@ -722,11 +723,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __g
         }
     }
     if (!BWD && valid) {
-        out_rgb[pix * 3 + 0] = ps.C0;
-        out_rgb[pix * 3 + 1] = ps.C1;
-        out_rgb[pix * 3 + 2] = ps.C2;
-        out_depth[pix] = ps.D;
-        out_alpha[pix] = 1.0f - ps.T;
+        fp.rgb[lpix * 3 + 0] = ps.C0;
+        fp.rgb[lpix * 3 + 1] = ps.C1;
+        fp.rgb[lpix * 3 + 2] = ps.C2;
+        fp.depth[lpix] = ps.D;
+        fp.alpha[lpix] = 1.0f - ps.T;
         n_seg[pix] = ps.n;
         t_final[pix] = ps.T;
     }

@@ -36,7 +36,10 @@ struct ViewParams {
     float near_, far_;
     float z_clip;        // camera-frame depth below which no ray sample can lie (near * min unit dz)
     int32_t tile_base;   // first global tile index of this view
-    int64_t pix_base;    // first pixel of this view in the concatenated outputs
+    int64_t pix_base;    // first pixel of this view in the call's per-pixel arrays (upstream gradients, state)
+    float* rgb;          // this view's outputs [H*W][3], [H*W], [H*W] (device)
+    float* depth;
+    float* alpha;
 };
 
 // Shared by every kernel of a render call (passed by value).
@@ -146,5 +149,10 @@ cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const
                                  float* grad_rec, cudaStream_t s);
 cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
                           const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s);
+
+// render of views whose outputs live in separate device buffers (serving loop)
+dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
+                            const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,
+                            void* stream);
 
 }  // namespace dv

@@ -537,6 +537,12 @@ def config3(seed: int = 0):
     return sc, cams
 
 
+def config4(seed: int = 0):
+    """Serving scene: the config-2 background with 20 actors of 20k leaves on straight lanes (their
+    poses follow the request timestamp)."""
+    return street_scene(500_000, [20_000] * 20, seed)
+
+
 def config5(seed: int = 0):
     """Stress: 32M-leaf background (levels 6-16, 500 x 500 x 40 m), 64 actors of 40k leaves,
     6 cameras at 3840x2160."""
@@ -563,7 +569,7 @@ class Request:
 
 def request_stream(n: int, rate_hz: float, seed: int, resolutions=RESOLUTIONS, track_len=100.0):
     """Poisson arrivals; camera at u ~ U(0,1) along a 100 m straight trajectory (x axis),
-    timestamp ~ U(0, 10) s, resolution uniform over ``resolutions``."""
+    timestamp ~ U(0, 10) s (it sets every actor pose), resolution uniform over ``resolutions``."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_hz, n)
     arr = np.cumsum(gaps)
@@ -574,3 +580,8 @@ def request_stream(n: int, rate_hz: float, seed: int, resolutions=RESOLUTIONS, t
         cam = vehicle_camera(W, H, 60.0, 0.0, position=(-50.0 + track_len * u, 0.0, 1.8))
         out.append(Request(r, float(arr[r]), cam, float(rng.uniform(0.0, 10.0))))
     return out
+
+
+def request_poses(scene, t: float):
+    """Octree poses at timestamp t: background fixed, every actor on its lane."""
+    return [scene.poses[0]] + [tr.pose(t) for tr in scene.tracks]

@@ -107,3 +107,43 @@ def test_config2_sampled_pixel_gradients(dv, config2_scene):
     g_d[pix] = rng.normal(size=pix.size) * 0.01
     g_a[pix] = rng.normal(size=pix.size)
     _compare(sc, cams, g_rgb, g_d, g_a, 1, 1e-4, what="cfg2 sampled", pixels=pix)
+
+
+def test_batched_views_backward(dv):
+    """Backward of a batched call over views with different poses == the sum of the oracle's
+    gradients of every view."""
+    import torch
+    import paper_2606_23031_gb300 as m
+    sc = small_comp_scene(seed=13, n_actors=2)
+    rng = np.random.default_rng(13)
+    views = []
+    for k in range(3):
+        poses = [sc.poses[0]] + [synth.Pose(synth.random_rotation(rng), rng.uniform(-0.6, 0.6, 3))
+                                 for _ in sc.poses[1:]]
+        views.append((orbit(30 + 7 * k, 26, 50.0 + 90 * k, 15.0), poses))
+    ds = device_scene(sc)
+    rgb, depth, alpha, st = m.dv_render_views(ds, views, m.make_opts(1, 1e-4), save_state=True)
+    P = rgb.shape[0]
+    g = [rng.normal(size=(P, 3)), rng.normal(size=P) * 0.1, rng.normal(size=P)]
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+    d_dens = [torch.zeros_like(o.dens) for o in ds]
+    d_sh = [torch.zeros_like(o.sh) for o in ds]
+    m.dv_render_backward(st, t(g[0]), t(g[1]), t(g[2]), d_dens, d_sh)
+    torch.cuda.synchronize()
+    st.free()
+    ref_d = [np.zeros(o.dens.shape) for o in sc.octrees]
+    ref_s = [np.zeros(o.sh.shape) for o in sc.octrees]
+    off = 0
+    for cam, poses in views:
+        n = cam.W * cam.H
+        sl = slice(off, off + n)
+        od, os_ = oracle.backward(sc.octrees, poses, cam, np.float64(np.float32(g[0][sl])),
+                                  np.float64(np.float32(g[1][sl])), np.float64(np.float32(g[2][sl])),
+                                  oracle.Opts(1, 1e-4))
+        for i in range(len(ref_d)):
+            ref_d[i] += od[i]
+            ref_s[i] += os_[i]
+        off += n
+    for i in range(len(ds)):
+        check_grad(d_dens[i].cpu().numpy(), ref_d[i], f"batched d_dens[{i}]")
+        check_grad(d_sh[i].cpu().numpy(), ref_s[i], f"batched d_sh[{i}]")

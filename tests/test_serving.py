@@ -1,0 +1,82 @@
+"""Serving loop (continuous batching): results in the mix equal results alone, batches really form,
+waits are bounded, and the memory budget admits requests without losing any."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import check_forward, device_scene, small_comp_scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(sc, n, seed, sizes=((48, 27), (96, 54), (64, 64), (31, 17))):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W, H = sizes[int(rng.integers(0, len(sizes)))]
+        cam = synth.orbit_camera(W, H, 55.0, 2.8, float(rng.uniform(0, 360)), float(rng.uniform(-10, 40)), near=0.1,
+                                 far=50.0)
+        poses = [sc.poses[0]] + [synth.Pose(synth.random_rotation(rng), rng.uniform(-0.7, 0.7, 3))
+                                 for _ in sc.poses[1:]]
+        out.append((cam, poses))
+    return out
+
+
+def _outputs(cam):
+    import torch
+    n = cam.W * cam.H
+    return (torch.empty((n, 3), device="cuda"), torch.empty((n,), device="cuda"), torch.empty((n,), device="cuda"))
+
+
+def test_results_in_the_mix_equal_results_alone(dv):
+    import torch
+    sc = small_comp_scene(seed=30, n_actors=3)
+    ds = device_scene(sc)
+    reqs = _requests(sc, 40, seed=1)
+    opts = dv.make_opts(1, 1e-4)
+    srv = dv.Server(ds, max_views=8, n_workers=2, max_batch_pixels=10 ** 7, max_inflight_pixels=10 ** 8, opts=opts)
+    outs, tickets = [], []
+    for cam, poses in reqs:
+        o = _outputs(cam)
+        outs.append(o)
+        tickets.append(srv.submit(cam, poses, o))
+    lat = [srv.wait(t, 60000.0) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["requests"] == len(reqs)
+    assert st["batches"] < len(reqs), st          # requests were batched
+    assert st["max_batch"] > 1
+    assert all(x >= 0 for x in lat)
+    for (cam, poses), (rgb, depth, alpha) in zip(reqs, outs):
+        r1, d1, a1, _ = dv.dv_render_views(ds, [(cam, poses)], opts)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(rgb.cpu().numpy(), r1.cpu().numpy())
+        np.testing.assert_array_equal(depth.cpu().numpy(), d1.cpu().numpy())
+        np.testing.assert_array_equal(alpha.cpu().numpy(), a1.cpu().numpy())
+    # and one request of the mix against the oracle
+    cam, poses = reqs[3]
+    o = oracle.render(sc.octrees, poses, cam, oracle.Opts(1, 1e-4))
+    rgb, depth, alpha = outs[3]
+    check_forward(rgb.cpu().numpy().reshape(cam.H, cam.W, 3), depth.cpu().numpy().reshape(cam.H, cam.W),
+                  alpha.cpu().numpy().reshape(cam.H, cam.W), o[0], o[1], o[2], "served request")
+
+
+def test_bounded_wait_times_out_and_budget_admits_everything(dv):
+    sc = small_comp_scene(seed=31, n_actors=2)
+    ds = device_scene(sc)
+    reqs = _requests(sc, 12, seed=2)
+    # a budget smaller than one request: requests then run one at a time, none is lost
+    srv = dv.Server(ds, max_views=4, n_workers=2, max_batch_pixels=10 ** 6, max_inflight_pixels=100,
+                    opts=dv.make_opts(1, 1e-4))
+    tickets = [srv.submit(cam, poses, _outputs(cam)) for cam, poses in reqs]
+    with pytest.raises(dv.DVError) as ei:
+        srv.wait(tickets[-1], 0.0)                 # nothing is done in zero time
+    assert ei.value.status == dv.DV_ERR_TIMEOUT
+    for t in tickets:
+        srv.wait(t, 60000.0)
+        srv.release(t)
+    st = srv.stats()
+    srv.close()
+    assert st["requests"] == len(reqs)
+    assert st["max_batch"] == 1
