@@ -71,6 +71,21 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(values, world, device="cpu"):
+    """Per-rank timings -> their maximum over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_mpix_s(world, pixels_per_rank, ms_per_step):
+    """Weak scaling: every rank renders its own frame; the job processes world x pixels per step."""
+    return world * pixels_per_rank / (ms_per_step * 1e-3) / 1e6
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -417,12 +432,9 @@ def run_ours(args):
         ms_f += a.elapsed_time(b)
     sync_all()
 
-    t_step = torch.tensor([ms / args.steps, ms_f / args.steps], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
-    ms_step, ms_fwd = float(t_step[0]), float(t_step[1])
-    value = world * n_pix / (ms_step * 1e-3) / 1e6
-    value_fwd = world * n_pix / (ms_fwd * 1e-3) / 1e6
+    ms_step, ms_fwd = max_over_ranks([ms / args.steps, ms_f / args.steps], world, dev)
+    value = whole_job_mpix_s(world, n_pix, ms_step)
+    value_fwd = whole_job_mpix_s(world, n_pix, ms_fwd)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -460,11 +472,9 @@ def run_ours(args):
             b.synchronize()
             ms_e += a.elapsed_time(b)
             st.free()
-        t_e = torch.tensor([ms_e / args.steps], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * n_pix / (float(t_e[0]) * 1e-3) / 1e6, "unit": "Mpix/s",
-               "ms_per_step": float(t_e[0]), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        (ms_e2e,) = max_over_ranks([ms_e / args.steps], world, dev)
+        e2e = {"value": whole_job_mpix_s(world, n_pix, ms_e2e), "unit": "Mpix/s",
+               "ms_per_step": ms_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- roofline of the dominant stage ----
     pk = peaks()

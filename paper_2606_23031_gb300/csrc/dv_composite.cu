@@ -118,10 +118,9 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(
 
 // optical depth of the segment [t0, t1] through one voxel; optionally d tau / d dens[c]
 template <bool GRAD>
-__device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, const float* o, const float* d, float t0,
-                                         float t1, int K, float inv_k, int act, float* dtd) {
+__device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, float is, const float* o, const float* d,
+                                         float t0, float t1, int K, float inv_k, int act, float* dtd) {
     const float h = (t1 - t0) * inv_k;
-    const float is = __fdividef(1.0f, g.w);
     float tau = 0.0f;
     if (GRAD) {
 #pragma unroll
@@ -159,7 +158,7 @@ __device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchP
                                             float4 db, float4 col, const float* o, const float* d, float t0,
                                             float t1, float* acc) {
     float dtd[8];
-    const float tau = seg_tau<GRAD>(g, da, db, o, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
+    const float tau = seg_tau<GRAD>(g, da, db, col.w, o, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
     const float e = __expf(-tau);  // transmittance of the segment
     const float alpha = 1.0f - e;
     const float w = ps.T * alpha;
@@ -376,8 +375,15 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 //   s_st[q][5][lane]    = phase 1: partial segment count; phase 2: 0 not reached,
 //                         1 partial applied, 2 stop inside (replay)
 
+#ifndef DV_FWD_MIN_BLOCKS
+#define DV_FWD_MIN_BLOCKS 5  // resident CTAs per SM the forward is compiled for
+#endif
+#ifndef DV_BWD_MIN_BLOCKS
+#define DV_BWD_MIN_BLOCKS 4
+#endif
+
 template <bool BWD>
-__global__ void __launch_bounds__(CT_THREADS, BWD ? 4 : 5) k_composite(const __grid_constant__ BatchParams bp,
+__global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
                                                         const uint8_t* __restrict__ pmask,

@@ -66,7 +66,7 @@ static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
 //   v[0] = (min.x, min.y, min.z, size)   local frame
 //   v[1] = dens[0..3]
 //   v[2] = dens[4..7]
-//   v[3] = (r, g, b, unused)
+//   v[3] = (r, g, b, 1/size)
 struct __align__(16) VoxRec {
     float4 v[4];
 };

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
     R.v[0] = make_float4(L.mn[0], L.mn[1], L.mn[2], L.s);
     R.v[1] = da;
     R.v[2] = db;
-    R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 0.0f);
+    R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);
     rec[r] = R;
     cnt_sorted[r] = cnt[g];
     rect_sorted[r] = rect[g];

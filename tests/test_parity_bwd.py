@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import check_grad, device_scene, gpu_render, orbit, sample_pixels, small_comp_scene
+from helpers import check_grad, check_grads, device_scene, gpu_render, orbit, sample_pixels, small_comp_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -37,9 +37,8 @@ def _compare(sc, cams, g_rgb, g_depth, g_alpha, K=1, eps=1e-4, what="", pixels=N
                                   np.float64(np.float32(g_depth)).reshape(-1)[pixels],
                                   np.float64(np.float32(g_alpha)).reshape(-1)[pixels], oracle.Opts(K, eps),
                                   pixels=pixels)
-    for i in range(len(sc.octrees)):
-        check_grad(gd[i], od[i], f"{what} d_dens[{i}]")
-        check_grad(gs[i], os_[i], f"{what} d_sh[{i}]")
+    check_grads(gd, od, f"{what} d_dens")
+    check_grads(gs, os_, f"{what} d_sh")
     return gd, od
 
 
@@ -86,9 +85,8 @@ def test_autograd_function_matches_oracle(dv):
     g_rgb = (2.0 * (rgb - target)).detach().cpu().numpy().astype(np.float64)
     od, os_ = oracle.backward(sc.octrees, sc.poses, cam, g_rgb, np.full(40 * 32, np.float64(np.float32(0.1))),
                               np.ones(40 * 32), oracle.Opts(2, 1e-4))
-    for i in range(len(ds)):
-        check_grad(dens[i].grad.cpu().numpy(), od[i], f"autograd dens[{i}]")
-        check_grad(sh[i].grad.cpu().numpy(), os_[i], f"autograd sh[{i}]")
+    check_grads([d.grad.cpu().numpy() for d in dens], od, "autograd dens")
+    check_grads([s.grad.cpu().numpy() for s in sh], os_, "autograd sh")
 
 
 def test_config2_sampled_pixel_gradients(dv, config2_scene):
@@ -144,6 +142,5 @@ def test_batched_views_backward(dv):
             ref_d[i] += od[i]
             ref_s[i] += os_[i]
         off += n
-    for i in range(len(ds)):
-        check_grad(d_dens[i].cpu().numpy(), ref_d[i], f"batched d_dens[{i}]")
-        check_grad(d_sh[i].cpu().numpy(), ref_s[i], f"batched d_sh[{i}]")
+    check_grads([x.cpu().numpy() for x in d_dens], ref_d, "batched d_dens")
+    check_grads([x.cpu().numpy() for x in d_sh], ref_s, "batched d_sh")

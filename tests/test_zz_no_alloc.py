@@ -9,7 +9,7 @@ import pytest
 import ctypes as C
 
 import synth
-from helpers import check_grad, device_scene, orbit, small_comp_scene
+from helpers import check_grad, check_grads, device_scene, orbit, small_comp_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -37,9 +37,8 @@ def test_static_backward_matches_allocating_backward_twice(dv):
     assert sum(np.count_nonzero(x) for x in ref_d) > 100
     for call in range(2):
         got_d, got_s = _grads(dv.dv_render_backward_static, st, ds, g)
-        for i in range(len(ds)):
-            check_grad(got_d[i], ref_d[i], f"static call {call} d_dens[{i}]")
-            check_grad(got_s[i], ref_s[i], f"static call {call} d_sh[{i}]")
+        check_grads(got_d, ref_d, f"static call {call} d_dens")
+        check_grads(got_s, ref_s, f"static call {call} d_sh")
     st.free()
 
 
