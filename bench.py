@@ -39,12 +39,12 @@ WORKLOAD = ("compositional fwd+bwd: LiDAR-shaped background 500k leaves (levels 
             "20k leaves on straight lanes, SH degree 3, one 1920x1080 camera, K=1, eps_stop=1e-4")
 
 # FP32 operations per algorithmic unit, counted from the kernel source (FMA = 2)
-F_TEST = 28          # voxel slab test (per pixel x list entry examined)
+F_TEST = 23          # voxel slab test (per pixel x list entry examined)
 F_BOX = 50           # actor clip-box test (per pixel x box query)
-F_SAMPLE = 41        # one midpoint sample: position, trilinear (7 lerps), activation
-F_SEG = 30           # per segment: clipping, alpha, composite update, stop test
-F_SAMPLE_BWD = 74    # sample + trilinear weights and d tau / d dens
-F_SEG_BWD = 127      # segment + gradient of tau, colour, warp reduction
+F_SAMPLE = 39        # one midpoint sample: position, trilinear (7 lerps), activation
+F_SEG = 23           # per segment: clipping, alpha, composite update, stop test
+F_SAMPLE_BWD = 75    # sample + trilinear weights and d tau / d dens
+F_SEG_BWD = 128      # segment + gradient of tau and colour, share of the warp reduction
 
 
 def log(*a):

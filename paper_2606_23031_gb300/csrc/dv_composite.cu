@@ -85,19 +85,24 @@ __device__ __forceinline__ void rotate(const float* A, const float* x, float* y)
     for (int r = 0; r < 3; ++r) y[r] = fmaf(A[r * 3 + 0], x[0], fmaf(A[r * 3 + 1], x[1], A[r * 3 + 2] * x[2]));
 }
 
-__device__ __forceinline__ bool slab_cube(const float* o, const float* inv, float4 g, float& t0, float& t1) {
-    const float lo[3] = {g.x, g.y, g.z};
-    float a = -INFINITY, b = INFINITY;
+// Ray / voxel slab test.  rel = voxel min corner - ray origin (kept for the sample
+// positions); the far plane of each axis is reached at ta + size / d.
+__device__ __forceinline__ bool slab_cube(const float* o, const float* inv, float4 g, float& t0, float& t1,
+                                          float* rel) {
+    rel[0] = g.x - o[0];
+    rel[1] = g.y - o[1];
+    rel[2] = g.z - o[2];
+    float en[3], ex[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float ta = (lo[k] - o[k]) * inv[k];
-        const float tb = (lo[k] + g.w - o[k]) * inv[k];
-        a = fmaxf(a, fminf(ta, tb));
-        b = fminf(b, fmaxf(ta, tb));
+        const float ta = rel[k] * inv[k];
+        const float tb = fmaf(g.w, inv[k], ta);
+        en[k] = fminf(ta, tb);
+        ex[k] = fmaxf(ta, tb);
     }
-    t0 = a;
-    t1 = b;
-    return a < b;
+    t0 = fmaxf(fmaxf(en[0], en[1]), en[2]);
+    t1 = fminf(fminf(ex[0], ex[1]), ex[2]);
+    return t0 < t1;
 }
 
 __device__ __forceinline__ bool slab_box(const float* o, const float* inv, const float* h, float& t0, float& t1) {
@@ -117,9 +122,12 @@ __device__ __forceinline__ bool slab_box(const float* o, const float* inv, const
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
 // optical depth of the segment [t0, t1] through one voxel; optionally d tau / d dens[c]
-template <bool GRAD>
-__device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, float is, const float* o, const float* d,
-                                         float t0, float t1, int K, float inv_k, int act, float* dtd) {
+// KS > 0: K known at compile time (KS); KS == 0: K from the launch.
+template <bool GRAD, int KS>
+__device__ __forceinline__ float seg_tau(float4 da, float4 db, float is, const float* rel, const float* d, float t0,
+                                         float t1, int K_rt, float inv_k_rt, int act, float* dtd) {
+    const int K = KS > 0 ? KS : K_rt;
+    const float inv_k = KS == 1 ? 1.0f : inv_k_rt;
     const float h = (t1 - t0) * inv_k;
     float tau = 0.0f;
     if (GRAD) {
@@ -128,9 +136,10 @@ __device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, float i
     }
     for (int k = 0; k < K; ++k) {
         const float t = fmaf((float)k + 0.5f, h, t0);
-        const float x = __saturatef((fmaf(t, d[0], o[0]) - g.x) * is);
-        const float y = __saturatef((fmaf(t, d[1], o[1]) - g.y) * is);
-        const float z = __saturatef((fmaf(t, d[2], o[2]) - g.z) * is);
+        // voxel-local coordinates of the sample o + t d: (t d - (min - o)) / size
+        const float x = __saturatef(fmaf(t, d[0], -rel[0]) * is);
+        const float y = __saturatef(fmaf(t, d[1], -rel[1]) * is);
+        const float z = __saturatef(fmaf(t, d[2], -rel[2]) * is);
         const float e00 = lerpf(da.x, da.y, x), e10 = lerpf(da.z, da.w, x);
         const float e01 = lerpf(db.x, db.y, x), e11 = lerpf(db.z, db.w, x);
         const float rho = lerpf(lerpf(e00, e10, y), lerpf(e01, e11, y), z);
@@ -153,12 +162,12 @@ __device__ __forceinline__ float seg_tau(float4 g, float4 da, float4 db, float i
 
 // Composites one segment (with the stop test when STOP); with GRAD also adds
 // this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
-template <bool GRAD, bool STOP>
-__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchParams& bp, float4 g, float4 da,
-                                            float4 db, float4 col, const float* o, const float* d, float t0,
-                                            float t1, float* acc) {
+template <bool GRAD, bool STOP, int KS>
+__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchParams& bp, float4 da, float4 db,
+                                            float4 col, const float* rel, const float* d, float t0, float t1,
+                                            float* acc) {
     float dtd[8];
-    const float tau = seg_tau<GRAD>(g, da, db, col.w, o, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
+    const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
     const float e = __expf(-tau);  // transmittance of the segment
     const float alpha = 1.0f - e;
     const float w = ps.T * alpha;
@@ -272,7 +281,7 @@ __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
 
 // Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
 // NTA lockstep slots).
-template <bool GRAD>
+template <bool GRAD, int KS>
 __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const BatchParams& bp,
                                              const OctParams* __restrict__ vo, const ActInt& it,
                                              const uint32_t* __restrict__ pval, const uint8_t* __restrict__ pmask,
@@ -291,15 +300,15 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Batch
         const uint32_t r = __ldg(pval + q);
         const float4* R = rec[r].v;
         const float4 g = __ldg(R);
-        float t0, t1;
-        if (!slab_cube(o, inv, g, t0, t1)) continue;
+        float t0, t1, rel[3];
+        if (!slab_cube(o, inv, g, t0, t1, rel)) continue;
         t0 = fmaxf(t0, it.a);
         t1 = fminf(t1, it.b);
         if (!(t1 > t0)) continue;
         float acc[11];
 #pragma unroll
         for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
-        add_segment<GRAD, true>(ps, bw, bp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), o, d, t0, t1, acc);
+        add_segment<GRAD, true, KS>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), rel, d, t0, t1, acc);
         if (GRAD) atomic_grad(grad_rec, r, acc);
     }
 }
@@ -307,7 +316,7 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Batch
 // Warp-lockstep walk of octree o's sub-list [q0, q1): every lane with `act`
 // composites the segments inside its interval [a, b] into st (STOP: with the
 // stop test).  With GRAD the per-record gradients are reduced across the warp.
-template <bool GRAD, bool STOP>
+template <bool GRAD, bool STOP, int KS>
 __device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const BatchParams& bp,
                                              const OctParams* __restrict__ vo, int o, float a, float b,
                                              bool act, const uint32_t* __restrict__ pval,
@@ -342,13 +351,13 @@ __device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const Batch
         bool hit = false;
         if (act && !st.done) {
             st.tests += 1;
-            float t0, t1;
-            if (slab_cube(ol, inv, g, t0, t1)) {
+            float t0, t1, rel[3];
+            if (slab_cube(ol, inv, g, t0, t1, rel)) {
                 t0 = fmaxf(t0, a);
                 t1 = fminf(t1, b);
                 if (t1 > t0) {
-                    add_segment<GRAD, STOP>(st, bw, bp, g, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), ol, d, t0, t1,
-                                            acc);
+                    add_segment<GRAD, STOP, KS>(st, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), rel, d, t0, t1,
+                                                acc);
                     hit = true;
                 }
             }
@@ -382,7 +391,7 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 #define DV_BWD_MIN_BLOCKS 4
 #endif
 
-template <bool BWD>
+template <bool BWD, int KS>
 __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
@@ -537,7 +546,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         const int o = s_act[q];
         // a lane whose own transmittance already falls below eps_stop will stop inside this
         // actor whatever T it enters with (T <= 1), so its partial may stop there too
-        walk_actor_warp<false, true>(pt, bw, bp, vo, o, a, b, act, pval, pmask, wbit, rec, s_sub[o], s_sub[o + 1], dc,
+        walk_actor_warp<false, true, KS>(pt, bw, bp, vo, o, a, b, act, pval, pmask, wbit, rec, s_sub[o], s_sub[o + 1], dc,
                                      nullptr);
         ps.tests += pt.tests;
         if (act) {
@@ -585,7 +594,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 ps.n += pn;
             }
         } else {
-            walk_actor_lane<BWD>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc, grad_rec);
+            walk_actor_lane<BWD, KS>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc, grad_rec);
         }
     };
 
@@ -640,9 +649,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             }
             bool contributed = false;
             const float4 g = s_rec[slot][j][0];
-            float t_in, t_out;
+            float t_in, t_out, rel[3];
             if (!ps.done) ps.tests += 1;
-            if (!ps.done && slab_cube(ob, ib, g, t_in, t_out)) {
+            if (!ps.done && slab_cube(ob, ib, g, t_in, t_out, rel)) {
                 t_in = fmaxf(t_in, t_near);
                 t_out = fminf(t_out, t_far);
                 if (t_out > t_in) {
@@ -650,7 +659,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                     float cur = fmaxf(t_in, tau_cur);
                     while (nxt.o >= 0 && nxt.a < t_out && !ps.done) {
                         if (nxt.a > cur) {
-                            add_segment<BWD, true>(ps, bw, bp, g, da, dd, col, ob, db_, cur, nxt.a, acc);
+                            add_segment<BWD, true, KS>(ps, bw, bp, da, dd, col, rel, db_, cur, nxt.a, acc);
                             contributed = true;
                             if (ps.done) break;
                         }
@@ -661,7 +670,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                         ps.boxes += n_ta;
                     }
                     if (!ps.done && t_out > cur) {
-                        add_segment<BWD, true>(ps, bw, bp, g, da, dd, col, ob, db_, cur, t_out, acc);
+                        add_segment<BWD, true, KS>(ps, bw, bp, da, dd, col, rel, db_, cur, t_out, acc);
                         contributed = true;
                     }
                 }
@@ -701,7 +710,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         pt.boxes = 0;
         pt.done = false;
         const int o = s_act[q];
-        walk_actor_warp<BWD, true>(pt, bw, bp, vo, o, s_iv[q][0][tid], s_iv[q][1][tid], act, pval, pmask, wbit, rec,
+        walk_actor_warp<BWD, true, KS>(pt, bw, bp, vo, o, s_iv[q][0][tid], s_iv[q][1][tid], act, pval, pmask, wbit, rec,
                                    s_sub[o], s_sub[o + 1], dc, grad_rec);
         ps.tests += pt.tests;
         if (!BWD && act) {
@@ -839,9 +848,14 @@ cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const
                                  const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
                                  float* t_final, unsigned long long* work, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
-    k_composite<false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range, vis_start,
-                                                             tile_order, rgb, depth, alpha, n_seg, t_final, nullptr,
-                                                             nullptr, nullptr, nullptr, work);
+    if (bp.K == 1)
+        k_composite<false, 1><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range,
+                                                                    vis_start, tile_order, rgb, depth, alpha, n_seg,
+                                                                    t_final, nullptr, nullptr, nullptr, nullptr, work);
+    else
+        k_composite<false, 0><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range,
+                                                                    vis_start, tile_order, rgb, depth, alpha, n_seg,
+                                                                    t_final, nullptr, nullptr, nullptr, nullptr, work);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -852,11 +866,16 @@ cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const
                                  const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
                                  float* grad_rec, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
-    k_composite<true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range, vis_start,
-                                                            tile_order, const_cast<float*>(rgb),
-                                                            const_cast<float*>(depth), nullptr, nullptr,
-                                                            const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
-                                                            grad_rec, nullptr);
+    if (bp.K == 1)
+        k_composite<true, 1><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
+            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+            grad_rec, nullptr);
+    else
+        k_composite<true, 0><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
+            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+            grad_rec, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
