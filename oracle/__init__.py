@@ -61,7 +61,8 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        lib = C.CDLL(build())
+        override = os.environ.get("DV_ORACLE_LIB")   # a separately built oracle (mutation tests)
+        lib = C.CDLL(override if override else build())
         lib.orc_render.restype = C.c_int
         lib.orc_backward.restype = C.c_int
         lib.orc_pixel_segments.restype = C.c_int64

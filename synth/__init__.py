@@ -417,16 +417,16 @@ def lidar_background(n_target: int, seed: int, root_size=200.0, center=(0.0, 0.0
     key = pack_keys(lv_all, ijk_all[:, 0], ijk_all[:, 1], ijk_all[:, 2])
     order = np.argsort(key, kind="stable")
     key, lv_all, ijk_all = key[order], lv_all[order], ijk_all[order]
-    s = root_size / np.exp2(lv_all.astype(np.float64))
-    mn = rmin[None, :] + ijk_all * s[:, None]
+    s = (root_size / np.exp2(lv_all.astype(np.float64))).astype(np.float32)
+    mn = (rmin[None, :] + ijk_all * s[:, None].astype(np.float64)).astype(np.float32)
     if transparent:
-        dens = rng.lognormal(0.0, 1.0, (V, 8))
+        dens = rng.lognormal(0.0, 1.0, (V, 8)).astype(np.float32)
     else:
-        corners = mn[:, None, :] + _corner_offsets()[None, :, :] * s[:, None, None]
+        corners = mn[:, None, :] + _corner_offsets().astype(np.float32)[None, :, :] * s[:, None, None]
         dist = _surface_distance(corners, mn, s, lay)
-        v_hi = (3.0 / s)[:, None] * rng.lognormal(0.0, 0.25, (V, 8))
+        v_hi = (3.0 / s)[:, None] * rng.lognormal(0.0, 0.25, (V, 8)).astype(np.float32)
         dens = soft_prior_density(dist, s[:, None], v_hi)
-    sh = rng.normal(0.0, 0.1, (V, n_sh(sh_degree), 3)).astype(np.float32)
+    sh = rng.standard_normal((V, n_sh(sh_degree), 3), dtype=np.float32) * np.float32(0.1)
     oc = Octree(key, dens.astype(np.float32), sh, sh_degree,
                 tuple(float(x) for x in center), float(root_size), BG)
     return oc, lay

@@ -429,20 +429,19 @@ def _scipy_real_sh(l, m, x, y, z):
     return math.sqrt(2.0) * (-1) ** m * Y(-m).imag
 
 
-def test_sh_basis_matches_scipy_up_to_sign():
+def test_sh_basis_matches_scipy_with_odd_m_sign():
+    # Reading: the real SH of the SH-coloured voxel lineage (degree-1 terms -k*y, k*z, -k*x): scipy's
+    # real SH (built below from the complex ones with the Condon-Shortley phase cancelled) times
+    # (-1)^m, term for term.
     rng = np.random.default_rng(0)
     dirs = rng.normal(size=(25, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
     lm = [(l, m) for l in range(4) for m in range(-l, l + 1)]
-    signs = None
+    sign = np.array([(-1.0) ** m for _, m in lm])
     for x, y, z in dirs:
         Y = oracle.sh_basis(3, x, y, z)
         ref = np.array([_scipy_real_sh(l, m, x, y, z) for l, m in lm])
-        s = np.sign(Y * ref)
-        if signs is None:
-            signs = s
-        np.testing.assert_allclose(np.abs(Y), np.abs(ref), rtol=1e-10, atol=1e-12)
-        np.testing.assert_array_equal(s[np.abs(ref) > 1e-6], signs[np.abs(ref) > 1e-6])
+        np.testing.assert_allclose(Y, sign * ref, rtol=1e-10, atol=1e-12)
 
 
 def test_sh_basis_orthonormal():
@@ -528,3 +527,33 @@ def test_backward_matches_central_differences(K):
             assert ds[oi][v, lm_, ch] == pytest.approx(fd, rel=2e-5, abs=1e-8)
             checked += 1
     assert checked >= 20
+
+
+def test_backward_through_the_colour_clamp():
+    # colour = max(0, sum Y k + 0.5): a channel clamped at zero gets no SH gradient, the others get
+    # the full one; both checked against central differences of the whole image's loss
+    key = synth.pack_keys([1], [0], [0], [0])
+    sh = np.zeros((1, 4, 3), np.float32)
+    sh[0, 0, :] = (-3.0, 0.7, 0.1)       # red clamped: 0.5 - 3 * 0.282 < 0
+    sh[0, 1:, :] = 0.05
+    oc = synth.Octree(key, np.full((1, 8), 1.5, np.float32), sh, 1, (0.0, 0.0, 0.0), 2.0, synth.BG)
+    cam = cam_looking((1.3, 0.8, 3.0), (0.0, 0.0, 0.0), W=9, H=7, fov=40.0)
+    opts = oracle.Opts(K=2, eps_stop=0.0)
+    rng = np.random.default_rng(2)
+    g = (rng.normal(size=(cam.H, cam.W, 3)), np.zeros((cam.H, cam.W)), np.zeros((cam.H, cam.W)))
+    f64 = [(oc.dens.astype(np.float64), oc.sh.astype(np.float64))]
+    _, ds = oracle.backward([oc], [pose64()], cam, g[0].reshape(-1, 3), g[1].reshape(-1), g[2].reshape(-1), opts,
+                            f64_arrays=f64)
+    rgb, _, alpha, _ = oracle.render([oc], [pose64()], cam, opts)
+    assert alpha.max() > 0.1 and np.all(rgb[..., 0] == 0.0)
+    assert np.all(ds[0][0, :, 0] == 0.0) and np.abs(ds[0][0, :, 1]).max() > 1e-3
+    for lm_ in range(4):
+        for ch in range(3):
+            x0 = f64[0][1][0, lm_, ch]
+            h = 1e-6
+            f64[0][1][0, lm_, ch] = x0 + h
+            lp = _loss([oc], [pose64()], cam, f64, g, opts)
+            f64[0][1][0, lm_, ch] = x0 - h
+            lmv = _loss([oc], [pose64()], cam, f64, g, opts)
+            f64[0][1][0, lm_, ch] = x0
+            assert ds[0][0, lm_, ch] == pytest.approx((lp - lmv) / (2 * h), rel=2e-5, abs=1e-8)
