@@ -447,15 +447,30 @@ def run_ours(args):
         h2d = sum(x.numel() * 4 for x in h_g)
         d2h = sum(x.numel() * 4 for x in h_out) + sum(x.numel() * 4 for x in h_grad)
 
+        copy_stream = torch.cuda.Stream()
+
         def e2e_step():
-            for hd, dd in zip(h_g, d_g):
-                dd.copy_(hd, non_blocking=True)
+            # the upload of the upstream gradient only has to land before the backward: it overlaps the
+            # forward on a copy stream; the images go back while the backward runs
+            ev_in, ev_fwd, ev_bwd = (torch.cuda.Event() for _ in range(3))
+            with torch.cuda.stream(copy_stream):
+                for hd, dd in zip(h_g, d_g):
+                    dd.copy_(hd, non_blocking=True)
+                ev_in.record(copy_stream)
             rgb, depth, alpha, st = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
+            ev_fwd.record(stream)
+            stream.wait_event(ev_in)
             dv.dv_render_backward(st, d_g[0], d_g[1], d_g[2], d_dens, d_sh)
-            for ho, do in zip(h_out, (rgb, depth, alpha)):
-                ho.copy_(do, non_blocking=True)
-            for hg, dg in zip(h_grad, d_dens + d_sh):
-                hg.copy_(dg, non_blocking=True)
+            ev_bwd.record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_fwd)
+                for ho, do in zip(h_out, (rgb, depth, alpha)):
+                    do.record_stream(copy_stream)
+                    ho.copy_(do, non_blocking=True)
+                copy_stream.wait_event(ev_bwd)
+                for hg, dg in zip(h_grad, d_dens + d_sh):
+                    hg.copy_(dg, non_blocking=True)
+            stream.wait_stream(copy_stream)
             return st
 
         for _ in range(2):

@@ -85,13 +85,10 @@ __device__ __forceinline__ void rotate(const float* A, const float* x, float* y)
     for (int r = 0; r < 3; ++r) y[r] = fmaf(A[r * 3 + 0], x[0], fmaf(A[r * 3 + 1], x[1], A[r * 3 + 2] * x[2]));
 }
 
-// Ray / voxel slab test.  rel = voxel min corner - ray origin (kept for the sample
-// positions); the far plane of each axis is reached at ta + size / d.
-__device__ __forceinline__ bool slab_cube(const float* o, const float* inv, float4 g, float& t0, float& t1,
-                                          float* rel) {
-    rel[0] = g.x - o[0];
-    rel[1] = g.y - o[1];
-    rel[2] = g.z - o[2];
+// Ray / voxel slab test.  g = (min corner - ray origin, size), so the near plane of
+// each axis is reached at g * inv and the far one at (g + size) * inv.
+__device__ __forceinline__ bool slab_cube(const float* inv, float4 g, float& t0, float& t1) {
+    const float rel[3] = {g.x, g.y, g.z};
     float en[3], ex[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -160,14 +157,8 @@ __device__ __forceinline__ float seg_tau(float4 da, float4 db, float is, const f
     return tau * h;
 }
 
-// Composites one segment (with the stop test when STOP); with GRAD also adds
-// this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
-template <bool GRAD, bool STOP, int KS>
-__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchParams& bp, float4 da, float4 db,
-                                            float4 col, const float* rel, const float* d, float t0, float t1,
-                                            float* acc) {
-    float dtd[8];
-    const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
+// Front-to-back compositing of one segment of optical depth tau; returns its weight T alpha.
+__device__ __forceinline__ float composite_step(Pix& ps, float tau, float4 col, float t0, float t1) {
     const float e = __expf(-tau);  // transmittance of the segment
     const float alpha = 1.0f - e;
     const float w = ps.T * alpha;
@@ -178,7 +169,25 @@ __device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchP
     ps.D = fmaf(w, mid, ps.D);
     ps.T = ps.T * e;
     ps.n += 1;
+    return w;
+}
+
+__device__ __forceinline__ void composite_tau(Pix& ps, float tau, float4 col, float t0, float t1, float eps_stop) {
+    composite_step(ps, tau, col, t0, t1);
+    if (ps.T < eps_stop) ps.done = true;
+}
+
+// Composites one segment (with the stop test when STOP); with GRAD also adds
+// this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
+template <bool GRAD, bool STOP, int KS>
+__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchParams& bp, float4 da, float4 db,
+                                            float4 col, const float* rel, const float* d, float t0, float t1,
+                                            float* acc) {
+    float dtd[8];
+    const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
+    const float w = composite_step(ps, tau, col, t0, t1);
     if (GRAD) {
+        const float mid = 0.5f * (t0 + t1);
         const float Tn = ps.T;
         float gt = bw.gA * bw.Tend;
         gt = fmaf(bw.g0, fmaf(Tn, col.x, -(bw.Cf0 - ps.C0)), gt);
@@ -293,15 +302,15 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Batch
     inv[0] = 1.0f / d[0];
     inv[1] = 1.0f / d[1];
     inv[2] = 1.0f / d[2];
-    const float o[3] = {P.o_loc[0], P.o_loc[1], P.o_loc[2]};
     for (uint32_t q = q0; q < q1 && !ps.done; ++q) {
         if (!(__ldg(pmask + q) & wbit)) continue;
         ps.tests += 1;
         const uint32_t r = __ldg(pval + q);
         const float4* R = rec[r].v;
         const float4 g = __ldg(R);
-        float t0, t1, rel[3];
-        if (!slab_cube(o, inv, g, t0, t1, rel)) continue;
+        float t0, t1;
+        const float rel[3] = {g.x, g.y, g.z};
+        if (!slab_cube(inv, g, t0, t1)) continue;
         t0 = fmaxf(t0, it.a);
         t1 = fminf(t1, it.b);
         if (!(t1 > t0)) continue;
@@ -329,7 +338,6 @@ __device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const Batch
     inv[0] = 1.0f / d[0];
     inv[1] = 1.0f / d[1];
     inv[2] = 1.0f / d[2];
-    const float ol[3] = {P.o_loc[0], P.o_loc[1], P.o_loc[2]};
     uint32_t r_nx = q0 < q1 ? __ldg(pval + q0) : 0u;
     uint32_t m_nx = q0 < q1 ? __ldg(pmask + q0) : 0u;
     for (uint32_t q = q0; q < q1; ++q) {
@@ -351,8 +359,9 @@ __device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const Batch
         bool hit = false;
         if (act && !st.done) {
             st.tests += 1;
-            float t0, t1, rel[3];
-            if (slab_cube(ol, inv, g, t0, t1, rel)) {
+            float t0, t1;
+            const float rel[3] = {g.x, g.y, g.z};
+            if (slab_cube(inv, g, t0, t1)) {
                 t0 = fmaxf(t0, a);
                 t1 = fminf(t1, b);
                 if (t1 > t0) {
@@ -483,7 +492,6 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     ib[0] = 1.0f / db_[0];
     ib[1] = 1.0f / db_[1];
     ib[2] = 1.0f / db_[2];
-    const float ob[3] = {B.o_loc[0], B.o_loc[1], B.o_loc[2]};
 
     Pix ps;
     ps.C0 = ps.C1 = ps.C2 = ps.D = 0.0f;
@@ -639,9 +647,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         cp_async_wait_one();  // batch bi has landed (only batch bi+1 may still be in flight)
         __syncthreads();
         const uint32_t cnt = min((uint32_t)CT_THREADS, bg1 - bg0 - bi * CT_THREADS);
-        for (uint32_t j = 0; j < cnt; ++j) {
-            if (__all_sync(0xffffffffu, ps.done)) break;
-            if (!(s_m[slot][j] & wbit)) continue;  // the voxel misses this warp's 8x4 block
+        // one record of the batch, visited by the whole warp: actor entries, stop rule, gradients
+        auto visit = [&](uint32_t j) {
             float acc[11];
             if (BWD) {
 #pragma unroll
@@ -649,9 +656,10 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             }
             bool contributed = false;
             const float4 g = s_rec[slot][j][0];
-            float t_in, t_out, rel[3];
+            float t_in, t_out;
+            const float rel[3] = {g.x, g.y, g.z};
             if (!ps.done) ps.tests += 1;
-            if (!ps.done && slab_cube(ob, ib, g, t_in, t_out, rel)) {
+            if (!ps.done && slab_cube(ib, g, t_in, t_out)) {
                 t_in = fmaxf(t_in, t_near);
                 t_out = fminf(t_out, t_far);
                 if (t_out > t_in) {
@@ -679,6 +687,60 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 // every lane visits record j of the batch together: reduce across the warp
                 const unsigned any = __ballot_sync(0xffffffffu, contributed);
                 if (any) warp_reduce_add(acc, grad_rec + (size_t)s_r[slot][j] * GSTRIDE);
+            }
+        };
+        bool warp_done = false;
+        for (uint32_t c0 = 0; c0 < cnt && !warp_done; c0 += 32) {
+            // the records of these 32 that touch this warp's 8x4 block, in list order
+            const uint32_t jl = c0 + lane;
+            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && (s_m[slot][jl < cnt ? jl : 0] & wbit));
+            while (m) {
+                if (__all_sync(0xffffffffu, ps.done)) {
+                    warp_done = true;
+                    break;
+                }
+                const uint32_t j0 = c0 + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1;
+                if (BWD || m == 0) {
+                    visit(j0);
+                    continue;
+                }
+                const uint32_t j1 = c0 + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1;
+                // forward, two records at once: both slab tests, then (unless a lane enters an
+                // actor interval inside either segment) both optical depths, then compositing in
+                // list order with the stop rule -- the same arithmetic as two visits
+                const float4 g0 = s_rec[slot][j0][0], g1 = s_rec[slot][j1][0];
+                float a0, b0, a1, b1;
+                const bool x0 = slab_cube(ib, g0, a0, b0);
+                const bool x1 = slab_cube(ib, g1, a1, b1);
+                a0 = fmaxf(a0, t_near);
+                b0 = fminf(b0, t_far);
+                a1 = fmaxf(a1, t_near);
+                b1 = fminf(b1, t_far);
+                const bool live = !ps.done;
+                const bool in0 = live && x0 && b0 > a0, in1 = live && x1 && b1 > a1;
+                const bool cross = nxt.o >= 0 && ((in0 && nxt.a < b0) || (in1 && nxt.a < b1));
+                if (__any_sync(0xffffffffu, cross)) {
+                    visit(j0);
+                    visit(j1);
+                    continue;
+                }
+                a0 = fmaxf(a0, tau_cur);
+                a1 = fmaxf(a1, tau_cur);
+                const bool h0 = in0 && b0 > a0, h1 = in1 && b1 > a1;
+                const float4 da0 = s_rec[slot][j0][1], dd0 = s_rec[slot][j0][2], col0 = s_rec[slot][j0][3];
+                const float4 da1 = s_rec[slot][j1][1], dd1 = s_rec[slot][j1][2], col1 = s_rec[slot][j1][3];
+                const float r0[3] = {g0.x, g0.y, g0.z}, r1[3] = {g1.x, g1.y, g1.z};
+                const float u0 = h0 ? a0 : 0.0f, v0 = h0 ? b0 : 0.0f, u1 = h1 ? a1 : 0.0f, v1 = h1 ? b1 : 0.0f;
+                const float tau0 = seg_tau<false, KS>(da0, dd0, col0.w, r0, db_, u0, v0, bp.K, bp.inv_k, bp.activation,
+                                                      nullptr);
+                const float tau1 = seg_tau<false, KS>(da1, dd1, col1.w, r1, db_, u1, v1, bp.K, bp.inv_k, bp.activation,
+                                                      nullptr);
+                ps.tests += live ? 1u : 0u;
+                if (h0) composite_tau(ps, tau0, col0, u0, v0, bp.eps_stop);
+                ps.tests += (live && !ps.done) ? 1u : 0u;
+                if (h1 && !ps.done) composite_tau(ps, tau1, col1, u1, v1, bp.eps_stop);
             }
         }
         // every warp is done with this slot before batch bi+2 is copied into it
@@ -813,10 +875,10 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
     }
     const float gc0 = gr[8], gc1 = gr[9], gc2 = gr[10];
     if (!d_sh || (gc0 == 0.0f && gc1 == 0.0f && gc2 == 0.0f)) return;
-    const float4 g = rec[r].v[0];
-    float gx = g.x + 0.5f * g.w - P.o_loc[0];
-    float gy = g.y + 0.5f * g.w - P.o_loc[1];
-    float gz = g.z + 0.5f * g.w - P.o_loc[2];
+    const float4 g = rec[r].v[0];  // (min - camera centre, size): same direction as the records kernel
+    float gx = fmaf(0.5f, g.w, g.x);
+    float gy = fmaf(0.5f, g.w, g.y);
+    float gz = fmaf(0.5f, g.w, g.z);
     const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
     const float ig = gl > 0.0f ? 1.0f / gl : 0.0f;
     gx *= ig;

@@ -63,7 +63,7 @@ struct BatchParams {
 static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
 
 // 64-byte per-voxel render record, one per visible (view, voxel) in depth-key order.
-//   v[0] = (min.x, min.y, min.z, size)   local frame
+//   v[0] = (min - o, size)   min corner relative to the camera centre o, both in the octree's frame
 //   v[1] = dens[0..3]
 //   v[2] = dens[4..7]
 //   v[3] = (r, g, b, 1/size)

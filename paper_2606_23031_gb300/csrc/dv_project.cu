@@ -226,10 +226,12 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
     const Leaf L = decode_leaf(P, P.key[v]);
     const float4* d4 = reinterpret_cast<const float4*>(P.dens + v * 8);
     const float4 da = __ldg(d4), db = __ldg(d4 + 1);
-    // view direction: camera centre -> voxel centre, octree frame
-    float gx = L.mn[0] + 0.5f * L.s - P.o_loc[0];
-    float gy = L.mn[1] + 0.5f * L.s - P.o_loc[1];
-    float gz = L.mn[2] + 0.5f * L.s - P.o_loc[2];
+    // min corner relative to the camera centre (octree frame), then the view direction:
+    // camera centre -> voxel centre
+    const float rx = L.mn[0] - P.o_loc[0], ry = L.mn[1] - P.o_loc[1], rz = L.mn[2] - P.o_loc[2];
+    float gx = fmaf(0.5f, L.s, rx);
+    float gy = fmaf(0.5f, L.s, ry);
+    float gz = fmaf(0.5f, L.s, rz);
     const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
     const float ig = gl > 0.0f ? 1.0f / gl : 0.0f;
     gx *= ig;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
         c2 = fmaf(b[q], __ldg(shv + q * 3 + 2), c2);
     }
     VoxRec R;
-    R.v[0] = make_float4(L.mn[0], L.mn[1], L.mn[2], L.s);
+    R.v[0] = make_float4(rx, ry, rz, L.s);
     R.v[1] = da;
     R.v[2] = db;
     R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);

@@ -237,6 +237,209 @@ cudaError_t radix_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_al
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// one-sweep radix sort: one kernel per 8-bit pass
+//
+// The global digit histogram of every pass is computed up front in one read of
+// the keys.  A pass kernel then takes tiles in order from an atomic counter;
+// each tile ranks its keys stably (as above), publishes its per-digit counts
+// (flag AGG), looks back over its predecessors for its exclusive prefix -- an
+// inclusive predecessor (flag INC) ends the walk -- publishes its inclusive
+// count and scatters.  A tile only waits on tiles that took their index
+// earlier, so every wait ends; each spin is still bounded, and a bound that
+// runs out sets an error flag.
+// ---------------------------------------------------------------------------
+
+constexpr int OS_THREADS = 256;
+constexpr int OS_MAX_PASSES = 8;
+constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_VAL = (1u << 30) - 1u;
+constexpr int OS_SPIN_LIMIT = 1 << 22;
+constexpr int OS_LOOK = 8;  // predecessors read per look-back step
+
+template <typename K>
+__global__ void __launch_bounds__(OS_THREADS) k_os_hist(const K* __restrict__ keys, int64_t n, int n_passes,
+                                                         int n_bits, uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[OS_MAX_PASSES][RS_RADIX];
+    for (int p = 0; p < n_passes; ++p) h[p][threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const K k = keys[i];
+        for (int p = 0; p < n_passes; ++p) {
+            const int sh = 8 * p;
+            const int bits = n_bits - sh < 8 ? n_bits - sh : 8;
+            atomicAdd(&h[p][(uint32_t)(k >> sh) & ((1u << bits) - 1u)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < n_passes; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[p * RS_RADIX + threadIdx.x], h[p][threadIdx.x]);
+}
+
+// exclusive scan of each pass's 256 digit counts (one block per pass)
+__global__ void k_os_bins(uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t tot;
+    uint32_t* h = ghist + blockIdx.x * RS_RADIX;
+    const uint32_t x = h[threadIdx.x];
+    const uint32_t e = block_excl_scan<uint32_t>(x, &tot);
+    h[threadIdx.x] = e;
+}
+
+__device__ __forceinline__ uint32_t os_load(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+template <typename K, int ROUNDS>
+__global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                         int64_t n, int shift, uint32_t mask,
+                                                         const uint32_t* __restrict__ goff,
+                                                         uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
+                                                         uint32_t* __restrict__ err, K* __restrict__ okeys,
+                                                         uint32_t* __restrict__ ovals) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t run[RS_RADIX];
+    __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+    __shared__ uint32_t s_base[RS_RADIX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    run[tid] = 0;
+    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * OS_THREADS * ROUNDS;
+    const unsigned lt = (1u << lane) - 1u;
+    K key[ROUNDS];
+    uint32_t val[ROUNDS], dig[ROUNDS], rank[ROUNDS];
+    // all of the tile's loads first (no barrier between them), then the ranking rounds
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int64_t i = base + (int64_t)r * OS_THREADS + tid;
+        const bool ok = i < n;
+        key[r] = ok ? keys[i] : K(0);
+        val[r] = ok ? vals[i] : 0u;
+        dig[r] = ok ? ((uint32_t)(key[r] >> shift) & mask) : 0xffffffffu;
+    }
+    // stable tile-local ranks, round by round
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const uint32_t d = dig[r];
+        const bool ok = d != 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rk = __popc(peers & lt);
+        if (ok && rk == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            uint32_t before = 0;
+            for (int w = 0; w < warp; ++w) before += wcnt[w][d];
+            rank[r] = run[d] + before + (uint32_t)rk;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            add += wcnt[w][tid];
+            wcnt[w][tid] = 0;
+        }
+        run[tid] += add;
+        __syncthreads();
+    }
+    // publish, look back, publish inclusive (thread tid owns digit tid)
+    const uint32_t mine = run[tid];
+    uint32_t* st = status + (size_t)tile * RS_RADIX + tid;
+    if (tile == 0) {
+        *(volatile uint32_t*)st = OS_INC | mine;
+        s_base[tid] = goff[tid];
+    } else {
+        *(volatile uint32_t*)st = OS_AGG | mine;
+        // look back OS_LOOK predecessors at a time: their status words are loaded together, then
+        // summed from the nearest one until an inclusive prefix; a word not yet published is
+        // re-read (bounded)
+        uint32_t excl = 0;
+        int64_t t = (int64_t)tile - 1;
+        bool fin = false;
+        while (!fin && t >= 0) {
+            uint32_t v[OS_LOOK];
+#pragma unroll
+            for (int i = 0; i < OS_LOOK; ++i) v[i] = t - i >= 0 ? os_load(status + (size_t)(t - i) * RS_RADIX + tid) : OS_INC;
+#pragma unroll
+            for (int i = 0; i < OS_LOOK; ++i) {
+                if (fin) break;
+                if (t - i < 0) {
+                    fin = true;
+                    break;
+                }
+                const uint32_t* sp = status + (size_t)(t - i) * RS_RADIX + tid;
+                int spins = 0;
+                while ((v[i] & ~OS_VAL) == 0 && ++spins < OS_SPIN_LIMIT) v[i] = os_load(sp);
+                if ((v[i] & ~OS_VAL) == 0) {
+                    atomicOr(err, 1u);
+                    fin = true;
+                    break;
+                }
+                excl += v[i] & OS_VAL;
+                if (v[i] & OS_INC) fin = true;
+            }
+            t -= OS_LOOK;
+        }
+        __threadfence();
+        *(volatile uint32_t*)st = OS_INC | ((excl + mine) & OS_VAL);
+        s_base[tid] = goff[tid] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int64_t i = base + (int64_t)r * OS_THREADS + tid;
+        if (i < n) {
+            int64_t pos = (int64_t)s_base[dig[r]] + rank[r];
+            pos = pos < n ? pos : n - 1;  // only a timed-out look-back can leave the range
+            okeys[pos] = key[r];
+            ovals[pos] = val[r];
+        }
+    }
+}
+
+template <typename K>
+cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits,
+                          Arena& ar, cudaStream_t s) {
+    constexpr int ROUNDS = 8;
+    const int passes = (n_bits + 7) / 8;
+    const int64_t tile = (int64_t)OS_THREADS * ROUNDS;
+    const int64_t n_tiles = (n + tile - 1) / tile;
+    const size_t words = (size_t)passes * (RS_RADIX + 1 + (size_t)n_tiles * RS_RADIX) + 1;
+    uint32_t* w = ar.alloc<uint32_t>(words);
+    if (!w) return ar.err;
+    uint32_t* ghist = w;                                   // [passes][256]
+    uint32_t* counters = ghist + passes * RS_RADIX;        // [passes]
+    uint32_t* err = counters + passes;                     // [1]
+    uint32_t* status = err + 1;                            // [passes][n_tiles][256]
+    cudaError_t e = cudaMemsetAsync(w, 0, words * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    int64_t hist_blocks = (n + OS_THREADS * 4 - 1) / (OS_THREADS * 4);  // ~4 keys per thread, at most 8 CTAs per SM
+    if (hist_blocks > 152 * 8) hist_blocks = 152 * 8;
+    k_os_hist<K><<<(unsigned)(hist_blocks < 1 ? 1 : hist_blocks), OS_THREADS, 0, s>>>(keys, n, passes, n_bits, ghist);
+    count_launches(1);
+    k_os_bins<<<passes, RS_RADIX, 0, s>>>(ghist);
+    count_launches(1);
+    K* src_k = keys;
+    uint32_t* src_v = vals;
+    K* dst_k = keys_alt;
+    uint32_t* dst_v = vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        const int bits = n_bits - shift < 8 ? n_bits - shift : 8;
+        k_os_pass<K, ROUNDS><<<(unsigned)n_tiles, OS_THREADS, 0, s>>>(
+            src_k, src_v, n, shift, (1u << bits) - 1u, ghist + p * RS_RADIX, status + (size_t)p * n_tiles * RS_RADIX,
+            counters + p, err, dst_k, dst_v);
+        count_launches(1);
+        K* tk = src_k;
+        src_k = dst_k;
+        dst_k = tk;
+        uint32_t* tv = src_v;
+        src_v = dst_v;
+        dst_v = tv;
+    }
+    keys = src_k;
+    vals = src_v;
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
@@ -249,13 +452,20 @@ cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32
     return scan_impl<uint32_t, uint32_t>(in, out, n, total_dev, ar, s);
 }
 
+// one-sweep passes while the counts fit the 30-bit status words, reduce-then-scan passes beyond
 cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
                            int n_bits, Arena& ar, cudaStream_t s) {
+    if (n <= 1 || n_bits <= 0) return cudaSuccess;
+    if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
+        return onesweep_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
     return radix_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 
 cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
                            int n_bits, Arena& ar, cudaStream_t s) {
+    if (n <= 1 || n_bits <= 0) return cudaSuccess;
+    if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
+        return onesweep_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
     return radix_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 
