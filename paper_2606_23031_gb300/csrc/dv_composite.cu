@@ -9,11 +9,13 @@
 //  * Each pixel splits its ray into background and actor intervals with the
 //    actor clip boxes (slab test in each actor's frame, reached through the
 //    inverse pose; the box entered first owns any overlap).
-//  * Phase 1: for every actor of the tile, each warp walks that actor's
-//    sub-list in lockstep; every lane composites the segments inside its own
-//    interval of that actor into a partial (C_A, D_A, T_A) starting from T = 1.
-//  * Phase 2: the background sub-list streams through a two-slot shared-memory
-//    ring (cp.async, one batch ahead).  A background hit that reaches past the
+//  * Every sub-list (each actor's, the background's) streams through a two-slot
+//    shared-memory ring (cp.async, one batch ahead); each warp visits, in list
+//    order and in lockstep, the records that touch its 8x4 pixel block.
+//  * Phase 1: for every actor of the tile, every lane composites the segments
+//    inside its own interval of that actor into a partial (C_A, D_A, T_A)
+//    starting from T = 1.
+//  * Phase 2: the background sub-list.  A background hit that reaches past the
 //    next actor's entry composites its part in front of the box, then applies
 //    that actor's partial with the running transmittance (C += T C_A,
 //    D += T D_A, T *= T_A), then continues behind the box.  If T T_A < eps_stop
@@ -38,6 +40,8 @@
 //    walk of the actor's sub-list (correct, but divergent).
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "dv_internal.cuh"
 
@@ -322,62 +326,6 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Batch
     }
 }
 
-// Warp-lockstep walk of octree o's sub-list [q0, q1): every lane with `act`
-// composites the segments inside its interval [a, b] into st (STOP: with the
-// stop test).  With GRAD the per-record gradients are reduced across the warp.
-template <bool GRAD, bool STOP, int KS>
-__device__ __noinline__ void walk_actor_warp(Pix& st, const Bwd& bw, const BatchParams& bp,
-                                             const OctParams* __restrict__ vo, int o, float a, float b,
-                                             bool act, const uint32_t* __restrict__ pval,
-                                             const uint8_t* __restrict__ pmask, uint32_t wbit,
-                                             const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
-                                             const float* dc, float* grad_rec) {
-    const OctParams& P = vo[o];
-    float d[3], inv[3];
-    rotate(P.A, dc, d);
-    inv[0] = 1.0f / d[0];
-    inv[1] = 1.0f / d[1];
-    inv[2] = 1.0f / d[2];
-    uint32_t r_nx = q0 < q1 ? __ldg(pval + q0) : 0u;
-    uint32_t m_nx = q0 < q1 ? __ldg(pmask + q0) : 0u;
-    for (uint32_t q = q0; q < q1; ++q) {
-        if (!__any_sync(0xffffffffu, act && !st.done)) break;
-        const uint32_t r = r_nx;
-        const uint32_t m = m_nx;
-        if (q + 1 < q1) {
-            r_nx = __ldg(pval + q + 1);
-            m_nx = __ldg(pmask + q + 1);
-        }
-        if (!(m & wbit)) continue;  // the voxel misses this warp's 8x4 block
-        const float4* R = rec[r].v;
-        const float4 g = __ldg(R);
-        float acc[11];
-        if (GRAD) {
-#pragma unroll
-            for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
-        }
-        bool hit = false;
-        if (act && !st.done) {
-            st.tests += 1;
-            float t0, t1;
-            const float rel[3] = {g.x, g.y, g.z};
-            if (slab_cube(inv, g, t0, t1)) {
-                t0 = fmaxf(t0, a);
-                t1 = fminf(t1, b);
-                if (t1 > t0) {
-                    add_segment<GRAD, STOP, KS>(st, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), rel, d, t0, t1,
-                                                acc);
-                    hit = true;
-                }
-            }
-        }
-        if (GRAD) {
-            const unsigned any = __ballot_sync(0xffffffffu, hit);
-            if (any) warp_reduce_add(acc, grad_rec + (size_t)r * GSTRIDE);
-        }
-    }
-}
-
 // 16-byte asynchronous global -> shared copy (L2 only), and its group fences
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -539,23 +487,128 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         }
     }
 
+    // Every sub-list (an actor's, then the background's) streams through the shared
+    // two-slot ring, CT_THREADS records per batch (cp.async, one batch ahead).  Each warp
+    // visits the records of a batch that touch its 8x4 block (ballot over the pair
+    // masks), 32 at a time: chunk(slot, c0, m) gets the ring slot, the first record of
+    // the 32 and the mask of those to visit, and returns true once the warp has nothing
+    // left to do in this list.  The batch loop, its barriers and its early exit are
+    // CTA-uniform.
+    auto stream = [&](uint32_t q0, uint32_t q1, auto&& chunk) {
+        const uint32_t n_batch = (q1 - q0 + CT_THREADS - 1) / CT_THREADS;
+        uint32_t r_ahead = 0, m_ahead = 0;
+        if (n_batch > 0) {
+            const uint32_t qa = q0 + tid;
+            if (qa < q1) {
+                const uint32_t r = __ldg(pval + qa);
+                const float4* R = rec[r].v;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async16(&s_rec[0][tid][k], R + k);
+                s_r[0][tid] = r;
+                s_m[0][tid] = __ldg(pmask + qa);
+            }
+            cp_async_commit();
+            const uint32_t qb = q0 + CT_THREADS + tid;
+            if (qb < q1) {
+                r_ahead = __ldg(pval + qb);
+                m_ahead = __ldg(pmask + qb);
+            }
+        }
+        bool fin = false;
+        for (uint32_t bi = 0; bi < n_batch; ++bi) {
+            const int slot = bi & 1;
+            {
+                const uint32_t qa = q0 + (bi + 1) * CT_THREADS + tid;
+                if (qa < q1) {
+                    const float4* R = rec[r_ahead].v;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cp_async16(&s_rec[slot ^ 1][tid][k], R + k);
+                    s_r[slot ^ 1][tid] = r_ahead;
+                    s_m[slot ^ 1][tid] = (uint8_t)m_ahead;
+                }
+                cp_async_commit();
+                const uint32_t qb = q0 + (bi + 2) * CT_THREADS + tid;
+                if (qb < q1) {
+                    r_ahead = __ldg(pval + qb);
+                    m_ahead = __ldg(pmask + qb);
+                }
+            }
+            cp_async_wait_one();  // batch bi has landed (only batch bi+1 may still be in flight)
+            __syncthreads();
+            const uint32_t cnt = min((uint32_t)CT_THREADS, q1 - q0 - bi * CT_THREADS);
+            for (uint32_t c0 = 0; c0 < cnt && !fin; c0 += 32) {
+                const uint32_t jl = c0 + lane;
+                const unsigned m = __ballot_sync(0xffffffffu, jl < cnt && (s_m[slot][jl < cnt ? jl : 0] & wbit));
+                fin = chunk(slot, c0, m);
+            }
+            // every warp is done with this slot before batch bi+2 is copied into it
+            if (__syncthreads_or(!fin) == 0) break;
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the list (early exit)
+        __syncthreads();                                     // the ring is free for the next list
+    };
+
+    // Lockstep walk of actor o's sub-list: lanes not yet done composite the segments inside
+    // their interval [a, b] of that actor into pt, with the stop rule (and, with G, the
+    // per-record gradients reduced across the warp).
+    auto walk_actor = [&](Pix& pt, int o, float a, float b, auto grad) {
+        constexpr bool G = decltype(grad)::value;
+        const OctParams& P = vo[o];
+        float d[3], inv[3];
+        rotate(P.A, dc, d);
+        inv[0] = 1.0f / d[0];
+        inv[1] = 1.0f / d[1];
+        inv[2] = 1.0f / d[2];
+        stream(s_sub[o], s_sub[o + 1], [&](int slot, uint32_t c0, unsigned m) -> bool {
+            while (m) {
+                if (__all_sync(0xffffffffu, pt.done)) return true;
+                const uint32_t j = c0 + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1;
+                float acc[11];
+                if (G) {
+#pragma unroll
+                    for (int i = 0; i < 11; ++i) acc[i] = 0.0f;
+                }
+                bool hit = false;
+                if (!pt.done) {
+                    pt.tests += 1;
+                    const float4 g = s_rec[slot][j][0];
+                    float t0, t1;
+                    if (slab_cube(inv, g, t0, t1)) {
+                        t0 = fmaxf(t0, a);
+                        t1 = fminf(t1, b);
+                        if (t1 > t0) {
+                            const float rel[3] = {g.x, g.y, g.z};
+                            add_segment<G, true, KS>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
+                                                     s_rec[slot][j][3], rel, d, t0, t1, acc);
+                            hit = true;
+                        }
+                    }
+                }
+                if (G) {
+                    const unsigned any = __ballot_sync(0xffffffffu, hit);
+                    if (any) warp_reduce_add(acc, grad_rec + (size_t)s_r[slot][j] * GSTRIDE);
+                }
+            }
+            return __all_sync(0xffffffffu, pt.done);
+        });
+    };
+
     // ---- phase 1: partial composite of every lockstep actor interval ----
     for (int q = 0; q < n_lock; ++q) {
         const float a = s_iv[q][0][tid], b = s_iv[q][1][tid];
         const bool act = valid && b > a;
-        if (!__any_sync(0xffffffffu, act)) continue;
+        if (__syncthreads_or(act) == 0) continue;
         Pix pt;
         pt.C0 = pt.C1 = pt.C2 = pt.D = 0.0f;
         pt.T = 1.0f;
         pt.n = 0;
         pt.tests = 0;
         pt.boxes = 0;
-        pt.done = false;
-        const int o = s_act[q];
+        pt.done = !act;
         // a lane whose own transmittance already falls below eps_stop will stop inside this
         // actor whatever T it enters with (T <= 1), so its partial may stop there too
-        walk_actor_warp<false, true, KS>(pt, bw, bp, vo, o, a, b, act, pval, pmask, wbit, rec, s_sub[o], s_sub[o + 1], dc,
-                                     nullptr);
+        walk_actor(pt, s_act[q], a, b, std::false_type());
         ps.tests += pt.tests;
         if (act) {
             s_st[q][0][tid] = pt.C0;
@@ -606,53 +659,13 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         }
     };
 
-    const uint32_t bg0 = s_sub[0], bg1 = s_sub[1];
-    const uint32_t n_batch = (bg1 - bg0 + CT_THREADS - 1) / CT_THREADS;
-    uint32_t r_ahead = 0, m_ahead = 0;
-    if (n_batch > 0) {
-        const uint32_t q0 = bg0 + tid;
-        if (q0 < bg1) {
-            const uint32_t r = __ldg(pval + q0);
-            const float4* R = rec[r].v;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cp_async16(&s_rec[0][tid][k], R + k);
-            s_r[0][tid] = r;
-            s_m[0][tid] = __ldg(pmask + q0);
-        }
-        cp_async_commit();
-        const uint32_t q1 = bg0 + CT_THREADS + tid;
-        if (q1 < bg1) {
-            r_ahead = __ldg(pval + q1);
-            m_ahead = __ldg(pmask + q1);
-        }
-    }
-    for (uint32_t bi = 0; bi < n_batch; ++bi) {
-        const int slot = bi & 1;
-        {
-            const uint32_t q1 = bg0 + (bi + 1) * CT_THREADS + tid;
-            if (q1 < bg1) {
-                const float4* R = rec[r_ahead].v;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) cp_async16(&s_rec[slot ^ 1][tid][k], R + k);
-                s_r[slot ^ 1][tid] = r_ahead;
-                s_m[slot ^ 1][tid] = (uint8_t)m_ahead;
-            }
-            cp_async_commit();
-            const uint32_t q2 = bg0 + (bi + 2) * CT_THREADS + tid;
-            if (q2 < bg1) {
-                r_ahead = __ldg(pval + q2);
-                m_ahead = __ldg(pmask + q2);
-            }
-        }
-        cp_async_wait_one();  // batch bi has landed (only batch bi+1 may still be in flight)
-        __syncthreads();
-        const uint32_t cnt = min((uint32_t)CT_THREADS, bg1 - bg0 - bi * CT_THREADS);
+    stream(s_sub[0], s_sub[1], [&](int slot, uint32_t c0, unsigned m) -> bool {
         // one record of the batch, visited by the whole warp: actor entries, stop rule, gradients
         auto visit = [&](uint32_t j) {
             float acc[11];
             if (BWD) {
 #pragma unroll
-                for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
+                for (int i = 0; i < 11; ++i) acc[i] = 0.0f;
             }
             bool contributed = false;
             const float4 g = s_rec[slot][j][0];
@@ -690,63 +703,56 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             }
         };
         bool warp_done = false;
-        for (uint32_t c0 = 0; c0 < cnt && !warp_done; c0 += 32) {
-            // the records of these 32 that touch this warp's 8x4 block, in list order
-            const uint32_t jl = c0 + lane;
-            unsigned m = __ballot_sync(0xffffffffu, jl < cnt && (s_m[slot][jl < cnt ? jl : 0] & wbit));
-            while (m) {
-                if (__all_sync(0xffffffffu, ps.done)) {
-                    warp_done = true;
-                    break;
-                }
-                const uint32_t j0 = c0 + (uint32_t)(__ffs(m) - 1);
-                m &= m - 1;
-                if (BWD || m == 0) {
-                    visit(j0);
-                    continue;
-                }
-                const uint32_t j1 = c0 + (uint32_t)(__ffs(m) - 1);
-                m &= m - 1;
-                // forward, two records at once: both slab tests, then (unless a lane enters an
-                // actor interval inside either segment) both optical depths, then compositing in
-                // list order with the stop rule -- the same arithmetic as two visits
-                const float4 g0 = s_rec[slot][j0][0], g1 = s_rec[slot][j1][0];
-                float a0, b0, a1, b1;
-                const bool x0 = slab_cube(ib, g0, a0, b0);
-                const bool x1 = slab_cube(ib, g1, a1, b1);
-                a0 = fmaxf(a0, t_near);
-                b0 = fminf(b0, t_far);
-                a1 = fmaxf(a1, t_near);
-                b1 = fminf(b1, t_far);
-                const bool live = !ps.done;
-                const bool in0 = live && x0 && b0 > a0, in1 = live && x1 && b1 > a1;
-                const bool cross = nxt.o >= 0 && ((in0 && nxt.a < b0) || (in1 && nxt.a < b1));
-                if (__any_sync(0xffffffffu, cross)) {
-                    visit(j0);
-                    visit(j1);
-                    continue;
-                }
-                a0 = fmaxf(a0, tau_cur);
-                a1 = fmaxf(a1, tau_cur);
-                const bool h0 = in0 && b0 > a0, h1 = in1 && b1 > a1;
-                const float4 da0 = s_rec[slot][j0][1], dd0 = s_rec[slot][j0][2], col0 = s_rec[slot][j0][3];
-                const float4 da1 = s_rec[slot][j1][1], dd1 = s_rec[slot][j1][2], col1 = s_rec[slot][j1][3];
-                const float r0[3] = {g0.x, g0.y, g0.z}, r1[3] = {g1.x, g1.y, g1.z};
-                const float u0 = h0 ? a0 : 0.0f, v0 = h0 ? b0 : 0.0f, u1 = h1 ? a1 : 0.0f, v1 = h1 ? b1 : 0.0f;
-                const float tau0 = seg_tau<false, KS>(da0, dd0, col0.w, r0, db_, u0, v0, bp.K, bp.inv_k, bp.activation,
-                                                      nullptr);
-                const float tau1 = seg_tau<false, KS>(da1, dd1, col1.w, r1, db_, u1, v1, bp.K, bp.inv_k, bp.activation,
-                                                      nullptr);
-                ps.tests += live ? 1u : 0u;
-                if (h0) composite_tau(ps, tau0, col0, u0, v0, bp.eps_stop);
-                ps.tests += (live && !ps.done) ? 1u : 0u;
-                if (h1 && !ps.done) composite_tau(ps, tau1, col1, u1, v1, bp.eps_stop);
+        while (m) {
+            if (__all_sync(0xffffffffu, ps.done)) {
+                warp_done = true;
+                break;
             }
+            const uint32_t j0 = c0 + (uint32_t)(__ffs(m) - 1);
+            m &= m - 1;
+            if (BWD || m == 0) {
+                visit(j0);
+                continue;
+            }
+            const uint32_t j1 = c0 + (uint32_t)(__ffs(m) - 1);
+            m &= m - 1;
+            // forward, two records at once: both slab tests, then (unless a lane enters an
+            // actor interval inside either segment) both optical depths, then compositing in
+            // list order with the stop rule -- the same arithmetic as two visits
+            const float4 g0 = s_rec[slot][j0][0], g1 = s_rec[slot][j1][0];
+            float a0, b0, a1, b1;
+            const bool x0 = slab_cube(ib, g0, a0, b0);
+            const bool x1 = slab_cube(ib, g1, a1, b1);
+            a0 = fmaxf(a0, t_near);
+            b0 = fminf(b0, t_far);
+            a1 = fmaxf(a1, t_near);
+            b1 = fminf(b1, t_far);
+            const bool live = !ps.done;
+            const bool in0 = live && x0 && b0 > a0, in1 = live && x1 && b1 > a1;
+            const bool cross = nxt.o >= 0 && ((in0 && nxt.a < b0) || (in1 && nxt.a < b1));
+            if (__any_sync(0xffffffffu, cross)) {
+                visit(j0);
+                visit(j1);
+                continue;
+            }
+            a0 = fmaxf(a0, tau_cur);
+            a1 = fmaxf(a1, tau_cur);
+            const bool h0 = in0 && b0 > a0, h1 = in1 && b1 > a1;
+            const float4 da0 = s_rec[slot][j0][1], dd0 = s_rec[slot][j0][2], col0 = s_rec[slot][j0][3];
+            const float4 da1 = s_rec[slot][j1][1], dd1 = s_rec[slot][j1][2], col1 = s_rec[slot][j1][3];
+            const float r0[3] = {g0.x, g0.y, g0.z}, r1[3] = {g1.x, g1.y, g1.z};
+            const float u0 = h0 ? a0 : 0.0f, v0 = h0 ? b0 : 0.0f, u1 = h1 ? a1 : 0.0f, v1 = h1 ? b1 : 0.0f;
+            const float tau0 = seg_tau<false, KS>(da0, dd0, col0.w, r0, db_, u0, v0, bp.K, bp.inv_k, bp.activation,
+                                                  nullptr);
+            const float tau1 = seg_tau<false, KS>(da1, dd1, col1.w, r1, db_, u1, v1, bp.K, bp.inv_k, bp.activation,
+                                                  nullptr);
+            ps.tests += live ? 1u : 0u;
+            if (h0) composite_tau(ps, tau0, col0, u0, v0, bp.eps_stop);
+            ps.tests += (live && !ps.done) ? 1u : 0u;
+            if (h1 && !ps.done) composite_tau(ps, tau1, col1, u1, v1, bp.eps_stop);
         }
-        // every warp is done with this slot before batch bi+2 is copied into it
-        if (__syncthreads_count(!ps.done) == 0) break;
-    }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the loop (early exit)
+        return warp_done || __all_sync(0xffffffffu, ps.done);
+    });
     // actor intervals behind the last background hit
     while (nxt.o >= 0 && !ps.done) {
         enter_actor(nxt);
@@ -760,7 +766,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     for (int q = 0; q < n_lock; ++q) {
         const int status = valid ? (int)s_st[q][5][tid] : 0;
         const bool act = BWD ? status >= 1 : status == 2;
-        if (!__any_sync(0xffffffffu, act)) continue;
+        if (__syncthreads_or(act) == 0) continue;
         Pix pt;
         pt.C0 = act ? s_st[q][0][tid] : 0.0f;
         pt.C1 = act ? s_st[q][1][tid] : 0.0f;
@@ -770,10 +776,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         pt.n = 0;
         pt.tests = 0;
         pt.boxes = 0;
-        pt.done = false;
-        const int o = s_act[q];
-        walk_actor_warp<BWD, true, KS>(pt, bw, bp, vo, o, s_iv[q][0][tid], s_iv[q][1][tid], act, pval, pmask, wbit, rec,
-                                   s_sub[o], s_sub[o + 1], dc, grad_rec);
+        pt.done = !act;
+        walk_actor(pt, s_act[q], s_iv[q][0][tid], s_iv[q][1][tid], std::integral_constant<bool, BWD>());
         ps.tests += pt.tests;
         if (!BWD && act) {
             ps.C0 = pt.C0;
