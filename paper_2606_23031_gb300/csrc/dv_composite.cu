@@ -89,20 +89,54 @@ __device__ __forceinline__ void rotate(const float* A, const float* x, float* y)
     for (int r = 0; r < 3; ++r) y[r] = fmaf(A[r * 3 + 0], x[0], fmaf(A[r * 3 + 1], x[1], A[r * 3 + 2] * x[2]));
 }
 
-// Ray / voxel slab test.  g = (min corner - ray origin, size), so the near plane of
-// each axis is reached at g * inv and the far one at (g + size) * inv.
-__device__ __forceinline__ bool slab_cube(const float* inv, float4 g, float& t0, float& t1) {
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Inverse ray direction, also split by sign, so that the slab test takes each axis's
+// entry and exit plane without a min/max.  |d| is kept at or above 1e-20, so every
+// product stays finite: a ray parallel to a slab gets entry and exit times of order
+// 1e20 of the right signs instead of infinities (and NaN where inf - inf would meet).
+struct InvDir {
+    float inv[3];  // 1 / d
+    float ip[3];   // 1 / d where d > 0, else 0
+    float in[3];   // 1 / d where d < 0, else 0
+};
+
+__device__ __forceinline__ InvDir inv_dir(const float* d) {
+    InvDir r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float dk = fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k];
+        r.inv[k] = 1.0f / dk;
+        r.ip[k] = dk > 0.0f ? r.inv[k] : 0.0f;
+        r.in[k] = dk < 0.0f ? r.inv[k] : 0.0f;
+    }
+    return r;
+}
+
+// Ray / voxel slab test.  g = (min corner - ray origin, size): along axis k the ray
+// crosses the min plane at g_k / d_k and the max plane at (g_k + size) / d_k; which of
+// the two it enters by follows from the sign of d_k.
+__device__ __forceinline__ bool slab_cube(const InvDir& v, float4 g, float& t0, float& t1) {
     const float rel[3] = {g.x, g.y, g.z};
     float en[3], ex[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float ta = rel[k] * inv[k];
-        const float tb = fmaf(g.w, inv[k], ta);
-        en[k] = fminf(ta, tb);
-        ex[k] = fmaxf(ta, tb);
+        const float ta = rel[k] * v.inv[k];
+        en[k] = fmaf(g.w, v.in[k], ta);
+        ex[k] = fmaf(g.w, v.ip[k], ta);
     }
-    t0 = fmaxf(fmaxf(en[0], en[1]), en[2]);
-    t1 = fminf(fminf(ex[0], ex[1]), ex[2]);
+    t0 = max3f(en[0], en[1], en[2]);
+    t1 = min3f(ex[0], ex[1], ex[2]);
     return t0 < t1;
 }
 
@@ -301,11 +335,9 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Batch
                                              uint32_t wbit, const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
                                              const float* dc, float* grad_rec) {
     const OctParams& P = vo[it.o];
-    float d[3], inv[3];
+    float d[3];
     rotate(P.A, dc, d);
-    inv[0] = 1.0f / d[0];
-    inv[1] = 1.0f / d[1];
-    inv[2] = 1.0f / d[2];
+    const InvDir inv = inv_dir(d);
     for (uint32_t q = q0; q < q1 && !ps.done; ++q) {
         if (!(__ldg(pmask + q) & wbit)) continue;
         ps.tests += 1;
@@ -366,13 +398,16 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     __shared__ float4 s_rec[2][CT_THREADS][4];
     __shared__ uint32_t s_r[2][CT_THREADS];
     __shared__ uint8_t s_m[2][CT_THREADS];
-    __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];
+    __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];  // sub-list of octree o: [s_sub[o], s_sub[o+1])
+    __shared__ uint32_t s_vs[DV_MAX_OCTREES + 1];   // first record of octree o in this view
+    __shared__ bool s_flag[DV_MAX_OCTREES];         // actor o's box covers this tile
     __shared__ int16_t s_act[DV_MAX_OCTREES];
     __shared__ float s_iv[NTA][2][CT_THREADS];
     __shared__ float s_st[NTA][6][CT_THREADS];
     __shared__ int s_nact;
 
-    const int gtile = (int)tile_order[blockIdx.x >> 1];
+    const int tid = threadIdx.x;
+    const int gtile = (int)__ldg(tile_order + (blockIdx.x >> 1));
     const int half = blockIdx.x & 1;
     int view = 0;
     {
@@ -388,35 +423,13 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     }
     const ViewParams& fp = bp.views[view];
     const OctParams* __restrict__ vo = bp.octs + view * bp.n_oct;
+    const int n_oct = bp.n_oct;
     const int tiles_x = fp.tiles_x, W = fp.W, H = fp.H;
     const float t_near = fp.near_, t_far = fp.far_;
     const int tile = gtile - bp.tile_base[view];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const uint2 rg = tile_range[gtile];
-    const int tid = threadIdx.x;
-    if (tid <= bp.n_oct) {
-        const uint32_t key = vis_start[view * bp.n_oct + tid];
-        uint32_t lo = rg.x, hi = rg.y;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(pval + mid) < key)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        s_sub[tid] = lo;
-    }
-    if (tid == 0) {
-        int n = 0;
-        for (int o = 1; o < bp.n_oct; ++o) {
-            const OctParams& P = vo[o];
-            if (P.role == DV_ROLE_ACTOR && P.rect[0] <= tx && tx <= P.rect[2] && P.rect[1] <= ty && ty <= P.rect[3])
-                s_act[n++] = (int16_t)o;
-        }
-        s_nact = n;
-    }
-    __syncthreads();
-
+    const uint2 rg = __ldg(tile_range + gtile);
+    // per-pixel set-up first: its loads overlap the tile set-up below
     const int lane = tid & 31, warp = tid >> 5;
     const uint32_t wbit = 1u << ((half * 2 + (warp >> 1)) * 2 + (warp & 1));  // this warp's 8x4 block
     const int u = tx * DV_TILE + (warp & 1) * 8 + (lane & 7);
@@ -435,11 +448,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         dc[2] = in;
     }
     const OctParams& B = vo[0];
-    float db_[3], ib[3];
+    float db_[3];
     rotate(B.A, dc, db_);
-    ib[0] = 1.0f / db_[0];
-    ib[1] = 1.0f / db_[1];
-    ib[2] = 1.0f / db_[2];
+    const InvDir ib = inv_dir(db_);
 
     Pix ps;
     ps.C0 = ps.C1 = ps.C2 = ps.D = 0.0f;
@@ -464,6 +475,58 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         bw.g0 = bw.g1 = bw.g2 = bw.gD = bw.gA = 0.0f;
         bw.Cf0 = bw.Cf1 = bw.Cf2 = bw.Df = bw.Tend = 0.0f;
     }
+    // tile set-up, all loads independent of one another: the view's octree boundaries in
+    // the record order, and which actor boxes cover this tile
+    for (int i = tid; i <= n_oct; i += CT_THREADS) s_vs[i] = __ldg(vis_start + view * n_oct + i);
+    for (int o = tid; o < n_oct; o += CT_THREADS) {
+        const OctParams& P = vo[o];
+        s_flag[o] = o > 0 && P.role == DV_ROLE_ACTOR && P.rect[0] <= tx && tx <= P.rect[2] && P.rect[1] <= ty &&
+                    ty <= P.rect[3];
+    }
+    __syncthreads();
+    // the tile's list is grouped by octree (records are in depth-key order, octree above
+    // the BSP path), so octree o's sub-list starts at the first entry whose record is at
+    // or after s_vs[o]; entry q finds its octree by a search of s_vs and marks the starts
+    // of the octrees between its predecessor's and its own
+    {
+        auto oct_of = [&](uint32_t r) {
+            int lo = 0, hi = n_oct - 1;  // largest o with s_vs[o] <= r
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_vs[mid] <= r)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            return lo;
+        };
+        for (uint32_t base = rg.x; base < rg.y; base += CT_THREADS) {
+            const uint32_t q = base + tid;
+            if (q < rg.y) {
+                const int o = oct_of(__ldg(pval + q));
+                const int op = q > rg.x ? oct_of(__ldg(pval + q - 1)) : -1;
+                for (int x = op + 1; x <= o; ++x) s_sub[x] = q;
+                if (q + 1 == rg.y)
+                    for (int x = o + 1; x <= n_oct; ++x) s_sub[x] = rg.y;
+            }
+        }
+        if (rg.x == rg.y)
+            for (int i = tid; i <= n_oct; i += CT_THREADS) s_sub[i] = rg.x;
+    }
+    if (tid < 32) {
+        // actor list of the tile in octree order (warp 0, ballot compaction)
+        int n = 0;
+        for (int o0 = 0; o0 < n_oct; o0 += 32) {
+            const int o = o0 + tid;
+            const bool f = o < n_oct && s_flag[o];
+            const unsigned b = __ballot_sync(0xffffffffu, f);
+            if (f) s_act[n + __popc(b & ((1u << tid) - 1u))] = (int16_t)o;
+            n += __popc(b);
+        }
+        if (tid == 0) s_nact = n;
+    }
+    __syncthreads();
+
     const int n_ta = s_nact;
     const int n_lock = n_ta < NTA ? n_ta : NTA;
 
@@ -554,11 +617,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     auto walk_actor = [&](Pix& pt, int o, float a, float b, auto grad) {
         constexpr bool G = decltype(grad)::value;
         const OctParams& P = vo[o];
-        float d[3], inv[3];
+        float d[3];
         rotate(P.A, dc, d);
-        inv[0] = 1.0f / d[0];
-        inv[1] = 1.0f / d[1];
-        inv[2] = 1.0f / d[2];
+        const InvDir inv = inv_dir(d);
         stream(s_sub[o], s_sub[o + 1], [&](int slot, uint32_t c0, unsigned m) -> bool {
             while (m) {
                 if (__all_sync(0xffffffffu, pt.done)) return true;

@@ -144,3 +144,11 @@ def test_batched_views_backward(dv):
         off += n
     check_grads([x.cpu().numpy() for x in d_dens], ref_d, "batched d_dens")
     check_grads([x.cpu().numpy() for x in d_sh], ref_s, "batched d_sh")
+
+
+def test_maximum_octree_count_gradients(dv):
+    sc = small_comp_scene(seed=22, n_actors=127)
+    cams = [orbit(40, 32, 120.0, 20.0)]
+    rng = np.random.default_rng(22)
+    _compare(sc, cams, rng.normal(size=(32, 40, 3)), rng.normal(size=(32, 40)) * 0.2, rng.normal(size=(32, 40)), 1,
+             1e-4, what="128 octrees")

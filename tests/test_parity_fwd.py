@@ -144,3 +144,26 @@ def test_batched_views_with_their_own_poses(dv):
         torch.cuda.synchronize()
         np.testing.assert_allclose(r1.cpu().numpy().reshape(cam.H, cam.W, 3), gr[k], atol=1e-6)
         np.testing.assert_allclose(a1.cpu().numpy().reshape(cam.H, cam.W), ga[k], atol=1e-6)
+
+
+def test_maximum_octree_count_many_actors_per_tile(dv):
+    # 1 background + 127 actors (the most one call takes): most tiles see more actor boxes than
+    # the lockstep slots, so the per-lane actor walk runs as well
+    sc = small_comp_scene(seed=21, n_actors=127)
+    assert len(sc.octrees) == 128
+    cams = [orbit(48, 40, 35.0, 25.0)]
+    _compare_full(sc, cams, 1, 1e-4, what="128 octrees")
+
+
+def test_axis_parallel_rays(dv):
+    # camera axes exactly along the grid axes (x right = +x, y down = +y, z forward = +z) with the
+    # principal point on a pixel centre: the middle row and column of pixels have ray direction
+    # components that are exactly zero, i.e. rays parallel to voxel slabs, some starting inside
+    # a slab (the camera sits inside the grid's x and y extent)
+    sc = small_comp_scene(seed=23, n_actors=0)
+    W = H = 33
+    fx = 20.0
+    pose = synth.Pose(np.eye(3), np.array([0.13, -0.21, -1.9]))
+    cam = synth.Camera(W, H, fx, fx, 16.5, 16.5, pose, 0.05, 20.0)
+    gr, ga = _compare_full(sc, [cam], 2, 1e-4, what="axis-parallel rays")
+    assert ga[0][16, :].max() > 0.5 and ga[0][:, 16].max() > 0.5
