@@ -43,6 +43,7 @@ struct dv_ctx {
     std::string err;
     uint64_t* h_scalars = nullptr;  // pinned: [0] n_vis, [1] n_pairs, [2] flags
     uint64_t* d_scalars = nullptr;  // device mirror
+    cudaEvent_t ev_sizes = nullptr;  // the scalars have reached the host
     bool profiling = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> spare;
@@ -462,22 +463,23 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         ar.release();
         return cuda_fail(ctx, ar.err, "allocate scratch");
     }
-    uint64_t* d_nvis = ctx->d_scalars;
-    uint64_t* d_npairs = ctx->d_scalars + 1;
     uint32_t* d_flags = (uint32_t*)(ctx->d_scalars + 2);
     e = cudaMemsetAsync(ctx->d_scalars, 0, 3 * sizeof(uint64_t), s);
     {
         Prof p(ctx, KP_PROJECT, s);
-        if (e == cudaSuccess) e = launch_project(bp, cnt, rect, skey, vis, d_flags, s);
+        if (e == cudaSuccess)
+            e = launch_project(bp, cnt, rect, skey, vis, d_flags, (unsigned long long*)ctx->d_scalars, s);
     }
-    {
-        Prof p(ctx, KP_SCAN, s);
-        if (e == cudaSuccess) e = scan_u32_to_u32(vis, pos, NT, (uint32_t*)d_nvis, ar, s);
-        if (e == cudaSuccess) e = scan_u32_to_u64(cnt, nullptr, NT, d_npairs, ar, s);
-    }
+    // the sizes of everything below come back to the host while the GPU runs the
+    // visibility scan, which needs none of them
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_scalars, ctx->d_scalars, 3 * sizeof(uint64_t),
                                               cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_sizes, s);
+    {
+        Prof p(ctx, KP_SCAN, s);
+        if (e == cudaSuccess) e = scan_u32_to_u32(vis, pos, NT, nullptr, ar, s);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_sizes);
     if (e != cudaSuccess) {
         ar.release();
         return cuda_fail(ctx, e, "project");
@@ -636,6 +638,12 @@ dv_status dv_create(dv_ctx** out, int32_t device) {
         cudaMemPoolDestroy(ctx->pool);
         return DV_ERR_NOMEM;
     }
+    if (cudaEventCreateWithFlags(&ctx->ev_sizes, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(ctx->d_scalars);
+        cudaFreeHost(ctx->h_scalars);
+        cudaMemPoolDestroy(ctx->pool);
+        return DV_ERR_CUDA;
+    }
     *out = ctx.release();
     return DV_OK;
 }
@@ -649,6 +657,7 @@ void dv_destroy(dv_ctx* ctx) {
         cudaEventDestroy(r.b);
     }
     for (auto e : ctx->spare) cudaEventDestroy(e);
+    cudaEventDestroy(ctx->ev_sizes);
     cudaFree(ctx->d_scalars);
     cudaFreeHost(ctx->h_scalars);
     cudaMemPoolDestroy(ctx->pool);

@@ -931,15 +931,28 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
     const float* gr = grad_rec + (size_t)r * GSTRIDE;
     float* d_dens = sp.d_dens[lo];
     float* d_sh = sp.d_sh[lo];
-    // several views may touch the same voxel: accumulate with atomics
+    // several views may touch the same voxel: accumulate with atomics (16-byte vector
+    // atomics where the caller's rows are 16-byte aligned)
+    const float4 g03 = *reinterpret_cast<const float4*>(gr), g47 = *reinterpret_cast<const float4*>(gr + 4);
     if (d_dens) {
         float* dd = d_dens + v * 8;
+        if ((reinterpret_cast<uintptr_t>(dd) & 15) == 0) {
+            if (g03.x != 0.0f || g03.y != 0.0f || g03.z != 0.0f || g03.w != 0.0f)
+                atomicAdd(reinterpret_cast<float4*>(dd), g03);
+            if (g47.x != 0.0f || g47.y != 0.0f || g47.z != 0.0f || g47.w != 0.0f)
+                atomicAdd(reinterpret_cast<float4*>(dd) + 1, g47);
+        } else {
+            const float gd[8] = {g03.x, g03.y, g03.z, g03.w, g47.x, g47.y, g47.z, g47.w};
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (gr[c] != 0.0f) atomicAdd(dd + c, gr[c]);
+            for (int c = 0; c < 8; ++c)
+                if (gd[c] != 0.0f) atomicAdd(dd + c, gd[c]);
+        }
     }
-    const float gc0 = gr[8], gc1 = gr[9], gc2 = gr[10];
-    if (!d_sh || (gc0 == 0.0f && gc1 == 0.0f && gc2 == 0.0f)) return;
+    // colour channels clamped at zero in the forward (stored clamped in the record) pass no
+    // gradient to the SH coefficients
+    const float4 col = rec[r].v[3];
+    const float m0 = col.x > 0.0f ? gr[8] : 0.0f, m1 = col.y > 0.0f ? gr[9] : 0.0f, m2 = col.z > 0.0f ? gr[10] : 0.0f;
+    if (!d_sh || (m0 == 0.0f && m1 == 0.0f && m2 == 0.0f)) return;
     const float4 g = rec[r].v[0];  // (min - camera centre, size): same direction as the records kernel
     float gx = fmaf(0.5f, g.w, g.x);
     float gy = fmaf(0.5f, g.w, g.y);
@@ -952,19 +965,27 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
     float b[16];
     sh_basis_f(P.sh_degree, gx, gy, gz, b);
     const int nsh = (P.sh_degree + 1) * (P.sh_degree + 1);
-    const float* shv = P.sh + v * nsh * 3;
-    float c0 = 0.5f, c1 = 0.5f, c2 = 0.5f;
-    for (int q = 0; q < nsh; ++q) {
-        c0 = fmaf(b[q], shv[q * 3 + 0], c0);
-        c1 = fmaf(b[q], shv[q * 3 + 1], c1);
-        c2 = fmaf(b[q], shv[q * 3 + 2], c2);
-    }
-    const float m0 = c0 > 0.0f ? gc0 : 0.0f, m1 = c1 > 0.0f ? gc1 : 0.0f, m2 = c2 > 0.0f ? gc2 : 0.0f;
     float* ds = d_sh + v * nsh * 3;
-    for (int q = 0; q < nsh; ++q) {
-        if (m0 != 0.0f) atomicAdd(ds + q * 3 + 0, b[q] * m0);
-        if (m1 != 0.0f) atomicAdd(ds + q * 3 + 1, b[q] * m1);
-        if (m2 != 0.0f) atomicAdd(ds + q * 3 + 2, b[q] * m2);
+    if ((nsh * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(ds) & 15) == 0) {
+        // coefficient rows (q, channel) flattened: element e = 3 q + channel
+        const float m[3] = {m0, m1, m2};
+#pragma unroll
+        for (int e0 = 0; e0 < 48; e0 += 4) {
+            if (e0 >= nsh * 3) break;
+            float x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = e0 + i;
+                x[i] = b[e / 3] * m[e % 3];
+            }
+            atomicAdd(reinterpret_cast<float4*>(ds + e0), make_float4(x[0], x[1], x[2], x[3]));
+        }
+    } else {
+        for (int q = 0; q < nsh; ++q) {
+            if (m0 != 0.0f) atomicAdd(ds + q * 3 + 0, b[q] * m0);
+            if (m1 != 0.0f) atomicAdd(ds + q * 3 + 1, b[q] * m1);
+            if (m2 != 0.0f) atomicAdd(ds + q * 3 + 2, b[q] * m2);
+        }
     }
 }
 

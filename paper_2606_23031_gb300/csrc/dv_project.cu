@@ -79,11 +79,11 @@ __device__ __forceinline__ void proj_point(const ViewParams& fp, float x, float 
     v1 = fmaxf(v1, v);
 }
 
-__global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParams bp, uint32_t* __restrict__ cnt,
-                                                 uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
-                                                 uint32_t* __restrict__ vis, uint32_t* __restrict__ flags) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // view * n_vox + voxel
-    if (g >= bp.n_vox * bp.n_view) return;
+// Projection of (view, voxel) g; sets cnt[g], vis[g] (and rect[g], skey[g] when visible)
+// and returns the tile count (0: not visible).
+__device__ __forceinline__ uint32_t project_voxel(const BatchParams& bp, int64_t g, uint32_t* __restrict__ cnt,
+                                                  uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
+                                                  uint32_t* __restrict__ vis, uint32_t* __restrict__ flags) {
     const int view = (int)(g / bp.n_vox);
     const int64_t gv = g - (int64_t)view * bp.n_vox;
     const int o = find_octree(bp, gv);
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     const Leaf L = decode_leaf(P, key);
     if (L.level > P.max_level || L.i >> L.level || L.j >> L.level || L.k >> L.level) {
         atomicOr(flags, DV_FLAG_BAD_LEVEL);
-        return;
+        return 0;
     }
     // corners in the camera frame: p = M (mn + s*offset) + m
     float p0[3], e[3][3];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
         zmin = fminf(zmin, z);
         zmax = fmaxf(zmax, z);
     }
-    if (zmax < fp.z_clip || zmin > fp.far_) return;
+    if (zmax < fp.z_clip || zmin > fp.far_) return 0;
     float u0 = INFINITY, u1 = -INFINITY, w0 = INFINITY, w1 = -INFINITY;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -149,9 +149,10 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     const float lv = fmaxf(w0 - 0.5f - mv, -1.0f), hv = fminf(w1 - 0.5f + mv, (float)fp.H + 1.0f);
     const int pu0 = max((int)ceilf(lu), 0), pu1 = min((int)floorf(hu), fp.W - 1);
     const int pv0 = max((int)ceilf(lv), 0), pv1 = min((int)floorf(hv), fp.H - 1);
-    if (!(pu0 <= pu1 && pv0 <= pv1)) return;
+    if (!(pu0 <= pu1 && pv0 <= pv1)) return 0;
     const uint32_t tx0 = pu0 >> 4, tx1 = pu1 >> 4, ty0 = pv0 >> 4, ty1 = pv1 >> 4;
-    cnt[g] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    const uint32_t n_tiles = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    cnt[g] = n_tiles;
     vis[g] = 1;
     // pixel rectangle (tiles are its pixels >> 4)
     rect[g] = (uint64_t)pu0 | ((uint64_t)pu1 << 16) | ((uint64_t)pv0 << 32) | ((uint64_t)pv1 << 48);
@@ -171,6 +172,39 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     }
     bsp <<= 3 * (Lk - L.level);
     skey[g] = ((uint64_t)view << bp.view_shift) | ((uint64_t)o << bp.oct_shift) | bsp;
+    return n_tiles;
+}
+
+// One thread per (view, voxel); the block's visible voxels and (tile, voxel) pairs are
+// added to totals[0] and totals[1], so the host learns both sizes from this kernel alone.
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParams bp, uint32_t* __restrict__ cnt,
+                                                 uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
+                                                 uint32_t* __restrict__ vis, uint32_t* __restrict__ flags,
+                                                 unsigned long long* __restrict__ totals) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // view * n_vox + voxel
+    uint32_t c = 0;
+    if (g < bp.n_vox * bp.n_view) c = project_voxel(bp, g, cnt, rect, skey, vis, flags);
+    unsigned long long nv = c ? 1ull : 0ull, np = c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        nv += __shfl_down_sync(0xffffffffu, nv, off);
+        np += __shfl_down_sync(0xffffffffu, np, off);
+    }
+    __shared__ unsigned long long s_nv[8], s_np[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_nv[warp] = nv;
+        s_np[warp] = np;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            nv += s_nv[w];
+            np += s_np[w];
+        }
+        if (nv) atomicAdd(totals + 0, nv);
+        if (np) atomicAdd(totals + 1, np);
+    }
 }
 
 __global__ void k_compact(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ pos,
@@ -241,12 +275,25 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
     sh_eval_basis(P.sh_degree, gx, gy, gz, b);
     const int nsh = (P.sh_degree + 1) * (P.sh_degree + 1);
     const float* shv = P.sh + v * nsh * 3;
-    float c0 = 0.5f, c1 = 0.5f, c2 = 0.5f;
-    for (int q = 0; q < nsh; ++q) {
-        c0 = fmaf(b[q], __ldg(shv + q * 3 + 0), c0);
-        c1 = fmaf(b[q], __ldg(shv + q * 3 + 1), c1);
-        c2 = fmaf(b[q], __ldg(shv + q * 3 + 2), c2);
+    float cc[3] = {0.5f, 0.5f, 0.5f};
+    if ((nsh * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(shv) & 15) == 0) {
+        // 16-byte loads of the coefficient rows, flattened: element e = 3 q + channel
+#pragma unroll
+        for (int e0 = 0; e0 < 48; e0 += 4) {
+            if (e0 >= nsh * 3) break;
+            const float4 x4 = __ldg(reinterpret_cast<const float4*>(shv + e0));
+            const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cc[(e0 + i) % 3] = fmaf(b[(e0 + i) / 3], xs[i], cc[(e0 + i) % 3]);
+        }
+    } else {
+        for (int q = 0; q < nsh; ++q) {
+            cc[0] = fmaf(b[q], __ldg(shv + q * 3 + 0), cc[0]);
+            cc[1] = fmaf(b[q], __ldg(shv + q * 3 + 1), cc[1]);
+            cc[2] = fmaf(b[q], __ldg(shv + q * 3 + 2), cc[2]);
+        }
     }
+    const float c0 = cc[0], c1 = cc[1], c2 = cc[2];
     VoxRec R;
     R.v[0] = make_float4(rx, ry, rz, L.s);
     R.v[1] = da;
@@ -405,10 +452,10 @@ cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* sc
 }
 
 cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
-                           uint32_t* flags, cudaStream_t s) {
+                           uint32_t* flags, unsigned long long* totals, cudaStream_t s) {
     const int64_t n = bp.n_vox * bp.n_view;
     if (n <= 0) return cudaSuccess;
-    k_project<<<nblk(n, 256), 256, 0, s>>>(bp, cnt, rect, skey, vis, flags);
+    k_project<<<nblk(n, 256), 256, 0, s>>>(bp, cnt, rect, skey, vis, flags, totals);
     count_launches(1);
     return cudaGetLastError();
 }

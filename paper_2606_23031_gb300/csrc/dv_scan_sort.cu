@@ -395,10 +395,9 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
     }
 }
 
-template <typename K>
+template <typename K, int ROUNDS>
 cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits,
                           Arena& ar, cudaStream_t s) {
-    constexpr int ROUNDS = 8;
     const int passes = (n_bits + 7) / 8;
     const int64_t tile = (int64_t)OS_THREADS * ROUNDS;
     const int64_t n_tiles = (n + tile - 1) / tile;
@@ -440,6 +439,18 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
     return cudaGetLastError();
 }
 
+// Keys per tile: 256 x ROUNDS, the most that still gives every SM two or more tiles (a
+// pass's time is one tile's ranking plus the look-back, so small sorts want small tiles).
+template <typename K>
+cudaError_t onesweep(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits, Arena& ar,
+                     cudaStream_t s) {
+    const int64_t per_round = (int64_t)OS_THREADS * 2 * 152;
+    if (n <= per_round) return onesweep_impl<K, 1>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+    if (n <= 2 * per_round) return onesweep_impl<K, 2>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+    if (n <= 4 * per_round) return onesweep_impl<K, 4>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+    return onesweep_impl<K, 8>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+}
+
 }  // namespace
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
@@ -457,7 +468,7 @@ cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt,
                            int n_bits, Arena& ar, cudaStream_t s) {
     if (n <= 1 || n_bits <= 0) return cudaSuccess;
     if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
-        return onesweep_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+        return onesweep<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
     return radix_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 
@@ -465,7 +476,7 @@ cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt,
                            int n_bits, Arena& ar, cudaStream_t s) {
     if (n <= 1 || n_bits <= 0) return cudaSuccess;
     if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
-        return onesweep_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+        return onesweep<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
     return radix_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 
