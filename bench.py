@@ -171,9 +171,14 @@ def stage_models(stats, work, n_vox_total, n_pix, K, sh_bytes_per_vox, key_bits)
     }
 
 
+# the sources that decide the compositing kernels' DRAM traffic: the kernels themselves, the
+# record layout and the kernel that writes the records
+TRAFFIC_SOURCES = ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2606_23031_gb300", "csrc"))):
+    for f in TRAFFIC_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2606_23031_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
