@@ -136,9 +136,10 @@ def _threads(n):
     return int(n) if n else (os.cpu_count() or 1)
 
 
-def render(octrees, poses, cam, opts: Opts = Opts(), pixels=None, n_threads=None, f64_arrays=None):
+def render(octrees, poses, cam, opts: Opts = Opts(), pixels=None, n_threads=None, f64_arrays=None, normals=False):
     """Returns (rgb [n,3], depth [n], alpha [n], n_seg [n]) in float64 for the given linear pixel
-    indices (v*W+u), or the whole image ([H,W,...]) when ``pixels`` is None."""
+    indices (v*W+u), or the whole image ([H,W,...]) when ``pixels`` is None; with ``normals`` the
+    normal state N [n,3] (world frame) is appended."""
     lib = _load()
     m = _Marshal(octrees, poses, cam, opts, f64_arrays)
     if pixels is None:
@@ -152,22 +153,25 @@ def render(octrees, poses, cam, opts: Opts = Opts(), pixels=None, n_threads=None
     depth = np.zeros(n)
     alpha = np.zeros(n)
     nseg = np.zeros(n, np.int32)
+    nrm = np.zeros((n, 3)) if normals else None
     st = lib.orc_render(m.oct, C.c_int(m.n), m.poses, C.byref(m.cam), C.byref(m.opts), C.c_int64(n),
                         C.c_void_p(pix_ptr), rgb.ctypes.data_as(C.c_void_p), depth.ctypes.data_as(C.c_void_p),
                         alpha.ctypes.data_as(C.c_void_p), nseg.ctypes.data_as(C.c_void_p),
-                        C.c_int(_threads(n_threads)))
+                        C.c_int(_threads(n_threads)), C.c_void_p(nrm.ctypes.data if normals else None))
     if st != 0:
         raise RuntimeError(f"orc_render failed with status {st}")
     if pixels is None:
-        return (rgb.reshape(cam.H, cam.W, 3), depth.reshape(cam.H, cam.W), alpha.reshape(cam.H, cam.W),
-                nseg.reshape(cam.H, cam.W))
-    return rgb, depth, alpha, nseg
+        out = (rgb.reshape(cam.H, cam.W, 3), depth.reshape(cam.H, cam.W), alpha.reshape(cam.H, cam.W),
+               nseg.reshape(cam.H, cam.W))
+        return out + (nrm.reshape(cam.H, cam.W, 3),) if normals else out
+    return (rgb, depth, alpha, nseg, nrm) if normals else (rgb, depth, alpha, nseg)
 
 
 def backward(octrees, poses, cam, g_rgb, g_depth, g_alpha, opts: Opts = Opts(), pixels=None, n_threads=None,
-             f64_arrays=None):
+             f64_arrays=None, g_normal=None):
     """Analytic FP64 gradients (list of d_dens [V,8], list of d_sh [V,nsh,3]) for upstream
-    gradients given per pixel (same pixel convention as :func:`render`)."""
+    gradients given per pixel (same pixel convention as :func:`render`); ``g_normal`` [n,3] is
+    dL/dN (None: zero)."""
     lib = _load()
     m = _Marshal(octrees, poses, cam, opts, f64_arrays)
     if pixels is None:
@@ -180,6 +184,7 @@ def backward(octrees, poses, cam, g_rgb, g_depth, g_alpha, opts: Opts = Opts(), 
     g_rgb = np.ascontiguousarray(np.asarray(g_rgb, np.float64).reshape(n, 3))
     g_depth = np.ascontiguousarray(np.asarray(g_depth, np.float64).reshape(n))
     g_alpha = np.ascontiguousarray(np.asarray(g_alpha, np.float64).reshape(n))
+    g_nrm = None if g_normal is None else np.ascontiguousarray(np.asarray(g_normal, np.float64).reshape(n, 3))
     d_dens = [np.zeros((oc.n, 8)) for oc in octrees]
     d_sh = [np.zeros((oc.n, (oc.sh_degree + 1) ** 2, 3)) for oc in octrees]
     pd = (C.c_void_p * max(len(octrees), 1))(*[a.ctypes.data for a in d_dens])
@@ -187,7 +192,7 @@ def backward(octrees, poses, cam, g_rgb, g_depth, g_alpha, opts: Opts = Opts(), 
     st = lib.orc_backward(m.oct, C.c_int(m.n), m.poses, C.byref(m.cam), C.byref(m.opts), C.c_int64(n),
                           C.c_void_p(pix_ptr), g_rgb.ctypes.data_as(C.c_void_p),
                           g_depth.ctypes.data_as(C.c_void_p), g_alpha.ctypes.data_as(C.c_void_p), pd, ps,
-                          C.c_int(_threads(n_threads)))
+                          C.c_int(_threads(n_threads)), C.c_void_p(None if g_nrm is None else g_nrm.ctypes.data))
     if st != 0:
         raise RuntimeError(f"orc_backward failed with status {st}")
     return d_dens, d_sh

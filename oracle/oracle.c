@@ -34,7 +34,11 @@
  *   colour = max(0, sum_lm Y_lm(g) k_lm + 0.5) with g the unit direction from
  *   the camera centre to the voxel centre in the octree's local frame;
  *   overlapping actor boxes: the box entered first owns the overlap;
- *   the garbled "D = 1" of Alg. 1's initial state is read as T = 1.
+ *   the garbled "D = 1" of Alg. 1's initial state is read as T = 1;
+ *   the normal state N of Alg. 1 (Sec. 3.4: N aggregates voxel normals) is
+ *   N = sum_k T_k alpha_k n_k with n the voxel's normal in world coordinates:
+ *   minus the normalised gradient of the voxel's trilinear raw density at its
+ *   centre, rotated by the octree's pose (zero where that gradient is zero).
  *
  * Backward: analytic reverse sweep of the same composite (chain rule through
  * C, D and alpha = 1 - T_final), accumulated into FP64 gradient arrays.
@@ -358,7 +362,32 @@ static int gather(const orc_octree* oct, int n_oct, const orc_pose* poses, const
 typedef struct {
     double tau, alpha, rgb[3], pre[3], mid, g[3];
     double dtau_ddens[8];
+    double nrm[3]; /* voxel normal, world frame */
 } seg_eval;
+
+/* Gradient of the trilinear raw density of voxel v at its centre, in units of
+ * one corner-density difference per voxel edge times 4: component a is the sum
+ * of the four corners on the high side of axis a minus the four on the low
+ * side.  (The true gradient is this divided by 4 * size; only its direction is
+ * used.) */
+static void dens_gradient(const orc_octree* oc, int64_t v, double g[3]) {
+    for (int a = 0; a < 3; ++a) {
+        g[a] = 0.0;
+        for (int c = 0; c < 8; ++c) g[a] += ((c >> a) & 1) ? get_dens(oc, v, c) : -get_dens(oc, v, c);
+    }
+}
+
+/* Voxel normal: n_local = -g / |g| (0 if g = 0), then n_world = R n_local. */
+static void voxel_normal(const orc_octree* oc, const orc_pose* P, int64_t v, double n_loc[3], double n_world[3],
+                         double* gnorm) {
+    double g[3];
+    dens_gradient(oc, v, g);
+    double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    for (int a = 0; a < 3; ++a) n_loc[a] = gn > 0.0 ? -g[a] / gn : 0.0;
+    for (int r = 0; r < 3; ++r)
+        n_world[r] = P->R[r * 3 + 0] * n_loc[0] + P->R[r * 3 + 1] * n_loc[1] + P->R[r * 3 + 2] * n_loc[2];
+    *gnorm = gn;
+}
 
 static void eval_segment(const orc_octree* oc, const orc_pose* P, const double o[3], const double d[3],
                          const segment* sg, const orc_opts* opt, seg_eval* e) {
@@ -410,6 +439,8 @@ static void eval_segment(const orc_octree* oc, const orc_pose* P, const double o
         e->pre[ch] = c;
         e->rgb[ch] = c > 0.0 ? c : 0.0;
     }
+    double n_loc[3], grad_norm;
+    voxel_normal(oc, P, sg->vox, n_loc, e->nrm, &grad_norm);
 }
 
 /* ------------------------------------------------------------------ */
@@ -424,9 +455,9 @@ typedef struct {
     const orc_opts* opt;
     int64_t n_pix;
     const int64_t* pix;
-    double *rgb, *depth, *alpha;
+    double *rgb, *depth, *alpha, *normal;
     int32_t* n_seg;
-    const double *g_rgb, *g_depth, *g_alpha;
+    const double *g_rgb, *g_depth, *g_alpha, *g_normal;
     /* backward: per-thread records */
     int tid, n_threads;
     int status;
@@ -441,6 +472,7 @@ struct grad_rec {
     double g_rgb[3];
     double pre[3];
     double g[3];
+    double g_nrm[3]; /* dL/d(voxel normal, world frame) from this segment */
 };
 
 static int64_t pixel_index(const job* J, int64_t p) { return J->pix ? J->pix[p] : p; }
@@ -456,7 +488,7 @@ static void* fwd_worker(void* arg) {
             J->status = ORC_ENOMEM;
             break;
         }
-        double C[3] = {0, 0, 0}, D = 0.0, T = 1.0;
+        double C[3] = {0, 0, 0}, D = 0.0, T = 1.0, N[3] = {0, 0, 0};
         int32_t used = 0;
         for (int64_t k = 0; k < L.n; ++k) {
             seg_eval e;
@@ -464,6 +496,7 @@ static void* fwd_worker(void* arg) {
             eval_segment(&J->oct[sg->oct], &J->poses[sg->oct], o, d, sg, J->opt, &e);
             double w = T * e.alpha;
             for (int ch = 0; ch < 3; ++ch) C[ch] += w * e.rgb[ch];
+            for (int a = 0; a < 3; ++a) N[a] += w * e.nrm[a];
             D += w * e.mid;
             T *= (1.0 - e.alpha);
             ++used;
@@ -473,6 +506,8 @@ static void* fwd_worker(void* arg) {
         J->depth[p] = D;
         J->alpha[p] = 1.0 - T;
         if (J->n_seg) J->n_seg[p] = used;
+        if (J->normal)
+            for (int a = 0; a < 3; ++a) J->normal[p * 3 + a] = N[a];
     }
     free(L.s);
     return NULL;
@@ -515,10 +550,11 @@ static int run_jobs(job* base, int n_threads, void* (*fn)(void*), job** out) {
 
 /* Forward render of `n_pix` pixels (linear index v*W+u; pix == NULL means all
  * W*H pixels in order).  Outputs rgb[n][3], depth[n], alpha[n] and, if
- * non-NULL, the number of composited segments per pixel. */
+ * non-NULL, the number of composited segments per pixel and the normal state
+ * normal[n][3] (world frame). */
 int orc_render(const orc_octree* oct, int n_oct, const orc_pose* poses, const orc_camera* cam, const orc_opts* opt,
                int64_t n_pix, const int64_t* pix, double* rgb, double* depth, double* alpha, int32_t* n_seg,
-               int n_threads) {
+               int n_threads, double* normal) {
     int st = check_inputs(oct, n_oct, cam, opt);
     if (st != ORC_OK) return st;
     if (!pix) n_pix = (int64_t)cam->W * cam->H;
@@ -535,6 +571,7 @@ int orc_render(const orc_octree* oct, int n_oct, const orc_pose* poses, const or
     base.depth = depth;
     base.alpha = alpha;
     base.n_seg = n_seg;
+    base.normal = normal;
     return run_jobs(&base, n_threads, fwd_worker, NULL);
 }
 
@@ -591,8 +628,11 @@ static void* bwd_worker(void* arg) {
         double Tend = T;
         const double* gC = &J->g_rgb[p * 3];
         double gD = J->g_depth[p], gA = J->g_alpha[p];
+        double gN[3] = {0, 0, 0};
+        if (J->g_normal)
+            for (int a = 0; a < 3; ++a) gN[a] = J->g_normal[p * 3 + a];
         /* reverse sweep: R = contribution of everything behind segment k */
-        double RC[3] = {0, 0, 0}, RD = 0.0;
+        double RC[3] = {0, 0, 0}, RD = 0.0, RN[3] = {0, 0, 0};
         for (int64_t k = n - 1; k >= 0; --k) {
             const seg_eval* e = &E[k];
             double Tn = Tb[k] * (1.0 - e->alpha); /* T after segment k */
@@ -600,6 +640,7 @@ static void* bwd_worker(void* arg) {
             double gtau = gA * Tend;
             for (int ch = 0; ch < 3; ++ch) gtau += gC[ch] * (Tn * e->rgb[ch] - RC[ch]);
             gtau += gD * (Tn * e->mid - RD);
+            for (int a = 0; a < 3; ++a) gtau += gN[a] * (Tn * e->nrm[a] - RN[a]);
             struct grad_rec r;
             r.oct = L.s[k].oct;
             r.vox = L.s[k].vox;
@@ -608,6 +649,7 @@ static void* bwd_worker(void* arg) {
                 r.g_rgb[ch] = gC[ch] * w;
                 r.pre[ch] = e->pre[ch];
                 r.g[ch] = e->g[ch];
+                r.g_nrm[ch] = gN[ch] * w;
             }
             if (push_rec(J, &r) != ORC_OK) {
                 J->status = ORC_ENOMEM;
@@ -615,6 +657,7 @@ static void* bwd_worker(void* arg) {
             }
             for (int ch = 0; ch < 3; ++ch) RC[ch] += w * e->rgb[ch];
             RD += w * e->mid;
+            for (int a = 0; a < 3; ++a) RN[a] += w * e->nrm[a];
         }
         free(Tb);
         if (J->status != ORC_OK) break;
@@ -626,11 +669,13 @@ static void* bwd_worker(void* arg) {
 
 /* Gradients of L w.r.t. every corner density and SH coefficient, given dL/dC,
  * dL/dD and dL/dalpha for `n_pix` pixels (same pixel convention as
- * orc_render).  d_dens[i] ([n][8]) and d_sh[i] ([n][nsh][3]) are accumulated
+ * orc_render), and dL/dN (g_normal[n][3], world frame; NULL = zero).  d_dens[i]
+ * ([n][8]) and d_sh[i] ([n][nsh][3]) are accumulated
  * into (callers zero them). */
 int orc_backward(const orc_octree* oct, int n_oct, const orc_pose* poses, const orc_camera* cam,
                  const orc_opts* opt, int64_t n_pix, const int64_t* pix, const double* g_rgb, const double* g_depth,
-                 const double* g_alpha, double* const* d_dens, double* const* d_sh, int n_threads) {
+                 const double* g_alpha, double* const* d_dens, double* const* d_sh, int n_threads,
+                 const double* g_normal) {
     int st = check_inputs(oct, n_oct, cam, opt);
     if (st != ORC_OK) return st;
     if (!pix) n_pix = (int64_t)cam->W * cam->H;
@@ -646,6 +691,7 @@ int orc_backward(const orc_octree* oct, int n_oct, const orc_pose* poses, const 
     base.g_rgb = g_rgb;
     base.g_depth = g_depth;
     base.g_alpha = g_alpha;
+    base.g_normal = g_normal;
     if (n_threads < 1) n_threads = 1;
     job* J = NULL;
     st = run_jobs(&base, n_threads, bwd_worker, &J);
@@ -655,6 +701,21 @@ int orc_backward(const orc_octree* oct, int n_oct, const orc_pose* poses, const 
                 const struct grad_rec* g = &J[t].rec[r];
                 const orc_octree* oc = &oct[g->oct];
                 for (int c = 0; c < 8; ++c) d_dens[g->oct][g->vox * 8 + c] += g->g_dens[c];
+                if (g->g_nrm[0] != 0.0 || g->g_nrm[1] != 0.0 || g->g_nrm[2] != 0.0) {
+                    /* through the voxel normal: n_local = -g/|g|, n_world = R n_local */
+                    double n_loc[3], n_w[3], gn, dn[3], dg[3];
+                    voxel_normal(oc, &poses[g->oct], g->vox, n_loc, n_w, &gn);
+                    if (gn > 0.0) {
+                        const double* R = poses[g->oct].R;
+                        for (int k = 0; k < 3; ++k)
+                            dn[k] = R[0 * 3 + k] * g->g_nrm[0] + R[1 * 3 + k] * g->g_nrm[1] + R[2 * 3 + k] * g->g_nrm[2];
+                        double nd = n_loc[0] * dn[0] + n_loc[1] * dn[1] + n_loc[2] * dn[2];
+                        for (int a = 0; a < 3; ++a) dg[a] = -(dn[a] - n_loc[a] * nd) / gn;
+                        for (int c = 0; c < 8; ++c)
+                            for (int a = 0; a < 3; ++a)
+                                d_dens[g->oct][g->vox * 8 + c] += ((c >> a) & 1) ? dg[a] : -dg[a];
+                    }
+                }
                 double Y[16];
                 sh_basis(oc->sh_degree, g->g[0], g->g[1], g->g[2], Y);
                 int nsh = (oc->sh_degree + 1) * (oc->sh_degree + 1);

@@ -28,6 +28,11 @@ MUTANTS = {
     "backward colour suffix sign": ("gtau += gC[ch] * (Tn * e->rgb[ch] - RC[ch]);", "gtau += gC[ch] * (Tn * e->rgb[ch] + RC[ch]);"),
     "SH gradient ignores the clamp": ("if (!(g->pre[ch] > 0.0)) continue;", "if (0) continue;"),
     "SH gradient without the weight": ("r.g_rgb[ch] = gC[ch] * w;", "r.g_rgb[ch] = gC[ch];"),
+    "normal points up the density gradient": ("n_loc[a] = gn > 0.0 ? -g[a] / gn : 0.0;", "n_loc[a] = gn > 0.0 ? g[a] / gn : 0.0;"),
+    "normal left in the local frame": ("n_world[r] = P->R[r * 3 + 0] * n_loc[0] + P->R[r * 3 + 1] * n_loc[1] + P->R[r * 3 + 2] * n_loc[2];",
+                                       "n_world[r] = n_loc[r];"),
+    "normal gradient without the tangent projection": ("dg[a] = -(dn[a] - n_loc[a] * nd) / gn;", "dg[a] = -dn[a] / gn;"),
+    "normal suffix dropped": ("gtau += gN[a] * (Tn * e->nrm[a] - RN[a]);", "gtau += gN[a] * (Tn * e->nrm[a]);"),
     "SH sign flipped": ("Y[1] = -k1 * y;", "Y[1] = k1 * y;"),
     "pose rotation transposed": ("for (int r = 0; r < 3; ++r) q[r] = P->R[0 * 3 + r] * w[0] + P->R[1 * 3 + r] * w[1] + P->R[2 * 3 + r] * w[2];",
                                  "for (int r = 0; r < 3; ++r) q[r] = P->R[r * 3 + 0] * w[0] + P->R[r * 3 + 1] * w[1] + P->R[r * 3 + 2] * w[2];"),

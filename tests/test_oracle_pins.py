@@ -557,3 +557,126 @@ def test_backward_through_the_colour_clamp():
             lmv = _loss([oc], [pose64()], cam, f64, g, opts)
             f64[0][1][0, lm_, ch] = x0
             assert ds[0][0, lm_, ch] == pytest.approx((lp - lmv) / (2 * h), rel=2e-5, abs=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# normal state N (Alg. 1: N aggregates voxel normals)
+# ---------------------------------------------------------------------------
+
+def _linear_field(u, k0=3.0, scale=0.7):
+    # corner densities k0 - scale * (u . corner bits): the trilinear field decreases along u, so the
+    # voxel normal (minus the normalised density gradient) is u / |u|
+    bits = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], np.float64)
+    return k0 - scale * bits @ np.asarray(u, np.float64)
+
+
+def test_normal_of_a_linear_field_is_its_descent_direction():
+    rng = np.random.default_rng(31)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    dens = np.float32(_linear_field(u)).astype(np.float64)
+    oc = one_voxel(0, (0, 0, 0), dens, (0.4, 0.5, 0.6))
+    cam = cam_looking((2.0, 1.4, 1.1), (0.0, 0.0, 0.0), W=9, H=9, fov=40.0)
+    # the float32-stored corners give the exact field direction up to float32 rounding of the inputs
+    bits = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], np.float64)
+    g = np.array([np.sum(np.where(bits[:, a] == 1, dens, -dens)) for a in range(3)])
+    n_exp = -g / np.linalg.norm(g)
+    assert np.allclose(n_exp, u, atol=1e-6)
+    rgb, _, alpha, _, N = oracle.render([oc], [pose64()], cam, oracle.Opts(K=1, eps_stop=0.0), normals=True)
+    hit = alpha > 1e-3
+    assert hit.sum() > 20
+    np.testing.assert_allclose(N[hit] / alpha[hit, None], np.broadcast_to(n_exp, (hit.sum(), 3)), rtol=1e-10,
+                               atol=1e-12)
+    # the same voxel as an actor under a rotation: the normal turns with the pose
+    R = synth.random_rotation(rng).astype(np.float64)
+    t = np.array([0.1, -0.2, 0.05])
+    act = one_voxel(0, (0, 0, 0), dens, (0.4, 0.5, 0.6), role=synth.ACTOR, clip_half=(0.6, 0.6, 0.6))
+    empty = one_voxel(0, np.zeros((0, 3), int), 1.0, (0.5, 0.5, 0.5))
+    _, _, a2, _, N2 = oracle.render([empty, act], [pose64(), pose64(R, t)], cam, oracle.Opts(K=1, eps_stop=0.0),
+                                    normals=True)
+    hit = a2 > 1e-3
+    assert hit.sum() > 20
+    np.testing.assert_allclose(N2[hit] / a2[hit, None], np.broadcast_to(R @ n_exp, (hit.sum(), 3)), rtol=1e-10,
+                               atol=1e-12)
+
+
+def test_normal_of_a_constant_voxel_is_zero():
+    oc = one_voxel(0, (0, 0, 0), 2.0, (0.4, 0.5, 0.6))
+    cam = cam_looking((2.0, 1.4, 1.1), (0.0, 0.0, 0.0), W=7, H=7, fov=40.0)
+    _, _, alpha, _, N = oracle.render([oc], [pose64()], cam, oracle.Opts(K=2, eps_stop=0.0), normals=True)
+    assert alpha.max() > 0.5 and np.all(N == 0.0)
+
+
+def test_normals_of_stacked_voxels_are_weighted_front_to_back():
+    # two voxels on the optical axis with different normals: N = a1 n1 + (1 - a1) a2 n2, with each
+    # voxel's own alpha taken from a render of that voxel alone
+    rng = np.random.default_rng(32)
+    u1, u2 = rng.normal(size=3), rng.normal(size=3)
+    u1 /= np.linalg.norm(u1)
+    u2 /= np.linalg.norm(u2)
+    d1 = np.float32(_linear_field(u1, k0=1.6, scale=0.5)).astype(np.float64)
+    d2 = np.float32(_linear_field(u2, k0=2.4, scale=0.9)).astype(np.float64)
+    both = one_voxel(1, [(0, 0, 0), (1, 0, 0)], np.stack([d1, d2]), (0.5, 0.5, 0.5), center=(0.5, 0.5, 0.5),
+                     root=2.0)
+    front = one_voxel(1, [(0, 0, 0)], d1, (0.5, 0.5, 0.5), center=(0.5, 0.5, 0.5), root=2.0)
+    back = one_voxel(1, [(1, 0, 0)], d2, (0.5, 0.5, 0.5), center=(0.5, 0.5, 0.5), root=2.0)
+    cam = cam_looking((-3.0, 0.0, 0.0), (1.0, 0.0, 0.0), W=1, H=1, fov=1.0, up=(0.0, 0.0, 1.0))
+    opts = oracle.Opts(K=1, eps_stop=0.0)
+    _, _, a1, _ = oracle.render([front], [pose64()], cam, opts)
+    _, _, a2, _ = oracle.render([back], [pose64()], cam, opts)
+    _, _, a, _, N = oracle.render([both], [pose64()], cam, opts, normals=True)
+    a1, a2 = float(a1[0, 0]), float(a2[0, 0])
+    assert 0.05 < a1 < 0.95 and 0.05 < a2 < 0.99
+    n = lambda d: (lambda g: -g / np.linalg.norm(g))(
+        np.array([np.sum([d[c] if (c >> ax) & 1 else -d[c] for c in range(8)]) for ax in range(3)]))
+    np.testing.assert_allclose(N[0, 0], a1 * n(d1) + (1 - a1) * a2 * n(d2), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(a[0, 0], 1 - (1 - a1) * (1 - a2), rtol=1e-12)
+
+
+def test_normals_turn_with_a_rigid_motion_of_scene_and_camera():
+    octs, poses = _comp_scene()
+    cam = cam_looking((2.4, -1.5, 1.1), (0.0, 0.0, 0.0), W=20, H=16, fov=50.0)
+    rng = np.random.default_rng(33)
+    G = np.eye(4)
+    G[:3, :3] = synth.random_rotation(rng)
+    G[:3, 3] = rng.uniform(-3, 3, 3)
+    mv = lambda p: (lambda m: pose64(m[:3, :3], m[:3, 3]))(G @ np.block([[p.R, p.t[:, None]], [np.zeros((1, 3)), 1]]))
+    cam2 = SimpleNamespace(**{**cam.__dict__, "pose": mv(cam.pose)})
+    a = oracle.render(octs, poses, cam, oracle.Opts(K=2, eps_stop=1e-4), normals=True)
+    b = oracle.render(octs, [mv(p) for p in poses], cam2, oracle.Opts(K=2, eps_stop=1e-4), normals=True)
+    assert np.abs(a[4]).max() > 0.3
+    np.testing.assert_allclose(b[4], a[4] @ G[:3, :3].T, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_backward_through_normals_matches_central_differences(K):
+    octs, poses = _comp_scene(seed=12)
+    cam = cam_looking((2.2, 1.7, 0.9), (0.0, 0.0, 0.0), W=11, H=9, fov=45.0)
+    opts = oracle.Opts(K=K, eps_stop=0.0)
+    rng = np.random.default_rng(34)
+    gN = rng.normal(size=(cam.H * cam.W, 3))
+    gC = 0.3 * rng.normal(size=(cam.H * cam.W, 3))
+    z = np.zeros(cam.H * cam.W)
+    f64 = [(o.dens.astype(np.float64), o.sh.astype(np.float64)) for o in octs]
+    dd, _ = oracle.backward(octs, poses, cam, gC, z, z, opts, f64_arrays=f64, g_normal=gN)
+
+    def loss():
+        r = oracle.render(octs, poses, cam, opts, f64_arrays=f64, normals=True)
+        return float(np.sum(gC * r[0].reshape(-1, 3)) + np.sum(gN * r[4].reshape(-1, 3)))
+
+    checked = 0
+    for oi in range(len(octs)):
+        nz = np.argwhere(np.abs(dd[oi]) > 1e-4)
+        for v, c in nz[rng.permutation(len(nz))[:8]]:
+            x0 = f64[oi][0][v, c]
+            if abs(x0 - 1.1) < 1e-3:
+                continue
+            h = 1e-6 * max(1.0, abs(x0))
+            f64[oi][0][v, c] = x0 + h
+            lp = loss()
+            f64[oi][0][v, c] = x0 - h
+            lm = loss()
+            f64[oi][0][v, c] = x0
+            assert dd[oi][v, c] == pytest.approx((lp - lm) / (2 * h), rel=2e-5, abs=1e-8)
+            checked += 1
+    assert checked >= 16
