@@ -168,6 +168,33 @@ dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, cons
 dv_status dv_render_backward(dv_ctx* ctx, dv_state* state, const float* d_rgb, const float* d_depth,
                              const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream);
 
+/*
+ * dv_render plus the normal state N of Algorithm 1 (Sec. 3.4: the pixel state
+ * aggregates voxel normals): N = sum over the composited segments of
+ * T_k alpha_k n_k, with n the voxel's normal in world coordinates -- minus the
+ * normalised gradient of the voxel's trilinear raw density at its centre
+ * (per axis: the four corners on the high side minus the four on the low
+ * side), rotated by its octree's pose; zero where that gradient vanishes.  N is
+ * not normalised (compare with N / |N|, as the normal loss of the paper does).
+ *   normal   device output [sum H*W][3], concatenated per camera like rgb
+ * Other arguments, errors and the saved state as for dv_render; the state also
+ * borrows `normal`.
+ */
+dv_status dv_render_normals(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* poses,
+                            const dv_camera* cams, int32_t n_cam, const dv_opts* opts, float* rgb, float* depth,
+                            float* alpha, float* normal, dv_state** saved, void* stream);
+
+/*
+ * Backward of dv_render_normals: as dv_render_backward, plus dL/dN
+ * (d_normal, device [sum H*W][3], world frame; NULL = zero), which reaches the
+ * corner densities both through the compositing weights and through each
+ * voxel's normal.  DV_ERR_INVALID_ARG if `state` comes from a call without
+ * normals and d_normal is non-NULL.
+ */
+dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* state, const float* d_rgb, const float* d_depth,
+                                     const float* d_alpha, const float* d_normal, float* const* d_dens,
+                                     float* const* d_sh, void* stream);
+
 /* Releases a saved state (stream-ordered on the stream of its render call). */
 void dv_state_free(dv_state* state);
 

@@ -139,6 +139,14 @@ def load(path: str | None = None):
     lib.dv_render_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]
     lib.dv_render_backward.restype = C.c_int
+    lib.dv_render_normals.argtypes = [C.c_void_p, C.POINTER(dv_octree), C.c_int32, C.POINTER(dv_pose),
+                                      C.POINTER(dv_camera), C.c_int32, C.POINTER(dv_opts), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p]
+    lib.dv_render_normals.restype = C.c_int
+    lib.dv_render_backward_normals.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                               C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                               C.c_void_p]
+    lib.dv_render_backward_normals.restype = C.c_int
     lib.dv_state_free.argtypes = [C.c_void_p]
     lib.dv_state_free.restype = None
     lib.dv_state_stats.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -351,9 +359,11 @@ class State:
 
 
 def dv_render(octrees, poses, cams, opts=None, *, ctx: Context | None = None, save_state=False, out=None,
-              dens=None, sh=None, stream=None):
+              dens=None, sh=None, stream=None, normals=False):
     """Forward render; returns (rgb [P,3], depth [P], alpha [P], state or None) with P = sum of H*W
-    over the cameras (images concatenated in camera order)."""
+    over the cameras (images concatenated in camera order).  With ``normals`` the normal state
+    N [P,3] (world frame) is rendered too and returned before the state:
+    (rgb, depth, alpha, normal, state)."""
     import torch
     lib = load()
     ctx = ctx or default_context()
@@ -369,16 +379,22 @@ def dv_render(octrees, poses, cams, opts=None, *, ctx: Context | None = None, sa
         rgb = torch.empty((P, 3), device=dev, dtype=torch.float32)
         depth = torch.empty((P,), device=dev, dtype=torch.float32)
         alpha = torch.empty((P,), device=dev, dtype=torch.float32)
+        normal = torch.empty((P, 3), device=dev, dtype=torch.float32) if normals else None
     else:
-        rgb, depth, alpha = out
+        rgb, depth, alpha = out[:3]
+        normal = out[3] if normals else None
     st = C.c_void_p()
-    status = lib.dv_render(ctx.handle, oct_arr, n, pose_arr, cam_arr, len(cams), C.byref(opts),
-                           C.c_void_p(rgb.data_ptr() if P else None), C.c_void_p(depth.data_ptr() if P else None),
-                           C.c_void_p(alpha.data_ptr() if P else None), C.byref(st) if save_state else None,
-                           _stream_ptr(stream))
+    ptr = lambda t: C.c_void_p(t.data_ptr() if P else None)
+    if normals:
+        status = lib.dv_render_normals(ctx.handle, oct_arr, n, pose_arr, cam_arr, len(cams), C.byref(opts), ptr(rgb),
+                                       ptr(depth), ptr(alpha), ptr(normal), C.byref(st) if save_state else None,
+                                       _stream_ptr(stream))
+    else:
+        status = lib.dv_render(ctx.handle, oct_arr, n, pose_arr, cam_arr, len(cams), C.byref(opts), ptr(rgb),
+                               ptr(depth), ptr(alpha), C.byref(st) if save_state else None, _stream_ptr(stream))
     ctx.check(status)
-    state = State(ctx, st, len(cams), (octrees, dens, sh, rgb, depth, alpha)) if save_state else None
-    return rgb, depth, alpha, state
+    state = State(ctx, st, len(cams), (octrees, dens, sh, rgb, depth, alpha, normal)) if save_state else None
+    return (rgb, depth, alpha, normal, state) if normals else (rgb, depth, alpha, state)
 
 
 def dv_render_views(octrees, views, opts=None, *, ctx: Context | None = None, save_state=False, out=None,
@@ -416,15 +432,21 @@ def dv_render_views(octrees, views, opts=None, *, ctx: Context | None = None, sa
     return rgb, depth, alpha, state
 
 
-def dv_render_backward(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_dens=None, d_sh=None, stream=None):
-    """Adds dL/d dens and dL/d sh into the given per-octree tensors (lists; None entries skipped)."""
+def dv_render_backward(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_dens=None, d_sh=None, stream=None,
+                       d_normal=None):
+    """Adds dL/d dens and dL/d sh into the given per-octree tensors (lists; None entries skipped).
+    ``d_normal`` [P,3] is dL/dN of a render with normals."""
     lib = load()
     n = len(d_dens) if d_dens is not None else len(d_sh)
     pd = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_dens or [None] * n)])
     ps = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_sh or [None] * n)])
     ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
-    status = lib.dv_render_backward(state.ctx.handle, state.handle, ptr(d_rgb), ptr(d_depth), ptr(d_alpha), pd, ps,
-                                    _stream_ptr(stream))
+    if d_normal is not None:
+        status = lib.dv_render_backward_normals(state.ctx.handle, state.handle, ptr(d_rgb), ptr(d_depth),
+                                                ptr(d_alpha), ptr(d_normal), pd, ps, _stream_ptr(stream))
+    else:
+        status = lib.dv_render_backward(state.ctx.handle, state.handle, ptr(d_rgb), ptr(d_depth), ptr(d_alpha), pd,
+                                        ps, _stream_ptr(stream))
     state.ctx.check(status)
 
 
@@ -450,26 +472,28 @@ def _autograd_fn():
 
         @staticmethod
         def forward(ctx_, meta, *tensors):
-            octrees, poses, cams, opts = meta
+            octrees, poses, cams, opts, normals = meta
             n = len(octrees)
             dens, sh = list(tensors[:n]), list(tensors[n:])
-            rgb, depth, alpha, state = dv_render(octrees, poses, cams, opts, save_state=True,
-                                                 dens=[d.detach() for d in dens], sh=[s.detach() for s in sh])
-            ctx_.state = state
+            out = dv_render(octrees, poses, cams, opts, save_state=True, dens=[d.detach() for d in dens],
+                            sh=[s.detach() for s in sh], normals=normals)
+            ctx_.state = out[-1]
             ctx_.n = n
+            ctx_.normals = normals
             ctx_.shapes = [(d.shape, s.shape) for d, s in zip(dens, sh)]
-            return rgb, depth, alpha
+            return out[:-1]
 
         @staticmethod
-        def backward(ctx_, g_rgb, g_depth, g_alpha):
+        def backward(ctx_, g_rgb, g_depth, g_alpha, g_normal=None):
             import torch as T
             n = ctx_.n
             st = ctx_.state
-            dev = g_rgb.device if g_rgb is not None else g_alpha.device
+            dev = next(g.device for g in (g_rgb, g_depth, g_alpha, g_normal) if g is not None)
             d_dens = [T.zeros(s[0], device=dev, dtype=T.float32) for s in ctx_.shapes]
             d_sh = [T.zeros(s[1], device=dev, dtype=T.float32) for s in ctx_.shapes]
             c = lambda t: None if t is None else t.contiguous()
-            dv_render_backward(st, c(g_rgb), c(g_depth), c(g_alpha), d_dens, d_sh)
+            dv_render_backward(st, c(g_rgb), c(g_depth), c(g_alpha), d_dens, d_sh,
+                               d_normal=c(g_normal) if ctx_.normals else None)
             st.free()
             ctx_.state = None
             return (None, *d_dens, *d_sh)
@@ -489,15 +513,16 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-def render(octrees, poses, cams, opts=None, dens=None, sh=None):
+def render(octrees, poses, cams, opts=None, dens=None, sh=None, normals=False):
     """Autograd entry: gradients flow to ``dens``/``sh`` (lists of per-octree tensors; defaults
-    to the octrees' own tensors)."""
+    to the octrees' own tensors).  Returns (rgb, depth, alpha), plus the normal state N with
+    ``normals``."""
     global _RenderFn
     if _RenderFn is None:
         _RenderFn = _autograd_fn()
     dens = [o.dens for o in octrees] if dens is None else dens
     sh = [o.sh for o in octrees] if sh is None else sh
-    return _RenderFn.apply((octrees, poses, cams, opts or make_opts()), *dens, *sh)
+    return _RenderFn.apply((octrees, poses, cams, opts or make_opts(), normals), *dens, *sh)
 
 
 STATIC_MAX_VISIBLE = 1 << 17  # visible voxels per render call, summed over its views

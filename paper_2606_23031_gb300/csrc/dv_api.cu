@@ -61,6 +61,7 @@ struct BatchState {
     OctParams* d_octs = nullptr;
     std::vector<ViewParams> h_views;
     VoxRec* rec = nullptr;
+    float4* nrm = nullptr;  // per record voxel normal (world), when the call renders normals
     uint32_t* sorted_g = nullptr;
     uint32_t* pval = nullptr;
     uint8_t* pmask = nullptr;  // per pair: 8x4-pixel blocks of the tile the voxel touches
@@ -280,6 +281,7 @@ void make_view(const dv_octree* oct, int n_oct, const dv_pose* poses, const dv_c
         for (int k = 0; k < 9; ++k) {
             Q.A[k] = (float)A.a[k];
             Q.M[k] = (float)Mc.a[k];
+            Q.Rw[k] = (float)Ri.a[k];
         }
         for (int k = 0; k < 3; ++k) {
             Q.m[k] = (float)mc[k];
@@ -388,7 +390,7 @@ T* pool_alloc(dv_ctx* ctx, cudaStream_t s, size_t count, std::vector<void*>& own
 // (freed by the caller when no state is wanted).
 dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pose* const* view_poses,
                        const dv_camera* cams, int n_view, const dv_opts& opt, dv_state* st, float* const* rgbs,
-                       float* const* depths, float* const* alphas, cudaStream_t s) {
+                       float* const* depths, float* const* alphas, float* const* normals, cudaStream_t s) {
     using namespace dv;
     BatchState& B = st->b;
     BatchParams& bp = B.bp;
@@ -398,6 +400,7 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     bp.K = opt.K;
     bp.inv_k = 1.0f / (float)opt.K;
     bp.eps_stop = opt.eps_stop;
+    bp.normals = normals ? 1 : 0;
     bp.activation = opt.activation;
     int Lkey = 0;
     for (int i = 0; i < n_oct; ++i) Lkey = std::max(Lkey, (int)oct[i].max_level);
@@ -420,6 +423,7 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         B.h_views[v].tile_base = (int32_t)tiles;
         B.h_views[v].pix_base = pix;
         B.h_views[v].rgb = rgbs[v];
+        B.h_views[v].normal = normals ? normals[v] : nullptr;
         B.h_views[v].depth = depths[v];
         B.h_views[v].alpha = alphas[v];
         bp.tile_base[v] = (int32_t)tiles;
@@ -521,6 +525,8 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     if (e == cudaSuccess && gg != B.sorted_g)
         e = cudaMemcpyAsync(B.sorted_g, gg, sizeof(uint32_t) * (size_t)n_vis, cudaMemcpyDeviceToDevice, s);
     B.rec = pool_alloc<VoxRec>(ctx, s, (size_t)n_vis, own, e);
+    if (bp.normals) B.nrm = pool_alloc<float4>(ctx, s, (size_t)n_vis, own, e);
+    bp.nrm = B.nrm;
     uint32_t* cnt_sorted = ar.alloc<uint32_t>((size_t)n_vis);
     uint64_t* rect_sorted = ar.alloc<uint64_t>((size_t)n_vis);
     uint64_t* off_pairs = ar.alloc<uint64_t>((size_t)n_vis);
@@ -530,7 +536,7 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     }
     {
         Prof p(ctx, KP_RECORDS, s);
-        e = launch_records(bp, B.sorted_g, n_vis, cnt, rect, B.rec, cnt_sorted, rect_sorted, s);
+        e = launch_records(bp, B.sorted_g, n_vis, cnt, rect, B.rec, B.nrm, cnt_sorted, rect_sorted, s);
         if (e == cudaSuccess) e = launch_vis_start(bp, kk, n_vis, B.vis_start, s);
     }
     {
@@ -578,19 +584,24 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     return DV_OK;
 }
 
+// floats per visible voxel of the backward's gradient scratch
+size_t grad_stride(bool with_normals) { return with_normals ? 16 : 12; }
+
+// d_normal: dL/dN of a call that rendered normals, or null (no gradient through N)
 dv_status backward_batch(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth, const float* d_alpha,
-                         float* const* d_dens, float* const* d_sh, float* grad, cudaStream_t s) {
+                         const float* d_normal, float* const* d_dens, float* const* d_sh, float* grad, cudaStream_t s) {
     BatchState& B = st->b;
-    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * 12 * (size_t)B.n_vis, s);
+    const bool nrm = d_normal != nullptr;
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * grad_stride(nrm) * (size_t)B.n_vis, s);
     {
         Prof p(ctx, KP_BWD, s);
         if (e == cudaSuccess)
             e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, nullptr,
-                                         nullptr, B.t_final, d_rgb, d_depth, d_alpha, grad, s);
+                                         nullptr, B.t_final, d_rgb, d_depth, d_alpha, d_normal, grad, s);
     }
     {
         Prof p(ctx, KP_SHBWD, s);
-        if (e == cudaSuccess) e = dv::launch_sh_bwd(B.bp, B.sorted_g, B.n_vis, B.rec, grad, d_dens, d_sh, s);
+        if (e == cudaSuccess) e = dv::launch_sh_bwd(B.bp, B.sorted_g, B.n_vis, B.rec, grad, nrm, d_dens, d_sh, s);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward");
     return DV_OK;
@@ -669,7 +680,7 @@ const char* dv_last_error(const dv_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* const* view_poses,
                                const dv_camera* cams, int32_t n_view, const dv_opts* opts, float* rgb, float* depth,
                                float* alpha, float* const* rgbs, float* const* depths, float* const* alphas,
-                               dv_state** saved, void* stream) {
+                               dv_state** saved, void* stream, float* normal = nullptr) {
     if (!ctx) return DV_ERR_INVALID_ARG;
     ctx->err.clear();
     if (saved) *saved = nullptr;
@@ -688,7 +699,7 @@ static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct,
     if (3 * Lkey + bits_for(n_oct) + bits_for(n_view) > 64)
         return fail(ctx, DV_ERR_CAPACITY, "depth key does not fit 64 bits");
     // per-view output pointers: given, or carved from the concatenated buffers
-    std::vector<float*> vr((size_t)std::max(n_view, 1)), vd(vr.size()), va(vr.size());
+    std::vector<float*> vr((size_t)std::max(n_view, 1)), vd(vr.size()), va(vr.size()), vn(vr.size());
     int64_t pb = 0;
     for (int v = 0; v < n_view; ++v) {
         const int64_t n = (int64_t)cams[v].W * cams[v].H;
@@ -701,6 +712,7 @@ static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct,
             vd[v] = depth ? depth + pb : nullptr;
             va[v] = alpha ? alpha + pb : nullptr;
         }
+        vn[v] = normal ? normal + pb * 3 : nullptr;
         if (n > 0 && (!vr[v] || !vd[v] || !va[v])) return fail(ctx, DV_ERR_INVALID_ARG, "NULL output buffer");
         pb += n;
     }
@@ -713,7 +725,7 @@ static dv_status render_common(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct,
     st->stream = s;
     if (n_view > 0) {
         dv_status rs = render_batch(ctx, oct, n_oct, view_poses, cams, n_view, *opts, st.get(), vr.data(), vd.data(),
-                                    va.data(), s);
+                                    va.data(), normal ? vn.data() : nullptr, s);
         if (rs != DV_OK) {
             free_state(st.release());
             return rs;
@@ -755,25 +767,57 @@ dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, cons
                          nullptr, saved, stream);
 }
 
-dv_status dv_render_backward(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
-                             const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream) {
+static dv_status backward_common(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
+                                 const float* d_alpha, const float* d_normal, float* const* d_dens, float* const* d_sh,
+                                 void* stream) {
     if (!ctx || !st) return DV_ERR_INVALID_ARG;
     ctx->err.clear();
     if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
+    if (d_normal && !st->b.bp.normals)
+        return fail(ctx, DV_ERR_INVALID_ARG, "a normal gradient for a render without normals");
     if (st->b.n_vis == 0) return DV_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     dv::Arena ar;
     ar.pool = ctx->pool;
     ar.stream = s;
-    float* grad = ar.alloc<float>((size_t)st->b.n_vis * 12);
+    float* grad = ar.alloc<float>((size_t)st->b.n_vis * grad_stride(d_normal != nullptr));
     if (!grad) {
         ar.release();
         return cuda_fail(ctx, ar.err, "allocate gradient scratch");
     }
-    dv_status r = backward_batch(ctx, st, d_rgb, d_depth, d_alpha, d_dens, d_sh, grad, s);
+    dv_status r = backward_batch(ctx, st, d_rgb, d_depth, d_alpha, d_normal, d_dens, d_sh, grad, s);
     ar.release();
     return r;
+}
+
+dv_status dv_render_backward(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
+                             const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream) {
+    return backward_common(ctx, st, d_rgb, d_depth, d_alpha, nullptr, d_dens, d_sh, stream);
+}
+
+dv_status dv_render_normals(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, const dv_pose* poses,
+                            const dv_camera* cams, int32_t n_cam, const dv_opts* opts, float* rgb, float* depth,
+                            float* alpha, float* normal, dv_state** saved, void* stream) {
+    if (n_cam < 0 || n_cam > DV_MAX_VIEWS) {
+        if (ctx) ctx->err = "camera count out of range (0..64)";
+        return n_cam < 0 ? DV_ERR_INVALID_ARG : DV_ERR_CAPACITY;
+    }
+    int64_t pix = 0;
+    for (int v = 0; v < n_cam && cams; ++v) pix += (int64_t)cams[v].W * cams[v].H;
+    if (pix > 0 && !normal) {
+        if (ctx) ctx->err = "NULL normal buffer";
+        return DV_ERR_INVALID_ARG;
+    }
+    std::vector<const dv_pose*> vp((size_t)std::max(n_cam, 1), poses);
+    return render_common(ctx, oct, n_oct, vp.data(), cams, n_cam, opts, rgb, depth, alpha, nullptr, nullptr, nullptr,
+                         saved, stream, normal);
+}
+
+dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* st, const float* d_rgb, const float* d_depth,
+                                     const float* d_alpha, const float* d_normal, float* const* d_dens,
+                                     float* const* d_sh, void* stream) {
+    return backward_common(ctx, st, d_rgb, d_depth, d_alpha, d_normal, d_dens, d_sh, stream);
 }
 
 void dv_state_free(dv_state* st) { free_state(st); }
@@ -949,5 +993,5 @@ extern "C" dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* st, const 
     float* grad = nullptr;
     cudaError_t e = static_grad_ptr(ctx->device, &grad);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(static gradient scratch)");
-    return backward_batch(ctx, st, d_rgb, d_depth, d_alpha, d_dens, d_sh, grad, (cudaStream_t)stream);
+    return backward_batch(ctx, st, d_rgb, d_depth, d_alpha, nullptr, d_dens, d_sh, grad, (cudaStream_t)stream);
 }

@@ -50,20 +50,37 @@ namespace dv {
 namespace {
 
 constexpr int CT_THREADS = 128;  // half a tile per CTA
-constexpr int GSTRIDE = 12;      // per-record gradient slots: 8 densities, 3 colour, 1 pad
+// per-record gradient slots: 8 densities, 3 colour (+ 3 normal with normals), padded to 16 bytes
+template <bool NRM>
+struct GradLayout {
+    static constexpr int NV = NRM ? 14 : 11;      // values per record
+    static constexpr int STRIDE = NRM ? 16 : 12;  // floats per record row
+};
 constexpr int NTA = 4;           // tile actors with lockstep partials
 
-struct Pix {
+struct PixBase {
     float C0, C1, C2, D, T;
     uint32_t n;
     uint32_t tests, boxes;  // work counters: voxel slab tests, actor box tests
     bool done;
 };
+template <bool NRM>
+struct Pix : PixBase {};
+template <>
+struct Pix<true> : PixBase {
+    float N0, N1, N2;  // normal state
+};
 
-struct Bwd {
+struct BwdBase {
     // upstream gradient and the forward's results
     float g0, g1, g2, gD, gA;
     float Cf0, Cf1, Cf2, Df, Tend;
+};
+template <bool NRM>
+struct Bwd : BwdBase {};
+template <>
+struct Bwd<true> : BwdBase {
+    float gN0, gN1, gN2, Nf0, Nf1, Nf2;  // normal state: upstream gradient and final value
 };
 
 struct ActInt {
@@ -196,7 +213,8 @@ __device__ __forceinline__ float seg_tau(float4 da, float4 db, float is, const f
 }
 
 // Front-to-back compositing of one segment of optical depth tau; returns its weight T alpha.
-__device__ __forceinline__ float composite_step(Pix& ps, float tau, float4 col, float t0, float t1) {
+template <bool NRM>
+__device__ __forceinline__ float composite_step(Pix<NRM>& ps, float tau, float4 col, float4 nv, float t0, float t1) {
     const float e = __expf(-tau);  // transmittance of the segment
     const float alpha = 1.0f - e;
     const float w = ps.T * alpha;
@@ -205,25 +223,32 @@ __device__ __forceinline__ float composite_step(Pix& ps, float tau, float4 col, 
     ps.C1 = fmaf(w, col.y, ps.C1);
     ps.C2 = fmaf(w, col.z, ps.C2);
     ps.D = fmaf(w, mid, ps.D);
+    if constexpr (NRM) {
+        ps.N0 = fmaf(w, nv.x, ps.N0);
+        ps.N1 = fmaf(w, nv.y, ps.N1);
+        ps.N2 = fmaf(w, nv.z, ps.N2);
+    }
     ps.T = ps.T * e;
     ps.n += 1;
     return w;
 }
 
-__device__ __forceinline__ void composite_tau(Pix& ps, float tau, float4 col, float t0, float t1, float eps_stop) {
-    composite_step(ps, tau, col, t0, t1);
+template <bool NRM>
+__device__ __forceinline__ void composite_tau(Pix<NRM>& ps, float tau, float4 col, float4 nv, float t0, float t1,
+                                              float eps_stop) {
+    composite_step<NRM>(ps, tau, col, nv, t0, t1);
     if (ps.T < eps_stop) ps.done = true;
 }
 
 // Composites one segment (with the stop test when STOP); with GRAD also adds
 // this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
-template <bool GRAD, bool STOP, int KS>
-__device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchParams& bp, float4 da, float4 db,
-                                            float4 col, const float* rel, const float* d, float t0, float t1,
-                                            float* acc) {
+template <bool GRAD, bool STOP, int KS, bool NRM>
+__device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp, float4 da, float4 db,
+                                            float4 col, float4 nv, const float* rel, const float* d, float t0,
+                                            float t1, float* acc) {
     float dtd[8];
     const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
-    const float w = composite_step(ps, tau, col, t0, t1);
+    const float w = composite_step<NRM>(ps, tau, col, nv, t0, t1);
     if (GRAD) {
         const float mid = 0.5f * (t0 + t1);
         const float Tn = ps.T;
@@ -232,6 +257,14 @@ __device__ __forceinline__ void add_segment(Pix& ps, const Bwd& bw, const BatchP
         gt = fmaf(bw.g1, fmaf(Tn, col.y, -(bw.Cf1 - ps.C1)), gt);
         gt = fmaf(bw.g2, fmaf(Tn, col.z, -(bw.Cf2 - ps.C2)), gt);
         gt = fmaf(bw.gD, fmaf(Tn, mid, -(bw.Df - ps.D)), gt);
+        if constexpr (NRM) {
+            gt = fmaf(bw.gN0, fmaf(Tn, nv.x, -(bw.Nf0 - ps.N0)), gt);
+            gt = fmaf(bw.gN1, fmaf(Tn, nv.y, -(bw.Nf1 - ps.N1)), gt);
+            gt = fmaf(bw.gN2, fmaf(Tn, nv.z, -(bw.Nf2 - ps.N2)), gt);
+            acc[11] = fmaf(bw.gN0, w, acc[11]);
+            acc[12] = fmaf(bw.gN1, w, acc[12]);
+            acc[13] = fmaf(bw.gN2, w, acc[13]);
+        }
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = fmaf(gt, dtd[c], acc[c]);
         acc[8] = fmaf(bw.g0, w, acc[8]);
@@ -271,23 +304,25 @@ __device__ __forceinline__ ActInt next_interval(const OctParams* __restrict__ vo
     return r;
 }
 
+template <bool NRM>
 __device__ __forceinline__ void atomic_grad(float* grad_rec, uint32_t r, const float* acc) {
-    float* gp = grad_rec + (size_t)r * GSTRIDE;
+    float* gp = grad_rec + (size_t)r * GradLayout<NRM>::STRIDE;
 #pragma unroll
-    for (int c = 0; c < 11; ++c)
+    for (int c = 0; c < GradLayout<NRM>::NV; ++c)
         if (acc[c] != 0.0f) atomicAdd(gp + c, acc[c]);
 }
 
-// Sum of acc[0..10] over the warp, transposed: each butterfly level keeps half of
-// the values and exchanges the other half, so 16 shuffles reduce all 11 values
+// Sum of acc[0..NV-1] (NV <= 16) over the warp, transposed: each butterfly level keeps
+// half of the values and exchanges the other half, so 16 shuffles reduce all of them
 // (instead of 5 per value).  Afterwards even lanes hold the totals, value index
 // ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1) for lane l, and each of
-// the 11 lanes owning a real value adds it to the record's gradient slot.
+// the NV lanes owning a real value adds it to the record's gradient slot.
+template <int NV>
 __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
     const int lane = threadIdx.x & 31;
     float v[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = c < 11 ? acc[c] : 0.0f;
+    for (int c = 0; c < 16; ++c) v[c] = c < NV ? acc[c] : 0.0f;
     {
         const bool up = lane & 16;
 #pragma unroll
@@ -323,13 +358,13 @@ __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
     }
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
     const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-    if (!(lane & 1) && idx < 11 && v[0] != 0.0f) atomicAdd(gp + idx, v[0]);
+    if (!(lane & 1) && idx < NV && v[0] != 0.0f) atomicAdd(gp + idx, v[0]);
 }
 
 // Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
 // NTA lockstep slots).
-template <bool GRAD, int KS>
-__device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const BatchParams& bp,
+template <bool GRAD, int KS, bool NRM>
+__device__ __noinline__ void walk_actor_lane(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp,
                                              const OctParams* __restrict__ vo, const ActInt& it,
                                              const uint32_t* __restrict__ pval, const uint8_t* __restrict__ pmask,
                                              uint32_t wbit, const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
@@ -350,11 +385,13 @@ __device__ __noinline__ void walk_actor_lane(Pix& ps, const Bwd& bw, const Batch
         t0 = fmaxf(t0, it.a);
         t1 = fminf(t1, it.b);
         if (!(t1 > t0)) continue;
-        float acc[11];
+        float acc[GradLayout<NRM>::NV];
 #pragma unroll
-        for (int c = 0; c < 11; ++c) acc[c] = 0.0f;
-        add_segment<GRAD, true, KS>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), rel, d, t0, t1, acc);
-        if (GRAD) atomic_grad(grad_rec, r, acc);
+        for (int c = 0; c < GradLayout<NRM>::NV; ++c) acc[c] = 0.0f;
+        const float4 nv = NRM ? __ldg(bp.nrm + r) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        add_segment<GRAD, true, KS, NRM>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), nv, rel, d, t0, t1,
+                                         acc);
+        if (GRAD) atomic_grad<NRM>(grad_rec, r, acc);
     }
 }
 
@@ -372,6 +409,7 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 //                         state at the interval's entry (C0, C1, C2, D, T) when it is replayed
 //   s_st[q][5][lane]    = phase 1: partial segment count; phase 2: 0 not reached,
 //                         1 partial applied, 2 stop inside (replay)
+//   s_st[q][6..8][lane] = with normals: the partial normal state N_A, then N at the entry
 
 #ifndef DV_FWD_MIN_BLOCKS
 #define DV_FWD_MIN_BLOCKS 5  // resident CTAs per SM the forward is compiled for
@@ -380,7 +418,7 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 #define DV_BWD_MIN_BLOCKS 4
 #endif
 
-template <bool BWD, int KS>
+template <bool BWD, int KS, bool NRM>
 __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
@@ -393,9 +431,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                                                         float* __restrict__ t_final, const float* __restrict__ g_rgb,
                                                         const float* __restrict__ g_depth,
                                                         const float* __restrict__ g_alpha,
+                                                        const float* __restrict__ g_normal,
                                                         float* __restrict__ grad_rec,
                                                         unsigned long long* __restrict__ work) {
     __shared__ float4 s_rec[2][CT_THREADS][4];
+    __shared__ float4 s_nv[NRM ? 2 : 1][NRM ? CT_THREADS : 1];  // voxel normals of the staged records
     __shared__ uint32_t s_r[2][CT_THREADS];
     __shared__ uint8_t s_m[2][CT_THREADS];
     __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];  // sub-list of octree o: [s_sub[o], s_sub[o+1])
@@ -403,7 +443,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     __shared__ bool s_flag[DV_MAX_OCTREES];         // actor o's box covers this tile
     __shared__ int16_t s_act[DV_MAX_OCTREES];
     __shared__ float s_iv[NTA][2][CT_THREADS];
-    __shared__ float s_st[NTA][6][CT_THREADS];
+    __shared__ float s_st[NTA][NRM ? 9 : 6][CT_THREADS];
     __shared__ int s_nact;
 
     const int tid = threadIdx.x;
@@ -452,14 +492,15 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     rotate(B.A, dc, db_);
     const InvDir ib = inv_dir(db_);
 
-    Pix ps;
+    Pix<NRM> ps;
     ps.C0 = ps.C1 = ps.C2 = ps.D = 0.0f;
+    if constexpr (NRM) ps.N0 = ps.N1 = ps.N2 = 0.0f;
     ps.T = 1.0f;
     ps.n = 0;
     ps.tests = 0;
     ps.boxes = 0;
     ps.done = !valid;
-    Bwd bw;
+    Bwd<NRM> bw;
     if (BWD && valid) {
         bw.g0 = g_rgb ? g_rgb[pix * 3 + 0] : 0.0f;
         bw.g1 = g_rgb ? g_rgb[pix * 3 + 1] : 0.0f;
@@ -474,6 +515,17 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     } else {
         bw.g0 = bw.g1 = bw.g2 = bw.gD = bw.gA = 0.0f;
         bw.Cf0 = bw.Cf1 = bw.Cf2 = bw.Df = bw.Tend = 0.0f;
+    }
+    if constexpr (NRM) {
+        bw.gN0 = bw.gN1 = bw.gN2 = bw.Nf0 = bw.Nf1 = bw.Nf2 = 0.0f;
+        if (BWD && valid) {
+            bw.gN0 = g_normal[pix * 3 + 0];
+            bw.gN1 = g_normal[pix * 3 + 1];
+            bw.gN2 = g_normal[pix * 3 + 2];
+            bw.Nf0 = fp.normal[lpix * 3 + 0];
+            bw.Nf1 = fp.normal[lpix * 3 + 1];
+            bw.Nf2 = fp.normal[lpix * 3 + 2];
+        }
     }
     // tile set-up, all loads independent of one another: the view's octree boundaries in
     // the record order, and which actor boxes cover this tile
@@ -567,6 +619,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 const float4* R = rec[r].v;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) cp_async16(&s_rec[0][tid][k], R + k);
+                if (NRM) cp_async16(&s_nv[0][NRM ? tid : 0], bp.nrm + r);
                 s_r[0][tid] = r;
                 s_m[0][tid] = __ldg(pmask + qa);
             }
@@ -586,6 +639,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                     const float4* R = rec[r_ahead].v;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) cp_async16(&s_rec[slot ^ 1][tid][k], R + k);
+                    if (NRM) cp_async16(&s_nv[NRM ? (slot ^ 1) : 0][NRM ? tid : 0], bp.nrm + r_ahead);
                     s_r[slot ^ 1][tid] = r_ahead;
                     s_m[slot ^ 1][tid] = (uint8_t)m_ahead;
                 }
@@ -611,10 +665,17 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         __syncthreads();                                     // the ring is free for the next list
     };
 
+    // voxel normal of staged record j (zero without normals)
+    auto staged_nv = [&](int slot, uint32_t j) {
+        return NRM ? s_nv[NRM ? slot : 0][NRM ? j : 0] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    };
+    constexpr int NV = GradLayout<NRM>::NV;
+    constexpr int GS = GradLayout<NRM>::STRIDE;
+
     // Lockstep walk of actor o's sub-list: lanes not yet done composite the segments inside
     // their interval [a, b] of that actor into pt, with the stop rule (and, with G, the
     // per-record gradients reduced across the warp).
-    auto walk_actor = [&](Pix& pt, int o, float a, float b, auto grad) {
+    auto walk_actor = [&](Pix<NRM>& pt, int o, float a, float b, auto grad) {
         constexpr bool G = decltype(grad)::value;
         const OctParams& P = vo[o];
         float d[3];
@@ -625,10 +686,10 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 if (__all_sync(0xffffffffu, pt.done)) return true;
                 const uint32_t j = c0 + (uint32_t)(__ffs(m) - 1);
                 m &= m - 1;
-                float acc[11];
+                float acc[NV];
                 if (G) {
 #pragma unroll
-                    for (int i = 0; i < 11; ++i) acc[i] = 0.0f;
+                    for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
                 }
                 bool hit = false;
                 if (!pt.done) {
@@ -640,15 +701,16 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                         t1 = fminf(t1, b);
                         if (t1 > t0) {
                             const float rel[3] = {g.x, g.y, g.z};
-                            add_segment<G, true, KS>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
-                                                     s_rec[slot][j][3], rel, d, t0, t1, acc);
+                            add_segment<G, true, KS, NRM>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
+                                                          s_rec[slot][j][3], staged_nv(slot, j), rel, d, t0, t1,
+                                                          acc);
                             hit = true;
                         }
                     }
                 }
                 if (G) {
                     const unsigned any = __ballot_sync(0xffffffffu, hit);
-                    if (any) warp_reduce_add(acc, grad_rec + (size_t)s_r[slot][j] * GSTRIDE);
+                    if (any) warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
                 }
             }
             return __all_sync(0xffffffffu, pt.done);
@@ -660,8 +722,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         const float a = s_iv[q][0][tid], b = s_iv[q][1][tid];
         const bool act = valid && b > a;
         if (__syncthreads_or(act) == 0) continue;
-        Pix pt;
+        Pix<NRM> pt;
         pt.C0 = pt.C1 = pt.C2 = pt.D = 0.0f;
+        if constexpr (NRM) pt.N0 = pt.N1 = pt.N2 = 0.0f;
         pt.T = 1.0f;
         pt.n = 0;
         pt.tests = 0;
@@ -678,6 +741,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             s_st[q][3][tid] = pt.D;
             s_st[q][4][tid] = pt.T;
             s_st[q][5][tid] = __int_as_float((int)pt.n);
+            if constexpr (NRM) {
+                s_st[q][NRM ? 6 : 0][tid] = pt.N0;
+                s_st[q][NRM ? 7 : 0][tid] = pt.N1;
+                s_st[q][NRM ? 8 : 0][tid] = pt.N2;
+            }
         }
     }
 
@@ -696,6 +764,12 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             const float pC0 = s_st[q][0][tid], pC1 = s_st[q][1][tid], pC2 = s_st[q][2][tid];
             const float pD = s_st[q][3][tid], pT = s_st[q][4][tid];
             const uint32_t pn = (uint32_t)__float_as_int(s_st[q][5][tid]);
+            float pN0 = 0.0f, pN1 = 0.0f, pN2 = 0.0f;
+            if (NRM) {
+                pN0 = s_st[q][NRM ? 6 : 0][tid];
+                pN1 = s_st[q][NRM ? 7 : 0][tid];
+                pN2 = s_st[q][NRM ? 8 : 0][tid];
+            }
             const bool stop_inside = ps.T * pT < bp.eps_stop;
             if (BWD || stop_inside) {
                 s_st[q][0][tid] = ps.C0;
@@ -703,6 +777,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 s_st[q][2][tid] = ps.C2;
                 s_st[q][3][tid] = ps.D;
                 s_st[q][4][tid] = ps.T;
+                if constexpr (NRM) {
+                    s_st[q][NRM ? 6 : 0][tid] = ps.N0;
+                    s_st[q][NRM ? 7 : 0][tid] = ps.N1;
+                    s_st[q][NRM ? 8 : 0][tid] = ps.N2;
+                }
             }
             s_st[q][5][tid] = stop_inside ? 2.0f : 1.0f;
             if (stop_inside) {
@@ -712,21 +791,27 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 ps.C1 = fmaf(ps.T, pC1, ps.C1);
                 ps.C2 = fmaf(ps.T, pC2, ps.C2);
                 ps.D = fmaf(ps.T, pD, ps.D);
+                if constexpr (NRM) {
+                    ps.N0 = fmaf(ps.T, pN0, ps.N0);
+                    ps.N1 = fmaf(ps.T, pN1, ps.N1);
+                    ps.N2 = fmaf(ps.T, pN2, ps.N2);
+                }
                 ps.T = ps.T * pT;
                 ps.n += pn;
             }
         } else {
-            walk_actor_lane<BWD, KS>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc, grad_rec);
+            walk_actor_lane<BWD, KS, NRM>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc,
+                                          grad_rec);
         }
     };
 
     stream(s_sub[0], s_sub[1], [&](int slot, uint32_t c0, unsigned m) -> bool {
         // one record of the batch, visited by the whole warp: actor entries, stop rule, gradients
         auto visit = [&](uint32_t j) {
-            float acc[11];
+            float acc[NV];
             if (BWD) {
 #pragma unroll
-                for (int i = 0; i < 11; ++i) acc[i] = 0.0f;
+                for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
             }
             bool contributed = false;
             const float4 g = s_rec[slot][j][0];
@@ -738,10 +823,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 t_out = fminf(t_out, t_far);
                 if (t_out > t_in) {
                     const float4 da = s_rec[slot][j][1], dd = s_rec[slot][j][2], col = s_rec[slot][j][3];
+                    const float4 nv = staged_nv(slot, j);
                     float cur = fmaxf(t_in, tau_cur);
                     while (nxt.o >= 0 && nxt.a < t_out && !ps.done) {
                         if (nxt.a > cur) {
-                            add_segment<BWD, true, KS>(ps, bw, bp, da, dd, col, rel, db_, cur, nxt.a, acc);
+                            add_segment<BWD, true, KS, NRM>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, nxt.a, acc);
                             contributed = true;
                             if (ps.done) break;
                         }
@@ -752,7 +838,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                         ps.boxes += n_ta;
                     }
                     if (!ps.done && t_out > cur) {
-                        add_segment<BWD, true, KS>(ps, bw, bp, da, dd, col, rel, db_, cur, t_out, acc);
+                        add_segment<BWD, true, KS, NRM>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, t_out, acc);
                         contributed = true;
                     }
                 }
@@ -760,7 +846,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             if (BWD) {
                 // every lane visits record j of the batch together: reduce across the warp
                 const unsigned any = __ballot_sync(0xffffffffu, contributed);
-                if (any) warp_reduce_add(acc, grad_rec + (size_t)s_r[slot][j] * GSTRIDE);
+                if (any) warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
             }
         };
         bool warp_done = false;
@@ -808,9 +894,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             const float tau1 = seg_tau<false, KS>(da1, dd1, col1.w, r1, db_, u1, v1, bp.K, bp.inv_k, bp.activation,
                                                   nullptr);
             ps.tests += live ? 1u : 0u;
-            if (h0) composite_tau(ps, tau0, col0, u0, v0, bp.eps_stop);
+            if (h0) composite_tau<NRM>(ps, tau0, col0, staged_nv(slot, j0), u0, v0, bp.eps_stop);
             ps.tests += (live && !ps.done) ? 1u : 0u;
-            if (h1 && !ps.done) composite_tau(ps, tau1, col1, u1, v1, bp.eps_stop);
+            if (h1 && !ps.done) composite_tau<NRM>(ps, tau1, col1, staged_nv(slot, j1), u1, v1, bp.eps_stop);
         }
         return warp_done || __all_sync(0xffffffffu, ps.done);
     });
@@ -828,12 +914,17 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         const int status = valid ? (int)s_st[q][5][tid] : 0;
         const bool act = BWD ? status >= 1 : status == 2;
         if (__syncthreads_or(act) == 0) continue;
-        Pix pt;
+        Pix<NRM> pt;
         pt.C0 = act ? s_st[q][0][tid] : 0.0f;
         pt.C1 = act ? s_st[q][1][tid] : 0.0f;
         pt.C2 = act ? s_st[q][2][tid] : 0.0f;
         pt.D = act ? s_st[q][3][tid] : 0.0f;
         pt.T = act ? s_st[q][4][tid] : 1.0f;
+        if constexpr (NRM) {
+            pt.N0 = act ? s_st[q][6][tid] : 0.0f;
+            pt.N1 = act ? s_st[q][7][tid] : 0.0f;
+            pt.N2 = act ? s_st[q][8][tid] : 0.0f;
+        }
         pt.n = 0;
         pt.tests = 0;
         pt.boxes = 0;
@@ -845,6 +936,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             ps.C1 = pt.C1;
             ps.C2 = pt.C2;
             ps.D = pt.D;
+            if constexpr (NRM) {
+                ps.N0 = pt.N0;
+                ps.N1 = pt.N1;
+                ps.N2 = pt.N2;
+            }
             ps.T = pt.T;
             ps.n += pt.n;
         }
@@ -872,6 +968,11 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         fp.alpha[lpix] = 1.0f - ps.T;
         n_seg[pix] = ps.n;
         t_final[pix] = ps.T;
+        if constexpr (NRM) {
+            fp.normal[lpix * 3 + 0] = ps.N0;
+            fp.normal[lpix * 3 + 1] = ps.N1;
+            fp.normal[lpix * 3 + 2] = ps.N2;
+        }
     }
 }
 
@@ -909,6 +1010,7 @@ struct ShBwdParams {
     float* d_sh[DV_MAX_OCTREES];
 };
 
+template <bool NRM>
 __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdParams sp,
                                                 const uint32_t* __restrict__ sorted_g, int64_t n_vis,
                                                 const VoxRec* __restrict__ rec, const float* __restrict__ grad_rec) {
@@ -928,12 +1030,45 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
     }
     const OctParams& P = bp.octs[view * bp.n_oct + lo];
     const int64_t v = gv - bp.vox_offset[lo];
-    const float* gr = grad_rec + (size_t)r * GSTRIDE;
+    const float* gr = grad_rec + (size_t)r * GradLayout<NRM>::STRIDE;
     float* d_dens = sp.d_dens[lo];
     float* d_sh = sp.d_sh[lo];
     // several views may touch the same voxel: accumulate with atomics (16-byte vector
     // atomics where the caller's rows are 16-byte aligned)
-    const float4 g03 = *reinterpret_cast<const float4*>(gr), g47 = *reinterpret_cast<const float4*>(gr + 4);
+    float4 g03 = *reinterpret_cast<const float4*>(gr), g47 = *reinterpret_cast<const float4*>(gr + 4);
+    if (NRM) {
+        // through the voxel normal n_w = R n_l, n_l = -g / |g| with g the corner-difference
+        // gradient (as in the records kernel): dL/dg = -(dL/dn_l - n_l (n_l . dL/dn_l)) / |g|,
+        // and each corner enters g_a with sign + on the high side of axis a, - on the low side
+        const float dw0 = gr[11], dw1 = gr[12], dw2 = gr[13];
+        if (d_dens && (dw0 != 0.0f || dw1 != 0.0f || dw2 != 0.0f)) {
+            const float4 da = rec[r].v[1], db = rec[r].v[2];
+            const float gx = (da.y + da.w + db.y + db.w) - (da.x + da.z + db.x + db.z);
+            const float gy = (da.z + da.w + db.z + db.w) - (da.x + da.y + db.x + db.y);
+            const float gz = (db.x + db.y + db.z + db.w) - (da.x + da.y + da.z + da.w);
+            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+            if (g2 > 0.0f) {
+                const float ig = rsqrtf(g2);
+                const float nl[3] = {-gx * ig, -gy * ig, -gz * ig};
+                float dn[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    dn[k] = fmaf(P.Rw[0 * 3 + k], dw0, fmaf(P.Rw[1 * 3 + k], dw1, P.Rw[2 * 3 + k] * dw2));
+                const float nd = fmaf(nl[0], dn[0], fmaf(nl[1], dn[1], nl[2] * dn[2]));
+                const float dgx = -(dn[0] - nl[0] * nd) * ig, dgy = -(dn[1] - nl[1] * nd) * ig,
+                            dgz = -(dn[2] - nl[2] * nd) * ig;
+                // corner c = (x, y, z) bits: + dg_a where bit a is set, - where clear
+                g03.x += -dgx - dgy - dgz;
+                g03.y += dgx - dgy - dgz;
+                g03.z += -dgx + dgy - dgz;
+                g03.w += dgx + dgy - dgz;
+                g47.x += -dgx - dgy + dgz;
+                g47.y += dgx - dgy + dgz;
+                g47.z += -dgx + dgy + dgz;
+                g47.w += dgx + dgy + dgz;
+            }
+        }
+    }
     if (d_dens) {
         float* dd = d_dens + v * 8;
         if ((reinterpret_cast<uintptr_t>(dd) & 15) == 0) {
@@ -989,6 +1124,38 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
     }
 }
 
+template <bool NRM>
+void composite_fwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val, const uint8_t* pair_mask,
+                     const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, float* rgb,
+                     float* depth, float* alpha, uint32_t* n_seg, float* t_final, unsigned long long* work,
+                     cudaStream_t s) {
+    if (bp.K == 1)
+        k_composite<false, 1, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha, n_seg, t_final,
+            nullptr, nullptr, nullptr, nullptr, nullptr, work);
+    else
+        k_composite<false, 0, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha, n_seg, t_final,
+            nullptr, nullptr, nullptr, nullptr, nullptr, work);
+}
+
+template <bool NRM>
+void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val, const uint8_t* pair_mask,
+                     const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, const float* rgb,
+                     const float* depth, const float* t_final, const float* g_rgb, const float* g_depth,
+                     const float* g_alpha, const float* g_normal, float* grad_rec, cudaStream_t s) {
+    if (bp.K == 1)
+        k_composite<true, 1, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
+            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+            g_normal, grad_rec, nullptr);
+    else
+        k_composite<true, 0, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
+            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+            g_normal, grad_rec, nullptr);
+}
+
 }  // namespace
 
 cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
@@ -996,14 +1163,12 @@ cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const
                                  const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
                                  float* t_final, unsigned long long* work, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
-    if (bp.K == 1)
-        k_composite<false, 1><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range,
-                                                                    vis_start, tile_order, rgb, depth, alpha, n_seg,
-                                                                    t_final, nullptr, nullptr, nullptr, nullptr, work);
+    if (bp.normals)
+        composite_fwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha,
+                              n_seg, t_final, work, s);
     else
-        k_composite<false, 0><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(bp, rec, pair_val, pair_mask, tile_range,
-                                                                    vis_start, tile_order, rgb, depth, alpha, n_seg,
-                                                                    t_final, nullptr, nullptr, nullptr, nullptr, work);
+        composite_fwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha,
+                               n_seg, t_final, work, s);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1012,24 +1177,21 @@ cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, const float* rgb, const float* depth,
                                  const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
-                                 float* grad_rec, cudaStream_t s) {
+                                 const float* g_normal, float* grad_rec, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
-    if (bp.K == 1)
-        k_composite<true, 1><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
-            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
-            grad_rec, nullptr);
+    if (g_normal)
+        composite_bwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, t_final,
+                              g_rgb, g_depth, g_alpha, g_normal, grad_rec, s);
     else
-        k_composite<true, 0><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
-            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
-            grad_rec, nullptr);
+        composite_bwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, t_final,
+                               g_rgb, g_depth, g_alpha, nullptr, grad_rec, s);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
-                          const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s) {
+                          const float* grad_rec, bool with_normals, float* const* d_dens, float* const* d_sh,
+                          cudaStream_t s) {
     if (n_vis <= 0) return cudaSuccess;
     ShBwdParams sp;
     sp.bp = bp;
@@ -1037,7 +1199,10 @@ cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64
         sp.d_dens[o] = (d_dens && o < bp.n_oct) ? d_dens[o] : nullptr;
         sp.d_sh[o] = (d_sh && o < bp.n_oct) ? d_sh[o] : nullptr;
     }
-    k_sh_bwd<<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(sp, sorted_g, n_vis, rec, grad_rec);
+    if (with_normals)
+        k_sh_bwd<true><<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(sp, sorted_g, n_vis, rec, grad_rec);
+    else
+        k_sh_bwd<false><<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(sp, sorted_g, n_vis, rec, grad_rec);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 // Per (view, octree) constants, computed on the host in double and rounded once.
 struct OctParams {
     float A[9];          // unit camera-frame ray direction -> octree-local direction (R_i^T R_c)
+    float Rw[9];         // octree-local -> world rotation (R_i), for voxel normals
     float M[9];          // octree-local point -> camera frame, rotation (R_c^T R_i)
     float m[3];          //   ... translation (R_c^T (t_i - t_c))
     float o_loc[3];      // camera centre in the octree's local frame (R_i^T (t_c - t_i))
@@ -40,6 +41,7 @@ struct ViewParams {
     float* rgb;          // this view's outputs [H*W][3], [H*W], [H*W] (device)
     float* depth;
     float* alpha;
+    float* normal;       // [H*W][3] normal state N (world frame), or null when normals are not rendered
 };
 
 // Shared by every kernel of a render call (passed by value).
@@ -53,11 +55,13 @@ struct BatchParams {
     int32_t oct_shift;   // 3 * Lkey
     int32_t view_shift;  // oct_shift + bits(n_oct)
     int32_t n_tiles;     // over all views
+    int32_t normals;     // the call renders the normal state N (records carry voxel normals)
     int64_t n_vox;       // voxels of one view (all octrees)
     int64_t vox_offset[DV_MAX_OCTREES + 1];
     int32_t tile_base[DV_MAX_VIEWS + 1];
     const ViewParams* views;  // device [n_view]
     const OctParams* octs;    // device [n_view][n_oct]
+    const float4* nrm;        // device [n_vis]: voxel normal (world frame) of each record, when normals
 };
 
 static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
@@ -124,8 +128,8 @@ cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect,
 cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
                            uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
 cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
-                           const uint64_t* rect, VoxRec* rec, uint32_t* cnt_sorted, uint64_t* rect_sorted,
-                           cudaStream_t s);
+                           const uint64_t* rect, VoxRec* rec, float4* nrm, uint32_t* cnt_sorted,
+                           uint64_t* rect_sorted, cudaStream_t s);
 // start of every (view, octree) group in depth-key order: vis_start[n_view * n_oct + 1]
 cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, int64_t n_vis, uint32_t* vis_start,
                              cudaStream_t s);
@@ -142,13 +146,16 @@ cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
                                  float* t_final, unsigned long long* work, cudaStream_t s);
+// with g_normal (the call rendered normals): gradient rows of 16 floats (8 densities, 3 colour, 3 normal, 2 pad),
+// else of 12 (8 densities, 3 colour, 1 pad)
 cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, const float* rgb, const float* depth,
                                  const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
-                                 float* grad_rec, cudaStream_t s);
+                                 const float* g_normal, float* grad_rec, cudaStream_t s);
 cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
-                          const float* grad_rec, float* const* d_dens, float* const* d_sh, cudaStream_t s);
+                          const float* grad_rec, bool with_normals, float* const* d_dens, float* const* d_sh,
+                          cudaStream_t s);
 
 // render of views whose outputs live in separate device buffers (serving loop)
 dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,

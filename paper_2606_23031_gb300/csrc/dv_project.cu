@@ -247,7 +247,8 @@ __device__ __forceinline__ void sh_eval_basis(int deg, float x, float y, float z
 __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchParams bp,
                                                  const uint32_t* __restrict__ sorted_g, int64_t n_vis,
                                                  const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ rect,
-                                                 VoxRec* __restrict__ rec, uint32_t* __restrict__ cnt_sorted,
+                                                 VoxRec* __restrict__ rec, float4* __restrict__ nrm,
+                                                 uint32_t* __restrict__ cnt_sorted,
                                                  uint64_t* __restrict__ rect_sorted) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
@@ -300,6 +301,21 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
     R.v[2] = db;
     R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);
     rec[r] = R;
+    if (nrm) {
+        // voxel normal: minus the direction of the trilinear density gradient at the voxel centre
+        // (per axis: the four corners on its high side minus the four on its low side), rotated
+        // into the world frame by the octree's pose
+        const float gxl = (da.y + da.w + db.y + db.w) - (da.x + da.z + db.x + db.z);
+        const float gyl = (da.z + da.w + db.z + db.w) - (da.x + da.y + db.x + db.y);
+        const float gzl = (db.x + db.y + db.z + db.w) - (da.x + da.y + da.z + da.w);
+        const float g2 = fmaf(gxl, gxl, fmaf(gyl, gyl, gzl * gzl));
+        const float s = g2 > 0.0f ? -rsqrtf(g2) : 0.0f;
+        const float nl[3] = {gxl * s, gyl * s, gzl * s};
+        float nw[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nw[k] = fmaf(P.Rw[k * 3 + 0], nl[0], fmaf(P.Rw[k * 3 + 1], nl[1], P.Rw[k * 3 + 2] * nl[2]));
+        nrm[r] = make_float4(nw[0], nw[1], nw[2], 0.0f);
+    }
     cnt_sorted[r] = cnt[g];
     rect_sorted[r] = rect[g];
 }
@@ -469,10 +485,10 @@ cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint6
 }
 
 cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
-                           const uint64_t* rect, VoxRec* rec, uint32_t* cnt_sorted, uint64_t* rect_sorted,
-                           cudaStream_t s) {
+                           const uint64_t* rect, VoxRec* rec, float4* nrm, uint32_t* cnt_sorted,
+                           uint64_t* rect_sorted, cudaStream_t s) {
     if (n_vis <= 0) return cudaSuccess;
-    k_records<<<nblk(n_vis, 256), 256, 0, s>>>(bp, sorted_g, n_vis, cnt, rect, rec, cnt_sorted, rect_sorted);
+    k_records<<<nblk(n_vis, 256), 256, 0, s>>>(bp, sorted_g, n_vis, cnt, rect, rec, nrm, cnt_sorted, rect_sorted);
     count_launches(1);
     return cudaGetLastError();
 }
