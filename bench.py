@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-normals", action="store_true", help="skip the fwd+bwd timing with the normal state N")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     p.add_argument("--seed", type=int, default=0)
@@ -437,7 +438,58 @@ def run_ours(args):
         ms_f += a.elapsed_time(b)
     sync_all()
 
-    ms_step, ms_fwd = max_over_ranks([ms / args.steps, ms_f / args.steps], world, dev)
+    # ---- timed fwd+bwd with the normal state N (rendered and differentiated as well) ----
+    g_n = None
+    ms_n = 0.0
+    if not args.no_normals:
+        g_n = torch.randn((n_pix, 3), generator=torch.Generator(dev).manual_seed(args.seed + 7), device=dev)
+
+        def step_n():
+            out = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True, normals=True)
+            dv.dv_render_backward(out[-1], g_rgb, g_d, g_a, d_dens, d_sh, d_normal=g_n)
+            return out[-1]
+
+        for _ in range(3):
+            step_n().free()
+        sync_all()
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = step_n()
+            b.record(stream)
+            b.synchronize()
+            ms_n += a.elapsed_time(b)
+            st.free()
+        sync_all()
+
+    # ---- sky composite of Eq. 2 on the frame (1024 x 2048 equirectangular map): forward and backward ----
+    ms_sky_f = ms_sky_b = 0.0
+    if not args.no_normals:
+        env = torch.rand((1024, 2048, 3), generator=torch.Generator(dev).manual_seed(args.seed + 9), device=dev)
+        rgb0, _, alpha0, _ = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx)
+        sky_out = torch.empty_like(rgb0)
+        d_env = torch.zeros_like(env)
+        d_alpha = torch.zeros_like(alpha0)
+        for _ in range(3):
+            dv.dv_sky_composite(cams, env, rgb0, alpha0, ctx=ctx, out=sky_out)
+            dv.dv_sky_backward(cams, env, alpha0, g_rgb, d_env, d_alpha, ctx=ctx)
+        sync_all()
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            dv.dv_sky_composite(cams, env, rgb0, alpha0, ctx=ctx, out=sky_out)
+            b.record(stream)
+            dv.dv_sky_backward(cams, env, alpha0, g_rgb, d_env, d_alpha, ctx=ctx)
+            c.record(stream)
+            c.synchronize()
+            ms_sky_f += a.elapsed_time(b)
+            ms_sky_b += b.elapsed_time(c)
+        sync_all()
+
+    ms_step, ms_fwd, ms_nrm = max_over_ranks([ms / args.steps, ms_f / args.steps, ms_n / args.steps], world, dev)
     value = whole_job_mpix_s(world, n_pix, ms_step)
     value_fwd = whole_job_mpix_s(world, n_pix, ms_fwd)
 
@@ -547,6 +599,15 @@ def run_ours(args):
                            "l2": "flushed between timed steps (512 MB write outside the step events)",
                            "visible_voxels": stats["n_visible"], "pairs": stats["n_pairs"]},
                 "fwd": {"value": value_fwd, "unit": "Mpix/s", "ms_per_step": ms_fwd},
+                "sky": None if args.no_normals else {
+                    "what": "sky composite of Eq. 2 on the frame, 1024x2048 equirectangular map",
+                    "fwd_us": 1e3 * ms_sky_f / args.steps, "bwd_us": 1e3 * ms_sky_b / args.steps,
+                    "fwd_gbs": 28.0 * n_pix / (ms_sky_f / args.steps * 1e-3) / 1e9,
+                    "fwd_frac": 28.0 * n_pix / (ms_sky_f / args.steps * 1e-3) / 1e9 / pk["hbm_gbs"],
+                    "bytes_per_pixel": {"fwd": 28, "bwd": 24}},
+                "normals": None if args.no_normals else {
+                    "value": whole_job_mpix_s(world, n_pix, ms_nrm), "unit": "Mpix/s", "ms_per_step": ms_nrm,
+                    "what": "fwd+bwd also rendering the normal state N and back-propagating a gradient on it"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
                 "serving": serving,
                 "gpu_launches_per_step": launches / max(args.steps, 1), "wall_s_timed": wall,

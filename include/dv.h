@@ -198,6 +198,34 @@ dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* state, const float* 
 /* Releases a saved state (stream-ordered on the stream of its render call). */
 void dv_state_free(dv_state* state);
 
+/*
+ * Sky composite (Sec. 3.2 "Sky Modeling", Eq. 2): out = rgb + (1 - alpha) *
+ * C_sky(d) per pixel, d the unit world direction of the pixel's ray, C_sky a
+ * bilinear lookup of an equirectangular environment map of the world frame
+ * (z up): column coordinate (atan2(d_y, d_x) + pi) / (2 pi) * env_w, row
+ * coordinate acos(d_z) / pi * env_h, texel values at texel centres, wrap-around
+ * in longitude, clamp to the first / last row in latitude.
+ *   cams[n_cam]   host array (only intrinsics and cam_to_world.R are used)
+ *   env           device [env_h][env_w][3]
+ *   rgb, alpha    device inputs as written by dv_render (concatenated per camera)
+ *   out           device output [sum H*W][3]; must not alias rgb when the render's
+ *                 saved state is still to be differentiated (its backward reads rgb)
+ * Errors: DV_ERR_INVALID_ARG / DV_ERR_INVALID_POSE / DV_ERR_CAPACITY before any
+ * work is enqueued.
+ */
+dv_status dv_sky_composite(dv_ctx* ctx, const dv_camera* cams, int32_t n_cam, const float* env, int32_t env_h,
+                           int32_t env_w, const float* rgb, const float* alpha, float* out, void* stream);
+
+/*
+ * Backward of dv_sky_composite for dL/d out (device [sum H*W][3]): ADDS
+ * dL/d env into d_env ([env_h][env_w][3], atomics; NULL = skip) and ADDS
+ * -dL/d out . C_sky into d_alpha ([sum H*W]; NULL = skip) -- pass that d_alpha,
+ * together with dL/d rgb = dL/d out, on to dv_render_backward.
+ */
+dv_status dv_sky_backward(dv_ctx* ctx, const dv_camera* cams, int32_t n_cam, const float* env, int32_t env_h,
+                          int32_t env_w, const float* alpha, const float* d_out, float* d_env, float* d_alpha,
+                          void* stream);
+
 /* Sizes of a saved state: visible voxels, (tile, voxel) pairs and tiles of view
  * `view`, or of the whole call for view = -1 (per-view figures synchronise the
  * state's stream).  Returns DV_ERR_INVALID_ARG for a bad index. */

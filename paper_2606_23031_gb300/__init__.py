@@ -23,7 +23,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libdv.so")
-SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu"]
+SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV_ERR_TIMEOUT, DV_ERR_NOMEM = range(7)
@@ -147,6 +147,12 @@ def load(path: str | None = None):
                                                C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                                C.c_void_p]
     lib.dv_render_backward_normals.restype = C.c_int
+    lib.dv_sky_composite.argtypes = [C.c_void_p, C.POINTER(dv_camera), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dv_sky_composite.restype = C.c_int
+    lib.dv_sky_backward.argtypes = [C.c_void_p, C.POINTER(dv_camera), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dv_sky_backward.restype = C.c_int
     lib.dv_state_free.argtypes = [C.c_void_p]
     lib.dv_state_free.restype = None
     lib.dv_state_stats.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -523,6 +529,33 @@ def render(octrees, poses, cams, opts=None, dens=None, sh=None, normals=False):
     dens = [o.dens for o in octrees] if dens is None else dens
     sh = [o.sh for o in octrees] if sh is None else sh
     return _RenderFn.apply((octrees, poses, cams, opts or make_opts(), normals), *dens, *sh)
+
+
+def dv_sky_composite(cams, env, rgb, alpha, *, ctx: Context | None = None, out=None, stream=None):
+    """Sky composite of Eq. 2: returns rgb + (1 - alpha) * C_sky(d) ([P,3]) for an equirectangular
+    world-frame map ``env`` ([He, We, 3], device)."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    cam_arr = (dv_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+    He, We = int(env.shape[0]), int(env.shape[1])
+    out = torch.empty_like(rgb) if out is None else out
+    P = rgb.shape[0]
+    p = lambda t: C.c_void_p(t.data_ptr() if P else None)
+    ctx.check(lib.dv_sky_composite(ctx.handle, cam_arr, len(cams), C.c_void_p(env.data_ptr()), He, We, p(rgb),
+                                   p(alpha), p(out), _stream_ptr(stream)))
+    return out
+
+
+def dv_sky_backward(cams, env, alpha, d_out, d_env=None, d_alpha=None, *, ctx: Context | None = None, stream=None):
+    """Adds dL/d env into ``d_env`` and -dL/d out . C_sky into ``d_alpha`` (either may be None)."""
+    lib = load()
+    ctx = ctx or default_context()
+    cam_arr = (dv_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+    He, We = int(env.shape[0]), int(env.shape[1])
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    ctx.check(lib.dv_sky_backward(ctx.handle, cam_arr, len(cams), ptr(env), He, We, ptr(alpha), ptr(d_out),
+                                  ptr(d_env), ptr(d_alpha), _stream_ptr(stream)))
 
 
 STATIC_MAX_VISIBLE = 1 << 17  # visible voxels per render call, summed over its views

@@ -822,6 +822,76 @@ dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* st, const float* d_r
 
 void dv_state_free(dv_state* st) { free_state(st); }
 
+// ---- sky composite (Eq. 2) ----
+
+static dv_status sky_views(dv_ctx* ctx, const dv_camera* cams, int32_t n_cam, int32_t env_h, int32_t env_w,
+                           std::vector<dv::SkyView>& out) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n_cam < 0 || n_cam > DV_MAX_VIEWS || (n_cam > 0 && !cams))
+        return fail(ctx, n_cam > DV_MAX_VIEWS ? DV_ERR_CAPACITY : DV_ERR_INVALID_ARG, "bad camera array");
+    if (env_h < 1 || env_w < 1 || (int64_t)env_h * env_w > ((int64_t)1 << 28))
+        return fail(ctx, DV_ERR_INVALID_ARG, "environment map size out of range");
+    out.resize((size_t)n_cam);
+    for (int v = 0; v < n_cam; ++v) {
+        const dv_camera& c = cams[v];
+        if (c.W < 0 || c.H < 0 || c.W > DV_MAX_IMAGE || c.H > DV_MAX_IMAGE || !(c.fx > 0.0f) || !(c.fy > 0.0f) ||
+            !std::isfinite(c.cx) || !std::isfinite(c.cy))
+            return fail(ctx, DV_ERR_INVALID_ARG, "bad camera");
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(c.cam_to_world.R[k])) return fail(ctx, DV_ERR_INVALID_POSE, "bad camera rotation");
+        dv::SkyView& s = out[v];
+        for (int k = 0; k < 9; ++k) s.R[k] = c.cam_to_world.R[k];
+        s.fx = c.fx;
+        s.fy = c.fy;
+        s.cx = c.cx;
+        s.cy = c.cy;
+        s.W = c.W;
+        s.H = c.H;
+    }
+    return DV_OK;
+}
+
+dv_status dv_sky_composite(dv_ctx* ctx, const dv_camera* cams, int32_t n_cam, const float* env, int32_t env_h,
+                           int32_t env_w, const float* rgb, const float* alpha, float* out, void* stream) {
+    std::vector<dv::SkyView> vs;
+    dv_status st = sky_views(ctx, cams, n_cam, env_h, env_w, vs);
+    if (st != DV_OK) return st;
+    int64_t pix = 0;
+    for (auto& v : vs) pix += (int64_t)v.W * v.H;
+    if (pix > 0 && (!env || !rgb || !alpha || !out)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t off = 0;
+    for (auto& v : vs) {
+        cudaError_t e = dv::launch_sky_fwd(v, env, env_h, env_w, rgb + off * 3, alpha + off, out + off * 3, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sky composite");
+        off += (int64_t)v.W * v.H;
+    }
+    return DV_OK;
+}
+
+dv_status dv_sky_backward(dv_ctx* ctx, const dv_camera* cams, int32_t n_cam, const float* env, int32_t env_h,
+                          int32_t env_w, const float* alpha, const float* d_out, float* d_env, float* d_alpha,
+                          void* stream) {
+    std::vector<dv::SkyView> vs;
+    dv_status st = sky_views(ctx, cams, n_cam, env_h, env_w, vs);
+    if (st != DV_OK) return st;
+    int64_t pix = 0;
+    for (auto& v : vs) pix += (int64_t)v.W * v.H;
+    if (pix > 0 && (!env || !alpha || !d_out)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t off = 0;
+    for (auto& v : vs) {
+        cudaError_t e = dv::launch_sky_bwd(v, env, env_h, env_w, alpha + off, d_out + off * 3, d_env,
+                                           d_alpha ? d_alpha + off : nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sky backward");
+        off += (int64_t)v.W * v.H;
+    }
+    return DV_OK;
+}
+
 dv_status dv_state_stats(const dv_state* st, int32_t view, int64_t* n_visible, int64_t* n_pairs, int64_t* n_tiles) {
     if (!st) return DV_ERR_INVALID_ARG;
     const BatchState& B = st->b;

@@ -157,6 +157,17 @@ cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64
                           const float* grad_rec, bool with_normals, float* const* d_dens, float* const* d_sh,
                           cudaStream_t s);
 
+// one camera of a sky composite: camera -> world rotation (row-major) and intrinsics
+struct SkyView {
+    float R[9];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+};
+cudaError_t launch_sky_fwd(const SkyView& v, const float* env, int He, int We, const float* rgb, const float* alpha,
+                           float* out, cudaStream_t s);
+cudaError_t launch_sky_bwd(const SkyView& v, const float* env, int He, int We, const float* alpha, const float* d_out,
+                           float* d_env, float* d_alpha, cudaStream_t s);
+
 // render of views whose outputs live in separate device buffers (serving loop)
 dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
                             const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,
