@@ -66,6 +66,7 @@ def _load():
         lib.orc_render.restype = C.c_int
         lib.orc_backward.restype = C.c_int
         lib.orc_pixel_segments.restype = C.c_int64
+        lib.orc_pixel_weights.restype = C.c_int64
         lib.orc_sh_basis.restype = None
         _lib = lib
     return _lib
@@ -213,6 +214,23 @@ def pixel_segments(octrees, poses, cam, u, v, cap=4096):
         raise RuntimeError("orc_pixel_segments failed")
     n = min(n, cap)
     return t0[:n], t1[:n], oi[:n], vi[:n]
+
+
+def pixel_weights(octrees, poses, cam, u, v, opts: Opts = Opts(), cap=65536):
+    """Composited segments of pixel (u, v) in front-to-back order: (octree [n], voxel [n],
+    weight T_k alpha_k [n]), ending at the early stop."""
+    lib = _load()
+    m = _Marshal(octrees, poses, cam, opts)
+    oi = np.zeros(cap, np.int32)
+    vi = np.zeros(cap, np.int64)
+    w = np.zeros(cap)
+    n = lib.orc_pixel_weights(m.oct, C.c_int(m.n), m.poses, C.byref(m.cam), C.byref(m.opts), C.c_int(u), C.c_int(v),
+                              C.c_int64(cap), oi.ctypes.data_as(C.c_void_p), vi.ctypes.data_as(C.c_void_p),
+                              w.ctypes.data_as(C.c_void_p))
+    if n < 0:
+        raise RuntimeError("orc_pixel_weights failed")
+    n = min(n, cap)
+    return oi[:n], vi[:n], w[:n]
 
 
 def sh_basis(deg, x, y, z):

@@ -750,5 +750,37 @@ int64_t orc_pixel_segments(const orc_octree* oct, int n_oct, const orc_pose* pos
     return n;
 }
 
+/* Compositing weights of pixel (u, v): for every segment that the forward
+ * composites (front to back, with the early stop), its octree, voxel and weight
+ * w_k = T_k alpha_k.  A feature f per voxel renders as F = sum_k w_k f(vox_k)
+ * (the RGB accumulation with the colour replaced by a feature, as used for
+ * feature fields); fusing 2-D features into voxels sums w_k F_pixel per voxel.
+ * Returns the number of composited segments (at most `cap` are written), or -1. */
+int64_t orc_pixel_weights(const orc_octree* oct, int n_oct, const orc_pose* poses, const orc_camera* cam,
+                          const orc_opts* opt, int u, int v, int64_t cap, int32_t* oct_idx, int64_t* vox_idx,
+                          double* weight) {
+    if (check_inputs(oct, n_oct, cam, opt) != ORC_OK) return -1;
+    seglist L = {0, 0, 0};
+    double o[3], d[3];
+    if (gather(oct, n_oct, poses, cam, u, v, &L, o, d) != ORC_OK) return -1;
+    double T = 1.0;
+    int64_t n = 0;
+    for (int64_t k = 0; k < L.n; ++k) {
+        seg_eval e;
+        const segment* sg = &L.s[k];
+        eval_segment(&oct[sg->oct], &poses[sg->oct], o, d, sg, opt, &e);
+        if (n < cap) {
+            oct_idx[n] = sg->oct;
+            vox_idx[n] = sg->vox;
+            weight[n] = T * e.alpha;
+        }
+        ++n;
+        T *= (1.0 - e.alpha);
+        if (T < opt->eps_stop) break;
+    }
+    free(L.s);
+    return n;
+}
+
 /* Test helper: the real SH basis values used by the oracle. */
 void orc_sh_basis(int deg, double x, double y, double z, double* Y) { sh_basis(deg, x, y, z, Y); }

@@ -680,3 +680,39 @@ def test_backward_through_normals_matches_central_differences(K):
             assert dd[oi][v, c] == pytest.approx((lp - lm) / (2 * h), rel=2e-5, abs=1e-8)
             checked += 1
     assert checked >= 16
+
+
+# ---------------------------------------------------------------------------
+# compositing weights (feature fields: RGB replaced by a per-voxel feature)
+# ---------------------------------------------------------------------------
+
+def test_pixel_weights_reproduce_colour_alpha_and_depth():
+    octs, poses = _comp_scene(seed=13)
+    cam = cam_looking((2.2, -1.2, 1.0), (0.0, 0.0, 0.0), W=9, H=7, fov=50.0)
+    opts = oracle.Opts(K=2, eps_stop=1e-3)
+    rgb, depth, alpha, nseg = oracle.render(octs, poses, cam, opts)
+    seen = 0
+    for v in range(cam.H):
+        for u in range(cam.W):
+            oi, vi, w = oracle.pixel_weights(octs, poses, cam, u, v, opts)
+            assert len(w) == nseg[v, u]
+            assert np.all(w >= 0)
+            np.testing.assert_allclose(w.sum(), alpha[v, u], rtol=1e-12, atol=1e-14)
+            seen += len(w) > 0
+    assert seen > 20
+
+
+def test_feature_of_a_constant_colour_scene_equals_its_render():
+    # degree-0 SH: every voxel's colour is its feature; F = sum w f must equal the rendered RGB
+    rng = np.random.default_rng(14)
+    ijk = np.argwhere(rng.uniform(size=(4, 4, 4)) < 0.6)
+    cols = rng.uniform(0.1, 0.9, size=(len(ijk), 3))
+    oc = one_voxel(2, ijk, rng.lognormal(0.0, 0.7, size=(len(ijk), 8)), cols)
+    cam = cam_looking((2.0, 1.1, 0.8), (0.0, 0.0, 0.0), W=8, H=6, fov=55.0)
+    opts = oracle.Opts(K=1, eps_stop=1e-4)
+    rgb, _, _, _ = oracle.render([oc], [pose64()], cam, opts)
+    feat = colour_of(cols)   # the colour each voxel actually renders with
+    for v in range(cam.H):
+        for u in range(cam.W):
+            _, vi, w = oracle.pixel_weights([oc], [pose64()], cam, u, v, opts)
+            np.testing.assert_allclose(w @ feat[vi] if len(w) else np.zeros(3), rgb[v, u], rtol=1e-12, atol=1e-14)
