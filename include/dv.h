@@ -199,6 +199,46 @@ dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* state, const float* 
 void dv_state_free(dv_state* state);
 
 /*
+ * Compositing weights of a saved render, for feature fields (Sec. 4, "3D
+ * Semantic Segmentation": RGB accumulation with the colour replaced by a
+ * per-voxel feature, and 2-D features fused into the voxels).  For pixel p
+ * (concatenated over the call's views like rgb), the segments the forward
+ * composited, with voxel index v (within the concatenation of the octrees in
+ * call order: octree o's voxel j is sum_{i<o} n_vox_i + j) and weight
+ * w = T alpha, so that RGB = sum w c(v) and alpha = sum w.  A voxel cut by an
+ * actor box can appear twice in one pixel's list.
+ *
+ * dv_state_weight_offsets: writes the exclusive prefix of the per-pixel segment
+ * counts to offsets ([sum H*W + 1], device; pixel p owns slots
+ * [offsets[p], offsets[p+1])) and the total to *total (host).  Synchronises the
+ * stream.
+ * dv_state_weights: fills voxel[total] and weight[total] (device).  The replay
+ * uses the forward's arithmetic and stop rule, so it fills exactly the counted
+ * slots.
+ */
+dv_status dv_state_weight_offsets(dv_ctx* ctx, dv_state* state, int64_t* offsets, int64_t* total, void* stream);
+dv_status dv_state_weights(dv_ctx* ctx, dv_state* state, const int64_t* offsets, uint32_t* voxel, float* weight,
+                           void* stream);
+
+/*
+ * Feature render over a weights export: out[p][c] = sum over p's slots of
+ * weight * feat[voxel][c], for C channels (feat device [n_voxels][C], out
+ * device [n_pix][C]; voxel indices must be < the rows of feat).
+ */
+dv_status dv_features_render(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, const uint32_t* voxel,
+                             const float* weight, const float* feat, int32_t C, float* out, void* stream);
+
+/*
+ * Feature fusion over a weights export (the transpose of dv_features_render):
+ * ADDS weight * feat2d[p][c] into accum[voxel][c] and weight into wsum[voxel]
+ * (NULL = skip) for every slot of every pixel (atomics); accum / wsum is then
+ * the weighted mean of the 2-D features seen by each voxel.
+ */
+dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, const uint32_t* voxel,
+                           const float* weight, const float* feat2d, int32_t C, float* accum, float* wsum,
+                           void* stream);
+
+/*
  * Sky composite (Sec. 3.2 "Sky Modeling", Eq. 2): out = rgb + (1 - alpha) *
  * C_sky(d) per pixel, d the unit world direction of the pixel's ray, C_sky a
  * bilinear lookup of an equirectangular environment map of the world frame

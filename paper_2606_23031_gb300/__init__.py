@@ -23,7 +23,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libdv.so")
-SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu"]
+SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu", "dv_features.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV_ERR_TIMEOUT, DV_ERR_NOMEM = range(7)
@@ -147,6 +147,16 @@ def load(path: str | None = None):
                                                C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                                C.c_void_p]
     lib.dv_render_backward_normals.restype = C.c_int
+    lib.dv_state_weight_offsets.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]
+    lib.dv_state_weight_offsets.restype = C.c_int
+    lib.dv_state_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dv_state_weights.restype = C.c_int
+    lib.dv_features_render.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int32, C.c_void_p, C.c_void_p]
+    lib.dv_features_render.restype = C.c_int
+    lib.dv_features_fuse.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dv_features_fuse.restype = C.c_int
     lib.dv_sky_composite.argtypes = [C.c_void_p, C.POINTER(dv_camera), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dv_sky_composite.restype = C.c_int
@@ -529,6 +539,68 @@ def render(octrees, poses, cams, opts=None, dens=None, sh=None, normals=False):
     dens = [o.dens for o in octrees] if dens is None else dens
     sh = [o.sh for o in octrees] if sh is None else sh
     return _RenderFn.apply((octrees, poses, cams, opts or make_opts(), normals), *dens, *sh)
+
+
+class Weights:
+    """Compositing weights of a saved render: pixel p's (voxel, weight) slots are
+    [offsets[p], offsets[p+1]) of ``voxel`` (int32 view of uint32 indices) and ``weight``."""
+
+    def __init__(self, offsets, voxel, weight):
+        self.offsets, self.voxel, self.weight = offsets, voxel, weight
+
+    @property
+    def n_pix(self):
+        return self.offsets.numel() - 1
+
+
+def dv_state_weights(state: State, stream=None) -> Weights:
+    """The weights export of a saved render (two calls through the C ABI: offsets, then slots)."""
+    import torch
+    lib = load()
+    P = _state_pixels(state)
+    dev = torch.device("cuda", state.ctx.device)
+    offsets = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    total = C.c_int64()
+    state.ctx.check(lib.dv_state_weight_offsets(state.ctx.handle, state.handle, C.c_void_p(offsets.data_ptr()),
+                                                C.byref(total), _stream_ptr(stream)))
+    if P == 0:
+        offsets.zero_()
+    n = int(total.value)
+    voxel = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+    weight = torch.zeros(max(n, 1), dtype=torch.float32, device=dev)
+    state.ctx.check(lib.dv_state_weights(state.ctx.handle, state.handle, C.c_void_p(offsets.data_ptr()),
+                                         C.c_void_p(voxel.data_ptr()), C.c_void_p(weight.data_ptr()),
+                                         _stream_ptr(stream)))
+    return Weights(offsets, voxel[:n], weight[:n])
+
+
+def _state_pixels(state: State) -> int:
+    keep = state.keep
+    return int(keep[3].shape[0]) if keep is not None else 0
+
+
+def dv_features_render(w: Weights, feat, *, ctx: Context | None = None, out=None, stream=None):
+    """F [P, C] = sum over each pixel's slots of weight * feat[voxel] (feat [n_voxels, C], device)."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    Cc = int(feat.shape[1])
+    out = torch.empty((w.n_pix, Cc), dtype=torch.float32, device=feat.device) if out is None else out
+    ctx.check(lib.dv_features_render(ctx.handle, w.n_pix, C.c_void_p(w.offsets.data_ptr()),
+                                     C.c_void_p(w.voxel.data_ptr()), C.c_void_p(w.weight.data_ptr()),
+                                     C.c_void_p(feat.data_ptr()), Cc, C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def dv_features_fuse(w: Weights, feat2d, accum, wsum=None, *, ctx: Context | None = None, stream=None):
+    """Adds weight * feat2d[p] into accum[voxel] and weight into wsum[voxel] for every slot."""
+    lib = load()
+    ctx = ctx or default_context()
+    Cc = int(feat2d.shape[1])
+    ctx.check(lib.dv_features_fuse(ctx.handle, w.n_pix, C.c_void_p(w.offsets.data_ptr()),
+                                   C.c_void_p(w.voxel.data_ptr()), C.c_void_p(w.weight.data_ptr()),
+                                   C.c_void_p(feat2d.data_ptr()), Cc, C.c_void_p(accum.data_ptr()),
+                                   C.c_void_p(wsum.data_ptr()) if wsum is not None else None, _stream_ptr(stream)))
 
 
 def dv_sky_composite(cams, env, rgb, alpha, *, ctx: Context | None = None, out=None, stream=None):

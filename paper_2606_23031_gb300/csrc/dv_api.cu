@@ -507,6 +507,7 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     uint64_t* k1 = ar.alloc<uint64_t>((size_t)n_vis);
     uint32_t* g1 = ar.alloc<uint32_t>((size_t)n_vis);
     B.sorted_g = pool_alloc<uint32_t>(ctx, s, (size_t)n_vis, own, e);
+    bp.sorted_g = B.sorted_g;
     uint32_t* g0 = B.sorted_g;
     if (ar.err != cudaSuccess || e != cudaSuccess) {
         ar.release();
@@ -821,6 +822,69 @@ dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* st, const float* d_r
 }
 
 void dv_state_free(dv_state* st) { free_state(st); }
+
+// ---- compositing weights and feature fields ----
+
+dv_status dv_state_weight_offsets(dv_ctx* ctx, dv_state* st, int64_t* offsets, int64_t* total, void* stream) {
+    if (!ctx || !st || !total) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
+    *total = 0;
+    BatchState& B = st->b;
+    if (B.n_pix > 0 && !offsets) return fail(ctx, DV_ERR_INVALID_ARG, "NULL offsets");
+    if (B.n_pix == 0) return DV_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::Arena ar;
+    ar.pool = ctx->pool;
+    ar.stream = s;
+    cudaError_t e = dv::scan_u32_to_u64(B.n_seg, (uint64_t*)offsets, B.n_pix, (uint64_t*)(offsets + B.n_pix), ar, s);
+    ar.release();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(total, offsets + B.n_pix, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight offsets");
+    return DV_OK;
+}
+
+dv_status dv_state_weights(dv_ctx* ctx, dv_state* st, const int64_t* offsets, uint32_t* voxel, float* weight,
+                           void* stream) {
+    if (!ctx || !st) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
+    BatchState& B = st->b;
+    if (B.n_pix == 0 || B.n_vis == 0) return DV_OK;
+    if (!offsets || !voxel || !weight) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = dv::launch_composite_export(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order,
+                                                offsets, voxel, weight, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weights export");
+    return DV_OK;
+}
+
+dv_status dv_features_render(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, const uint32_t* voxel,
+                             const float* weight, const float* feat, int32_t C, float* out, void* stream) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n_pix < 0 || C < 1 || C > 65536) return fail(ctx, DV_ERR_INVALID_ARG, "bad pixel or channel count");
+    if (n_pix > 0 && (!offsets || !feat || !out)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = dv::launch_feat_render(n_pix, offsets, voxel, weight, feat, C, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "feature render");
+    return DV_OK;
+}
+
+dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, const uint32_t* voxel,
+                           const float* weight, const float* feat2d, int32_t C, float* accum, float* wsum,
+                           void* stream) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n_pix < 0 || C < 1 || C > 65536) return fail(ctx, DV_ERR_INVALID_ARG, "bad pixel or channel count");
+    if (n_pix > 0 && (!offsets || !feat2d || !accum)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = dv::launch_feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "feature fusion");
+    return DV_OK;
+}
 
 // ---- sky composite (Eq. 2) ----
 

@@ -83,6 +83,15 @@ struct Bwd<true> : BwdBase {
     float gN0, gN1, gN2, Nf0, Nf1, Nf2;  // normal state: upstream gradient and final value
 };
 
+// per-lane writer of the composited segments' (voxel, weight) list (weights export)
+struct ExportSink {
+    uint32_t* vid;             // [total] voxel index within the view's concatenated octrees
+    float* w;                  // [total] T alpha
+    const uint32_t* sorted_g;  // record -> view * n_vox + voxel
+    int64_t base, voff;        // first slot of this pixel; view * n_vox
+    uint32_t n, lim;           // written so far; this pixel's slots
+};
+
 struct ActInt {
     int o;  // octree index (-1: none)
     int q;  // slot in the tile's actor list
@@ -242,13 +251,20 @@ __device__ __forceinline__ void composite_tau(Pix<NRM>& ps, float tau, float4 co
 
 // Composites one segment (with the stop test when STOP); with GRAD also adds
 // this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
-template <bool GRAD, bool STOP, int KS, bool NRM>
+template <bool GRAD, bool STOP, int KS, bool NRM, bool WEX = false>
 __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp, float4 da, float4 db,
                                             float4 col, float4 nv, const float* rel, const float* d, float t0,
-                                            float t1, float* acc) {
+                                            float t1, float* acc, uint32_t r = 0, ExportSink* ex = nullptr) {
     float dtd[8];
     const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
     const float w = composite_step<NRM>(ps, tau, col, nv, t0, t1);
+    if constexpr (WEX) {
+        if (ex->n < ex->lim) {
+            ex->vid[ex->base + ex->n] = (uint32_t)((int64_t)ex->sorted_g[r] - ex->voff);
+            ex->w[ex->base + ex->n] = w;
+        }
+        ex->n += 1;
+    }
     if (GRAD) {
         const float mid = 0.5f * (t0 + t1);
         const float Tn = ps.T;
@@ -363,12 +379,12 @@ __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
 
 // Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
 // NTA lockstep slots).
-template <bool GRAD, int KS, bool NRM>
+template <bool GRAD, int KS, bool NRM, bool WEX>
 __device__ __noinline__ void walk_actor_lane(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp,
                                              const OctParams* __restrict__ vo, const ActInt& it,
                                              const uint32_t* __restrict__ pval, const uint8_t* __restrict__ pmask,
                                              uint32_t wbit, const VoxRec* __restrict__ rec, uint32_t q0, uint32_t q1,
-                                             const float* dc, float* grad_rec) {
+                                             const float* dc, float* grad_rec, ExportSink* ex) {
     const OctParams& P = vo[it.o];
     float d[3];
     rotate(P.A, dc, d);
@@ -389,8 +405,8 @@ __device__ __noinline__ void walk_actor_lane(Pix<NRM>& ps, const Bwd<NRM>& bw, c
 #pragma unroll
         for (int c = 0; c < GradLayout<NRM>::NV; ++c) acc[c] = 0.0f;
         const float4 nv = NRM ? __ldg(bp.nrm + r) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        add_segment<GRAD, true, KS, NRM>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), nv, rel, d, t0, t1,
-                                         acc);
+        add_segment<GRAD, true, KS, NRM, WEX>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), nv, rel, d, t0,
+                                              t1, acc, r, ex);
         if (GRAD) atomic_grad<NRM>(grad_rec, r, acc);
     }
 }
@@ -418,8 +434,10 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 #define DV_BWD_MIN_BLOCKS 4
 #endif
 
-template <bool BWD, int KS, bool NRM>
-__global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
+// BWD: replay with gradients.  WEX: replay that writes every composited segment's (voxel,
+// weight) into the pixel's slots of the weights export (no outputs, no gradients).
+template <bool BWD, int KS, bool NRM, bool WEX>
+__global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
                                                         const uint8_t* __restrict__ pmask,
@@ -433,7 +451,10 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                                                         const float* __restrict__ g_alpha,
                                                         const float* __restrict__ g_normal,
                                                         float* __restrict__ grad_rec,
-                                                        unsigned long long* __restrict__ work) {
+                                                        unsigned long long* __restrict__ work,
+                                                        const int64_t* __restrict__ ex_off,
+                                                        uint32_t* __restrict__ ex_vid, float* __restrict__ ex_w) {
+    constexpr bool REPLAY = BWD || WEX;  // phase 3 replays every actor interval the ray reached
     __shared__ float4 s_rec[2][CT_THREADS][4];
     __shared__ float4 s_nv[NRM ? 2 : 1][NRM ? CT_THREADS : 1];  // voxel normals of the staged records
     __shared__ uint32_t s_r[2][CT_THREADS];
@@ -500,6 +521,16 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     ps.tests = 0;
     ps.boxes = 0;
     ps.done = !valid;
+    ExportSink ex;
+    ex.n = ex.lim = 0;
+    if (WEX) {
+        ex.vid = ex_vid;
+        ex.w = ex_w;
+        ex.sorted_g = bp.sorted_g;
+        ex.voff = (int64_t)view * bp.n_vox;
+        ex.base = valid ? ex_off[pix] : 0;
+        ex.lim = valid ? (uint32_t)(ex_off[pix + 1] - ex.base) : 0u;
+    }
     Bwd<NRM> bw;
     if (BWD && valid) {
         bw.g0 = g_rgb ? g_rgb[pix * 3 + 0] : 0.0f;
@@ -675,8 +706,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     // Lockstep walk of actor o's sub-list: lanes not yet done composite the segments inside
     // their interval [a, b] of that actor into pt, with the stop rule (and, with G, the
     // per-record gradients reduced across the warp).
-    auto walk_actor = [&](Pix<NRM>& pt, int o, float a, float b, auto grad) {
+    auto walk_actor = [&](Pix<NRM>& pt, int o, float a, float b, auto grad, auto wex) {
         constexpr bool G = decltype(grad)::value;
+        constexpr bool X = decltype(wex)::value;
         const OctParams& P = vo[o];
         float d[3];
         rotate(P.A, dc, d);
@@ -701,9 +733,9 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                         t1 = fminf(t1, b);
                         if (t1 > t0) {
                             const float rel[3] = {g.x, g.y, g.z};
-                            add_segment<G, true, KS, NRM>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
-                                                          s_rec[slot][j][3], staged_nv(slot, j), rel, d, t0, t1,
-                                                          acc);
+                            add_segment<G, true, KS, NRM, X>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
+                                                             s_rec[slot][j][3], staged_nv(slot, j), rel, d, t0, t1,
+                                                             acc, s_r[slot][j], &ex);
                             hit = true;
                         }
                     }
@@ -732,7 +764,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         pt.done = !act;
         // a lane whose own transmittance already falls below eps_stop will stop inside this
         // actor whatever T it enters with (T <= 1), so its partial may stop there too
-        walk_actor(pt, s_act[q], a, b, std::false_type());
+        walk_actor(pt, s_act[q], a, b, std::false_type(), std::false_type());
         ps.tests += pt.tests;
         if (act) {
             s_st[q][0][tid] = pt.C0;
@@ -771,7 +803,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 pN2 = s_st[q][NRM ? 8 : 0][tid];
             }
             const bool stop_inside = ps.T * pT < bp.eps_stop;
-            if (BWD || stop_inside) {
+            if (REPLAY || stop_inside) {
                 s_st[q][0][tid] = ps.C0;
                 s_st[q][1][tid] = ps.C1;
                 s_st[q][2][tid] = ps.C2;
@@ -800,8 +832,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                 ps.n += pn;
             }
         } else {
-            walk_actor_lane<BWD, KS, NRM>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o], s_sub[it.o + 1], dc,
-                                          grad_rec);
+            walk_actor_lane<BWD, KS, NRM, WEX>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o],
+                                               s_sub[it.o + 1], dc, grad_rec, &ex);
         }
     };
 
@@ -827,7 +859,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                     float cur = fmaxf(t_in, tau_cur);
                     while (nxt.o >= 0 && nxt.a < t_out && !ps.done) {
                         if (nxt.a > cur) {
-                            add_segment<BWD, true, KS, NRM>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, nxt.a, acc);
+                            add_segment<BWD, true, KS, NRM, WEX>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, nxt.a,
+                                                                 acc, s_r[slot][j], &ex);
                             contributed = true;
                             if (ps.done) break;
                         }
@@ -838,7 +871,8 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
                         ps.boxes += n_ta;
                     }
                     if (!ps.done && t_out > cur) {
-                        add_segment<BWD, true, KS, NRM>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, t_out, acc);
+                        add_segment<BWD, true, KS, NRM, WEX>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, t_out, acc,
+                                                             s_r[slot][j], &ex);
                         contributed = true;
                     }
                 }
@@ -857,7 +891,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             }
             const uint32_t j0 = c0 + (uint32_t)(__ffs(m) - 1);
             m &= m - 1;
-            if (BWD || m == 0) {
+            if (REPLAY || m == 0) {
                 visit(j0);
                 continue;
             }
@@ -912,7 +946,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
     //   forward: only those where the ray stops; backward: every one reached (gradients)
     for (int q = 0; q < n_lock; ++q) {
         const int status = valid ? (int)s_st[q][5][tid] : 0;
-        const bool act = BWD ? status >= 1 : status == 2;
+        const bool act = REPLAY ? status >= 1 : status == 2;
         if (__syncthreads_or(act) == 0) continue;
         Pix<NRM> pt;
         pt.C0 = act ? s_st[q][0][tid] : 0.0f;
@@ -929,9 +963,10 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         pt.tests = 0;
         pt.boxes = 0;
         pt.done = !act;
-        walk_actor(pt, s_act[q], s_iv[q][0][tid], s_iv[q][1][tid], std::integral_constant<bool, BWD>());
+        walk_actor(pt, s_act[q], s_iv[q][0][tid], s_iv[q][1][tid], std::integral_constant<bool, BWD>(),
+                   std::integral_constant<bool, WEX>());
         ps.tests += pt.tests;
-        if (!BWD && act) {
+        if (!REPLAY && act) {
             ps.C0 = pt.C0;
             ps.C1 = pt.C1;
             ps.C2 = pt.C2;
@@ -946,7 +981,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
         }
     }
 
-    if (!BWD && work) {
+    if (!REPLAY && work) {
         unsigned long long t = ps.tests, b = ps.boxes, n = ps.n;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -960,7 +995,7 @@ __global__ void __launch_bounds__(CT_THREADS, BWD ? DV_BWD_MIN_BLOCKS : DV_FWD_M
             atomicAdd(work + 2, n);
         }
     }
-    if (!BWD && valid) {
+    if (!REPLAY && valid) {
         fp.rgb[lpix * 3 + 0] = ps.C0;
         fp.rgb[lpix * 3 + 1] = ps.C1;
         fp.rgb[lpix * 3 + 2] = ps.C2;
@@ -1130,13 +1165,13 @@ void composite_fwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* p
                      float* depth, float* alpha, uint32_t* n_seg, float* t_final, unsigned long long* work,
                      cudaStream_t s) {
     if (bp.K == 1)
-        k_composite<false, 1, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+        k_composite<false, 1, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
             bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha, n_seg, t_final,
-            nullptr, nullptr, nullptr, nullptr, nullptr, work);
+            nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
     else
-        k_composite<false, 0, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+        k_composite<false, 0, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
             bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha, n_seg, t_final,
-            nullptr, nullptr, nullptr, nullptr, nullptr, work);
+            nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
 }
 
 template <bool NRM>
@@ -1145,15 +1180,15 @@ void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* p
                      const float* depth, const float* t_final, const float* g_rgb, const float* g_depth,
                      const float* g_alpha, const float* g_normal, float* grad_rec, cudaStream_t s) {
     if (bp.K == 1)
-        k_composite<true, 1, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+        k_composite<true, 1, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
             bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
             const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
-            g_normal, grad_rec, nullptr);
+            g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
     else
-        k_composite<true, 0, NRM><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+        k_composite<true, 0, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
             bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
             const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
-            g_normal, grad_rec, nullptr);
+            g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
 }
 
 }  // namespace
@@ -1185,6 +1220,23 @@ cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const
     else
         composite_bwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, t_final,
                                g_rgb, g_depth, g_alpha, nullptr, grad_rec, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
+                                    const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
+                                    const uint32_t* tile_order, const int64_t* offsets, uint32_t* voxel, float* weight,
+                                    cudaStream_t s) {
+    if (bp.n_tiles <= 0) return cudaSuccess;
+    if (bp.K == 1)
+        k_composite<false, 1, false, true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
+    else
+        k_composite<false, 0, false, true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
     count_launches(1);
     return cudaGetLastError();
 }

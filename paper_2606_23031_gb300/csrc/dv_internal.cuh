@@ -62,6 +62,7 @@ struct BatchParams {
     const ViewParams* views;  // device [n_view]
     const OctParams* octs;    // device [n_view][n_oct]
     const float4* nrm;        // device [n_vis]: voxel normal (world frame) of each record, when normals
+    const uint32_t* sorted_g; // device [n_vis]: record -> view * n_vox + voxel
 };
 
 static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
@@ -153,9 +154,21 @@ cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const
                                  const uint32_t* tile_order, const float* rgb, const float* depth,
                                  const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
                                  const float* g_normal, float* grad_rec, cudaStream_t s);
+// replay of the forward that writes, for pixel p, the (voxel, weight T alpha) of each composited
+// segment into slots [offsets[p], offsets[p+1]) (voxel index within the view's concatenated octrees)
+cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
+                                    const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
+                                    const uint32_t* tile_order, const int64_t* offsets, uint32_t* voxel, float* weight,
+                                    cudaStream_t s);
 cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
                           const float* grad_rec, bool with_normals, float* const* d_dens, float* const* d_sh,
                           cudaStream_t s);
+
+// feature fields over a weights export (see dv_features.cu)
+cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
+                               const float* feat, int C, float* out, cudaStream_t s);
+cudaError_t launch_feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
+                             const float* f2d, int C, float* acc, float* wsum, cudaStream_t s);
 
 // one camera of a sky composite: camera -> world rotation (row-major) and intrinsics
 struct SkyView {
