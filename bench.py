@@ -489,6 +489,39 @@ def run_ours(args):
             ms_sky_b += b.elapsed_time(c)
         sync_all()
 
+    # ---- feature fields: weights export of the frame, 64-channel feature render and fusion ----
+    feats = None
+    if not args.no_normals:
+        rgb0, _, alpha0, st0 = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
+        nv = sum(o.n for o in sc.octrees)
+        fe = torch.randn((nv, 64), generator=torch.Generator(dev).manual_seed(args.seed + 11), device=dev)
+        f2 = torch.randn((n_pix, 64), generator=torch.Generator(dev).manual_seed(args.seed + 12), device=dev)
+        acc = torch.zeros((nv, 64), device=dev)
+        Wt = dv.dv_state_weights(st0)
+        reps = max(3, args.steps // 10)
+        t_ex = t_r = t_fu = 0.0
+        for it in range(reps + 2):
+            a, b, c, d_ = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            flush.zero_()
+            a.record(stream)
+            dv.dv_state_weights(st0, out=Wt)
+            b.record(stream)
+            dv.dv_features_render(Wt, fe, ctx=ctx)
+            c.record(stream)
+            dv.dv_features_fuse(Wt, f2, acc, ctx=ctx)
+            d_.record(stream)
+            d_.synchronize()
+            if it >= 2:
+                t_ex += a.elapsed_time(b)
+                t_r += b.elapsed_time(c)
+                t_fu += c.elapsed_time(d_)
+        st0.free()
+        slots = int(Wt.voxel.numel())
+        feats = {"what": "weights export of the frame, then a 64-channel feature render and 2-D feature fusion",
+                 "slots": slots, "export_us": 1e3 * t_ex / reps, "render64_us": 1e3 * t_r / reps,
+                 "fuse64_us": 1e3 * t_fu / reps,
+                 "render64_gbs": (slots * (8 + 64 * 4) + n_pix * 64 * 4) / (t_r / reps * 1e-3) / 1e9}
+
     ms_step, ms_fwd, ms_nrm = max_over_ranks([ms / args.steps, ms_f / args.steps, ms_n / args.steps], world, dev)
     value = whole_job_mpix_s(world, n_pix, ms_step)
     value_fwd = whole_job_mpix_s(world, n_pix, ms_fwd)
@@ -599,6 +632,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (512 MB write outside the step events)",
                            "visible_voxels": stats["n_visible"], "pairs": stats["n_pairs"]},
                 "fwd": {"value": value_fwd, "unit": "Mpix/s", "ms_per_step": ms_fwd},
+                "features": feats,
                 "sky": None if args.no_normals else {
                     "what": "sky composite of Eq. 2 on the frame, 1024x2048 equirectangular map",
                     "fwd_us": 1e3 * ms_sky_f / args.steps, "bwd_us": 1e3 * ms_sky_b / args.steps,

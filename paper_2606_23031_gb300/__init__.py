@@ -553,10 +553,16 @@ class Weights:
         return self.offsets.numel() - 1
 
 
-def dv_state_weights(state: State, stream=None) -> Weights:
-    """The weights export of a saved render (two calls through the C ABI: offsets, then slots)."""
+def dv_state_weights(state: State, stream=None, out: Weights | None = None) -> Weights:
+    """The weights export of a saved render (two calls through the C ABI: offsets, then slots);
+    ``out``, a previous export of the same state, is refilled in place (slots only)."""
     import torch
     lib = load()
+    if out is not None:
+        state.ctx.check(lib.dv_state_weights(state.ctx.handle, state.handle, C.c_void_p(out.offsets.data_ptr()),
+                                             C.c_void_p(out.voxel.data_ptr()), C.c_void_p(out.weight.data_ptr()),
+                                             _stream_ptr(stream)))
+        return out
     P = _state_pixels(state)
     dev = torch.device("cuda", state.ctx.device)
     offsets = torch.empty(P + 1, dtype=torch.int64, device=dev)
