@@ -1,0 +1,90 @@
+"""Pins of the initialisation oracle (oracle/init.py, Sec. 3.3):
+
+- Eq. 1: v_close at d = 0, v_far far away, v_far + (v_close - v_far)/e at d = s/sqrt(2);
+- shared corners: a full n^3 grid of leaves has (n+1)^3 corners; every corner index of a leaf
+  points at the grid point of that corner; two face neighbours share exactly four corners;
+  a coarse leaf next to fine ones shares only the grid points the fine ones touch;
+- nearest distance == scipy's k-d tree query;
+- subdivision: the children exactly tile the parent, untouched leaves are kept, and a leaf is
+  split iff some point lies within the threshold of its box (checked against a dense sampling
+  of the box).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.init as oi
+import synth
+
+
+def test_eq1_closed_forms():
+    s = 0.3
+    assert oi.soft_prior(0.0, s) == pytest.approx(-2.0, abs=1e-15)
+    assert oi.soft_prior(100.0, s) == pytest.approx(-10.0, abs=1e-15)
+    assert oi.soft_prior(s / math.sqrt(2.0), s) == pytest.approx(-10.0 + 8.0 / math.e, rel=1e-14)
+    d = np.linspace(0, 1, 11)
+    assert np.all(np.diff(oi.soft_prior(d, s)) < 0)
+
+
+def test_full_grid_has_n_plus_one_cubed_corners():
+    n, L = 4, 2
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    keys = synth.pack_keys(np.full(n ** 3, L), i.ravel(), j.ravel(), k.ravel())
+    pts, idx = oi.shared_corners(keys, L)
+    assert len(pts) == (n + 1) ** 3
+    grid = oi.corner_grid_points(keys, L)
+    np.testing.assert_array_equal(pts[idx], grid)
+    # face neighbours along x share the 4 corners of their common face
+    a = int(np.where((i.ravel() == 1) & (j.ravel() == 2) & (k.ravel() == 0))[0][0])
+    b = int(np.where((i.ravel() == 2) & (j.ravel() == 2) & (k.ravel() == 0))[0][0])
+    assert len(set(idx[a]) & set(idx[b])) == 4
+    assert set(idx[a][[1, 3, 5, 7]]) == set(idx[b][[0, 2, 4, 6]])
+
+
+def test_mixed_levels_share_grid_points_only():
+    # one level-1 leaf and the 8 level-2 leaves of its +x neighbour: the coarse leaf's +x face has
+    # 4 corners; the fine leaves touch 9 points of that face, 4 of which are the coarse corners
+    keys = [synth.pack_keys([1], [0], [0], [0])[0]]
+    for c in range(8):
+        keys.append(synth.pack_keys([2], [2 + (c & 1)], [(c >> 1) & 1], [(c >> 2) & 1])[0])
+    keys = np.array(keys, np.uint64)
+    pts, idx = oi.shared_corners(keys, 2)
+    coarse_face = set(idx[0][[1, 3, 5, 7]])
+    fine_pts = set(idx[1:].ravel())
+    assert coarse_face <= fine_pts
+    assert len(pts) == 8 + 27 - 4
+
+
+def test_nearest_distance_matches_kdtree():
+    sp = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(0)
+    cloud = rng.normal(size=(300, 3))
+    q = rng.normal(size=(50, 3)) * 1.5
+    np.testing.assert_allclose(oi.nearest_distance(q, cloud), sp.cKDTree(cloud).query(q)[0], rtol=1e-12)
+
+
+def test_subdivision_round():
+    rng = np.random.default_rng(1)
+    L = 2
+    i, j, k = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
+    keys = synth.pack_keys(np.full(64, L), i.ravel(), j.ravel(), k.ravel())
+    cloud = rng.uniform(-1.0, 1.0, size=(6, 3))
+    center, root, thr = (0.0, 0.0, 0.0), 2.0, 0.12
+    new, split = oi.subdivide_round(keys, center, root, cloud, thr)
+    assert 0 < split.sum() < 64
+    assert len(new) == 64 + 7 * split.sum()
+    # volumes: children tile their parents
+    lev, *_ = oi._unpack(new)
+    assert np.sum(8.0 ** -lev) == pytest.approx(1.0)
+    # dense sampling of each box: split iff some point is within the threshold of a sample
+    root_min = -1.0
+    for v in range(64):
+        s = root / 4
+        lo = root_min + np.array([i.ravel()[v], j.ravel()[v], k.ravel()[v]]) * s
+        g = np.stack(np.meshgrid(*[np.linspace(0, 1, 21)] * 3, indexing="ij"), -1).reshape(-1, 3) * s + lo
+        dmin = np.min(np.linalg.norm(g[:, None, :] - cloud[None], axis=2))
+        if dmin <= thr - 0.06:
+            assert split[v]
+        if dmin > thr + 1e-9:
+            assert not split[v]
