@@ -239,6 +239,55 @@ dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, c
                            void* stream);
 
 /*
+ * LiDAR-guided initialisation of the background octree (Sec. 3.3).  Keys use
+ * the leaf layout of dv_octree (level << 57 | k << 38 | j << 19 | i); every
+ * call that returns a size synchronises the stream.
+ *
+ * dv_shared_corners: the distinct grid corners of n leaves (corner c =
+ * (c & 1, c >> 1 & 1, c >> 2 & 1) of leaf (l, i, j, k) lies at finest-level grid
+ * point ((i + c_x) 2^(L-l), (j + c_y) 2^(L-l), (k + c_z) 2^(L-l)), L =
+ * max_level): grid[n_corners] (device, capacity 8n) receives the distinct
+ * points packed as z << 42 | y << 21 | x in increasing order, index[n][8]
+ * (device) every leaf corner's position in grid.  Leaves that touch the same
+ * grid point share it.  DV_ERR_INVALID_ARG for a leaf level above max_level or
+ * max_level > 18.
+ */
+dv_status dv_shared_corners(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, uint64_t* grid,
+                            uint32_t* index, int64_t* n_corners, void* stream);
+
+/*
+ * Eq. 1 soft density prior for every shared corner (grid from
+ * dv_shared_corners, octree frame given by center[3] (host) and root_size):
+ * dens = v_far + (v_close - v_far) exp(-2 d^2 / s_min^2), d the distance from
+ * the corner to the nearest point of cloud[n_points][3] (device, world frame;
+ * the paper's values are v_close = -2, v_far = -10).  Points farther than
+ * 3 s_min are not searched: they would change the prior by at most
+ * 8 exp(-18) ~ 1e-7, below float resolution at v_far.
+ */
+dv_status dv_soft_prior(dv_ctx* ctx, const uint64_t* grid, int64_t n_corners, const double* center, double root_size,
+                        int32_t max_level, const float* cloud, int64_t n_points, float s_min, float v_close,
+                        float v_far, float* dens, void* stream);
+
+/*
+ * One round of proximity subdivision (Sec. 3.3, step 2): every leaf whose box
+ * lies within `threshold` (Euclidean point-to-box distance) of a point of cloud
+ * is replaced by its eight children.  out (device, capacity 8n) receives the
+ * kept leaves in input order, then child 0 of every split leaf (in input
+ * order), then child 1, ..., child 7; *n_out (host) its length.  Children must
+ * stay within level 18 (max_level < 18).
+ */
+dv_status dv_subdivide_round(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, const double* center,
+                             double root_size, const float* cloud, int64_t n_points, float threshold, uint64_t* out,
+                             int64_t* n_out, void* stream);
+
+/* Per-leaf densities [n][8] from shared corner values (dens[v][c] = corner[index[v][c]]), and the
+ * transpose for gradients: ADDS d_dens[v][c] into d_corner[index[v][c]] (atomics). */
+dv_status dv_corner_gather(dv_ctx* ctx, const uint32_t* index, int64_t n, const float* corner, float* dens,
+                           void* stream);
+dv_status dv_corner_scatter(dv_ctx* ctx, const uint32_t* index, int64_t n, const float* d_dens, float* d_corner,
+                            void* stream);
+
+/*
  * Sky composite (Sec. 3.2 "Sky Modeling", Eq. 2): out = rgb + (1 - alpha) *
  * C_sky(d) per pixel, d the unit world direction of the pixel's ray, C_sky a
  * bilinear lookup of an equirectangular environment map of the world frame

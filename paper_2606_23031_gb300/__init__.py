@@ -23,7 +23,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libdv.so")
-SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu", "dv_features.cu"]
+SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu", "dv_features.cu", "dv_init.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV_ERR_TIMEOUT, DV_ERR_NOMEM = range(7)
@@ -157,6 +157,20 @@ def load(path: str | None = None):
     lib.dv_features_fuse.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dv_features_fuse.restype = C.c_int
+    lib.dv_shared_corners.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.POINTER(C.c_int64), C.c_void_p]
+    lib.dv_shared_corners.restype = C.c_int
+    lib.dv_soft_prior.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_double, C.c_int32,
+                                  C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_void_p, C.c_void_p]
+    lib.dv_soft_prior.restype = C.c_int
+    lib.dv_subdivide_round.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+                                       C.c_double, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
+                                       C.POINTER(C.c_int64), C.c_void_p]
+    lib.dv_subdivide_round.restype = C.c_int
+    lib.dv_corner_gather.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dv_corner_gather.restype = C.c_int
+    lib.dv_corner_scatter.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.dv_corner_scatter.restype = C.c_int
     lib.dv_sky_composite.argtypes = [C.c_void_p, C.POINTER(dv_camera), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dv_sky_composite.restype = C.c_int
@@ -607,6 +621,77 @@ def dv_features_fuse(w: Weights, feat2d, accum, wsum=None, *, ctx: Context | Non
                                    C.c_void_p(w.voxel.data_ptr()), C.c_void_p(w.weight.data_ptr()),
                                    C.c_void_p(feat2d.data_ptr()), Cc, C.c_void_p(accum.data_ptr()),
                                    C.c_void_p(wsum.data_ptr()) if wsum is not None else None, _stream_ptr(stream)))
+
+
+def _u64(t):
+    """uint64 keys held in an int64 tensor (same bits)."""
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+def dv_shared_corners(keys, max_level, *, ctx: Context | None = None, stream=None):
+    """(grid [N] int64 tensor of packed points z<<42|y<<21|x, index [n, 8] int32 tensor) for leaf keys
+    (int64 tensor of the uint64 key bits)."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = int(keys.numel())
+    grid = torch.empty(max(8 * n, 1), dtype=torch.int64, device=keys.device)
+    index = torch.empty((max(n, 1), 8), dtype=torch.int32, device=keys.device)
+    nc = C.c_int64()
+    ctx.check(lib.dv_shared_corners(ctx.handle, _u64(keys), n, int(max_level), C.c_void_p(grid.data_ptr()),
+                                    C.c_void_p(index.data_ptr()), C.byref(nc), _stream_ptr(stream)))
+    return grid[:nc.value], index[:n]
+
+
+def dv_soft_prior(grid, center, root_size, max_level, cloud, s_min, v_close=-2.0, v_far=-10.0, *,
+                  ctx: Context | None = None, stream=None):
+    """Eq. 1 densities [N] for the shared corners ``grid`` from the LiDAR points ``cloud`` [m, 3]."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    dens = torch.empty(max(int(grid.numel()), 1), dtype=torch.float32, device=grid.device)
+    c3 = (C.c_double * 3)(*[float(x) for x in center])
+    ctx.check(lib.dv_soft_prior(ctx.handle, _u64(grid), int(grid.numel()), c3, float(root_size), int(max_level),
+                                C.c_void_p(cloud.data_ptr()) if cloud.numel() else None, int(cloud.shape[0]),
+                                float(s_min), float(v_close), float(v_far), C.c_void_p(dens.data_ptr()),
+                                _stream_ptr(stream)))
+    return dens[:grid.numel()]
+
+
+def dv_subdivide_round(keys, max_level, center, root_size, cloud, threshold, *, ctx: Context | None = None,
+                       stream=None):
+    """New leaf keys (int64 tensor of uint64 bits) after one proximity-subdivision round."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = int(keys.numel())
+    out = torch.empty(max(8 * n, 1), dtype=torch.int64, device=keys.device)
+    n_out = C.c_int64()
+    c3 = (C.c_double * 3)(*[float(x) for x in center])
+    ctx.check(lib.dv_subdivide_round(ctx.handle, _u64(keys), n, int(max_level), c3, float(root_size),
+                                     C.c_void_p(cloud.data_ptr()) if cloud.numel() else None, int(cloud.shape[0]),
+                                     float(threshold), C.c_void_p(out.data_ptr()), C.byref(n_out),
+                                     _stream_ptr(stream)))
+    return out[:n_out.value]
+
+
+def dv_corner_gather(index, corner, *, ctx: Context | None = None, stream=None):
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = int(index.shape[0])
+    dens = torch.empty((n, 8), dtype=torch.float32, device=corner.device)
+    ctx.check(lib.dv_corner_gather(ctx.handle, C.c_void_p(index.data_ptr()), n, C.c_void_p(corner.data_ptr()),
+                                   C.c_void_p(dens.data_ptr()), _stream_ptr(stream)))
+    return dens
+
+
+def dv_corner_scatter(index, d_dens, d_corner, *, ctx: Context | None = None, stream=None):
+    lib = load()
+    ctx = ctx or default_context()
+    ctx.check(lib.dv_corner_scatter(ctx.handle, C.c_void_p(index.data_ptr()), int(index.shape[0]),
+                                    C.c_void_p(d_dens.data_ptr()), C.c_void_p(d_corner.data_ptr()),
+                                    _stream_ptr(stream)))
 
 
 def dv_sky_composite(cams, env, rgb, alpha, *, ctx: Context | None = None, out=None, stream=None):

@@ -886,6 +886,111 @@ dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, c
     return DV_OK;
 }
 
+// ---- LiDAR-guided initialisation (Sec. 3.3) ----
+
+static dv_status init_begin(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, dv::Arena& ar,
+                            cudaStream_t s) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && !keys)) return fail(ctx, DV_ERR_INVALID_ARG, "bad key array");
+    if (n > ((int64_t)1 << 28)) return fail(ctx, DV_ERR_CAPACITY, "more than 2^28 leaves");
+    if (max_level < 0 || max_level > 18) return fail(ctx, DV_ERR_INVALID_ARG, "max_level out of range (0..18)");
+    uint32_t lv = 0;
+    cudaError_t e = dv::key_levels(keys, n, &lv, ar, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "key levels");
+    if (lv >> (max_level + 1)) return fail(ctx, DV_ERR_INVALID_ARG, "a leaf level above max_level");
+    return DV_OK;
+}
+
+dv_status dv_shared_corners(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, uint64_t* grid,
+                            uint32_t* index, int64_t* n_corners, void* stream) {
+    if (!n_corners) return DV_ERR_INVALID_ARG;
+    *n_corners = 0;
+    if (ctx) ctx->err.clear();
+    if (n > 0 && (!grid || !index)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL output");
+    DeviceGuard g(ctx ? ctx->device : 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::Arena ar;
+    ar.pool = ctx ? ctx->pool : nullptr;
+    ar.stream = s;
+    dv_status st = init_begin(ctx, keys, n, max_level, ar, s);
+    cudaError_t e = cudaSuccess;
+    if (st == DV_OK) e = dv::shared_corners(keys, n, max_level, grid, index, n_corners, ar, s);
+    ar.release();
+    if (st != DV_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "shared corners");
+    return DV_OK;
+}
+
+dv_status dv_soft_prior(dv_ctx* ctx, const uint64_t* grid, int64_t n_corners, const double* center, double root_size,
+                        int32_t max_level, const float* cloud, int64_t n_points, float s_min, float v_close,
+                        float v_far, float* dens, void* stream) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n_corners < 0 || n_points < 0 || !center || !(root_size > 0.0) || !(s_min > 0.0f) || max_level < 0 ||
+        max_level > 18 || n_points > ((int64_t)1 << 31))
+        return fail(ctx, DV_ERR_INVALID_ARG, "bad arguments");
+    if ((n_corners > 0 && (!grid || !dens)) || (n_points > 0 && !cloud))
+        return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::Arena ar;
+    ar.pool = ctx->pool;
+    ar.stream = s;
+    cudaError_t e = dv::soft_prior(grid, n_corners, center, root_size, max_level, cloud, n_points, s_min, v_close, v_far,
+                                   dens, ar, s);
+    ar.release();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "soft prior");
+    return DV_OK;
+}
+
+dv_status dv_subdivide_round(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, const double* center,
+                             double root_size, const float* cloud, int64_t n_points, float threshold, uint64_t* out,
+                             int64_t* n_out, void* stream) {
+    if (!n_out) return DV_ERR_INVALID_ARG;
+    *n_out = 0;
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!center || !(root_size > 0.0) || !(threshold >= 0.0f) || n_points < 0 || (n_points > 0 && !cloud) ||
+        (n > 0 && !out) || max_level >= 18)
+        return fail(ctx, DV_ERR_INVALID_ARG, "bad arguments (children must stay within level 18)");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::Arena ar;
+    ar.pool = ctx->pool;
+    ar.stream = s;
+    dv_status st = init_begin(ctx, keys, n, max_level, ar, s);
+    cudaError_t e = cudaSuccess;
+    if (st == DV_OK)
+        e = dv::subdivide_round(keys, n, center, root_size, max_level, cloud, n_points, threshold, out, n_out, ar, s);
+    ar.release();
+    if (st != DV_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "subdivision");
+    return DV_OK;
+}
+
+dv_status dv_corner_gather(dv_ctx* ctx, const uint32_t* index, int64_t n, const float* corner, float* dens,
+                           void* stream) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && (!index || !corner || !dens))) return fail(ctx, DV_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = dv::corner_gather(index, n, corner, dens, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "corner gather");
+    return DV_OK;
+}
+
+dv_status dv_corner_scatter(dv_ctx* ctx, const uint32_t* index, int64_t n, const float* d_dens, float* d_corner,
+                            void* stream) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && (!index || !d_dens || !d_corner))) return fail(ctx, DV_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = dv::corner_scatter(index, n, d_dens, d_corner, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "corner scatter");
+    return DV_OK;
+}
+
 // ---- sky composite (Eq. 2) ----
 
 static dv_status sky_views(dv_ctx* ctx, const dv_camera* cams, int32_t n_cam, int32_t env_h, int32_t env_w,

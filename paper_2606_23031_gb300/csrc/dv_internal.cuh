@@ -170,6 +170,19 @@ cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t
 cudaError_t launch_feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
                              const float* f2d, int C, float* acc, float* wsum, cudaStream_t s);
 
+// LiDAR-guided initialisation (see dv_init.cu); the calls that return a size synchronise the stream
+cudaError_t key_levels(const uint64_t* keys, int64_t n, uint32_t* levels_host, Arena& ar, cudaStream_t s);
+cudaError_t shared_corners(const uint64_t* keys, int64_t n, int max_level, uint64_t* grid_out, uint32_t* index_out,
+                           int64_t* n_corners, Arena& ar, cudaStream_t s);
+cudaError_t soft_prior(const uint64_t* grid, int64_t n_corners, const double* center, double root_size, int max_level,
+                       const float* cloud, int64_t m, float s_min, float v_close, float v_far, float* dens, Arena& ar,
+                       cudaStream_t s);
+cudaError_t subdivide_round(const uint64_t* keys, int64_t n, const double* center, double root_size, int max_level,
+                            const float* cloud, int64_t m, float thr, uint64_t* out, int64_t* n_out, Arena& ar,
+                            cudaStream_t s);
+cudaError_t corner_gather(const uint32_t* index, int64_t n, const float* corner, float* dens, cudaStream_t s);
+cudaError_t corner_scatter(const uint32_t* index, int64_t n, const float* d_dens, float* d_corner, cudaStream_t s);
+
 // one camera of a sky composite: camera -> world rotation (row-major) and intrinsics
 struct SkyView {
     float R[9];
