@@ -41,8 +41,9 @@ struct dv_ctx {
     int device = 0;
     cudaMemPool_t pool = nullptr;
     std::string err;
-    uint64_t* h_scalars = nullptr;  // pinned: [0] n_vis, [1] n_pairs, [2] flags
-    uint64_t* d_scalars = nullptr;  // device mirror
+    uint64_t* h_scalars = nullptr;  // pinned, mapped: [0] n_vis, [1] n_pairs, [2] flags
+    uint64_t* h_scalars_dev = nullptr;  // the same host words as the device sees them
+    uint64_t* d_scalars = nullptr;  // device counters
     cudaEvent_t ev_sizes = nullptr;  // the scalars have reached the host
     bool profiling = false;
     std::vector<ProfRec> pending;
@@ -476,8 +477,9 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     }
     // the sizes of everything below come back to the host while the GPU runs the
     // visibility scan, which needs none of them
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_scalars, ctx->d_scalars, 3 * sizeof(uint64_t),
-                                              cudaMemcpyDeviceToHost, s);
+    // a kernel stores the counters into mapped host memory: no copy engine is involved, so a large
+    // device-to-host transfer queued by the caller on another stream cannot delay this read-back
+    if (e == cudaSuccess) e = launch_publish(ctx->d_scalars, ctx->h_scalars_dev, 3, s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_sizes, s);
     {
         Prof p(ctx, KP_SCAN, s);
@@ -641,7 +643,9 @@ dv_status dv_create(dv_ctx** out, int32_t device) {
     if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) return DV_ERR_CUDA;
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    if (cudaMallocHost(&ctx->h_scalars, 4 * sizeof(uint64_t)) != cudaSuccess) {
+    if (cudaHostAlloc(&ctx->h_scalars, 4 * sizeof(uint64_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&ctx->h_scalars_dev, ctx->h_scalars, 0) != cudaSuccess) {
+        if (ctx->h_scalars) cudaFreeHost(ctx->h_scalars);
         cudaMemPoolDestroy(ctx->pool);
         return DV_ERR_NOMEM;
     }

@@ -126,6 +126,8 @@ cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt,
 // kernel launchers (one thread per (view, voxel) unless stated)
 cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
                            uint32_t* flags, unsigned long long* totals, cudaStream_t s);
+// n (<= 32) counters from device memory into mapped host memory, by a kernel (no copy engine)
+cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, cudaStream_t s);
 cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
                            uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
 cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,

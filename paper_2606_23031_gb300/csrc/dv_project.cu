@@ -467,6 +467,20 @@ cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* sc
     return cudaGetLastError();
 }
 
+// copies n counters into mapped host memory (system-scope stores, visible to the host once the
+// stream has passed this kernel)
+__global__ void k_publish(const uint64_t* __restrict__ src, volatile uint64_t* dst, int n) {
+    const int t = threadIdx.x;
+    if (t < n) dst[t] = src[t];
+    __threadfence_system();
+}
+
+cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, cudaStream_t s) {
+    k_publish<<<1, 32, 0, s>>>(src, host_mapped_dst, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
                            uint32_t* flags, unsigned long long* totals, cudaStream_t s) {
     const int64_t n = bp.n_vox * bp.n_view;
