@@ -280,6 +280,19 @@ dv_status dv_subdivide_round(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32
                              double root_size, const float* cloud, int64_t n_points, float threshold, uint64_t* out,
                              int64_t* n_out, void* stream);
 
+/*
+ * Visibility and height pruning of an initial grid (Sec. 3.3, step 1): keeps
+ * the leaves whose box top reaches z_min (world z) and that some camera of
+ * cams[n_cam] (host) sees: its 8 corners are not all in front of the near or
+ * all beyond the far plane, and either the box straddles the near plane or
+ * the bounding rectangle of its projected corners overlaps the image.  out
+ * (device, capacity n) receives the kept keys in input order, *n_out (host)
+ * their count.  Synchronises the stream.
+ */
+dv_status dv_visibility_prune(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, const double* center,
+                              double root_size, const dv_camera* cams, int32_t n_cam, double z_min, uint64_t* out,
+                              int64_t* n_out, void* stream);
+
 /* Per-leaf densities [n][8] from shared corner values (dens[v][c] = corner[index[v][c]]), and the
  * transpose for gradients: ADDS d_dens[v][c] into d_corner[index[v][c]] (atomics). */
 dv_status dv_corner_gather(dv_ctx* ctx, const uint32_t* index, int64_t n, const float* corner, float* dens,

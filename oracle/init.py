@@ -109,3 +109,40 @@ def subdivide_round(keys, center, root_size, cloud, threshold):
         out.append(_pack(lev[split] + 1, 2 * i[split] + (c & 1), 2 * j[split] + ((c >> 1) & 1),
                          2 * k[split] + ((c >> 2) & 1)))
     return np.concatenate(out).astype(np.uint64), split
+
+
+def visible_from(keys, center, root_size, cams, z_min):
+    """Step 1 (visibility and height pruning), as read here: a leaf is kept if its box's top is at
+    or above ``z_min`` (world z) and some camera sees it, i.e. its 8 corners (camera frame,
+    OpenCV axes) are not all behind the near plane or all beyond the far plane, and either some
+    corners lie on each side of the near plane (the box straddles it: kept) or the bounding
+    rectangle of the projected corners overlaps the image [0, W] x [0, H]."""
+    lev, i, j, k = _unpack(keys)
+    root_min = np.asarray(center, np.float64) - 0.5 * root_size
+    keep = np.zeros(len(lev), bool)
+    offs = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], np.float64)
+    for v in range(len(lev)):
+        s = root_size / 2.0 ** lev[v]
+        lo = root_min + np.array([i[v], j[v], k[v]], np.float64) * s
+        if lo[2] + s < z_min:
+            continue
+        corners = lo + offs * s
+        for cam in cams:
+            R = np.asarray(cam.pose.R, np.float64).reshape(3, 3)
+            t = np.asarray(cam.pose.t, np.float64)
+            pc = (corners - t) @ R          # camera-frame coordinates (R^T (p - t))
+            z = pc[:, 2]
+            near, far = float(np.float32(cam.near)), float(np.float32(cam.far))
+            if np.all(z < near) or np.all(z > far):
+                continue
+            if np.any(z < near):
+                keep[v] = True
+                break
+            fx, fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
+            cx, cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
+            u = fx * pc[:, 0] / z + cx
+            w = fy * pc[:, 1] / z + cy
+            if u.max() >= 0.0 and u.min() <= cam.W and w.max() >= 0.0 and w.min() <= cam.H:
+                keep[v] = True
+                break
+    return keep

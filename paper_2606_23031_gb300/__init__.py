@@ -167,6 +167,10 @@ def load(path: str | None = None):
                                        C.c_double, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
                                        C.POINTER(C.c_int64), C.c_void_p]
     lib.dv_subdivide_round.restype = C.c_int
+    lib.dv_visibility_prune.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+                                        C.c_double, C.POINTER(dv_camera), C.c_int32, C.c_double, C.c_void_p,
+                                        C.POINTER(C.c_int64), C.c_void_p]
+    lib.dv_visibility_prune.restype = C.c_int
     lib.dv_corner_gather.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dv_corner_gather.restype = C.c_int
     lib.dv_corner_scatter.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -672,6 +676,23 @@ def dv_subdivide_round(keys, max_level, center, root_size, cloud, threshold, *, 
                                      C.c_void_p(cloud.data_ptr()) if cloud.numel() else None, int(cloud.shape[0]),
                                      float(threshold), C.c_void_p(out.data_ptr()), C.byref(n_out),
                                      _stream_ptr(stream)))
+    return out[:n_out.value]
+
+
+def dv_visibility_prune(keys, max_level, center, root_size, cams, z_min, *, ctx: Context | None = None,
+                        stream=None):
+    """Kept leaf keys (int64 tensor of uint64 bits) after visibility and height pruning."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = int(keys.numel())
+    out = torch.empty(max(n, 1), dtype=torch.int64, device=keys.device)
+    n_out = C.c_int64()
+    c3 = (C.c_double * 3)(*[float(x) for x in center])
+    cam_arr = (dv_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+    ctx.check(lib.dv_visibility_prune(ctx.handle, _u64(keys), n, int(max_level), c3, float(root_size), cam_arr,
+                                      len(cams), float(z_min), C.c_void_p(out.data_ptr()), C.byref(n_out),
+                                      _stream_ptr(stream)))
     return out[:n_out.value]
 
 

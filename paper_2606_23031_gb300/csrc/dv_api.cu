@@ -973,6 +973,48 @@ dv_status dv_subdivide_round(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32
     return DV_OK;
 }
 
+dv_status dv_visibility_prune(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_t max_level, const double* center,
+                              double root_size, const dv_camera* cams, int32_t n_cam, double z_min, uint64_t* out,
+                              int64_t* n_out, void* stream) {
+    if (!n_out) return DV_ERR_INVALID_ARG;
+    *n_out = 0;
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!center || !(root_size > 0.0) || n_cam < 0 || n_cam > DV_MAX_VIEWS || (n_cam > 0 && !cams) ||
+        (n > 0 && !out))
+        return fail(ctx, DV_ERR_INVALID_ARG, "bad arguments");
+    std::vector<dv::InitCam> ic((size_t)std::max(n_cam, 1));
+    for (int c = 0; c < n_cam; ++c) {
+        const dv_camera& cm = cams[c];
+        if (cm.W < 0 || cm.H < 0 || !(cm.fx > 0.0f) || !(cm.fy > 0.0f) || !(cm.near_ > 0.0f) || !(cm.far_ > cm.near_))
+            return fail(ctx, DV_ERR_INVALID_ARG, "bad camera");
+        for (int k = 0; k < 9; ++k) ic[c].R[k] = cm.cam_to_world.R[k];
+        for (int k = 0; k < 3; ++k) ic[c].t[k] = cm.cam_to_world.t[k];
+        ic[c].fx = cm.fx;
+        ic[c].fy = cm.fy;
+        ic[c].cx = cm.cx;
+        ic[c].cy = cm.cy;
+        ic[c].near_ = cm.near_;
+        ic[c].far_ = cm.far_;
+        ic[c].W = cm.W;
+        ic[c].H = cm.H;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::Arena ar;
+    ar.pool = ctx->pool;
+    ar.stream = s;
+    dv_status st = init_begin(ctx, keys, n, max_level, ar, s);
+    cudaError_t e = cudaSuccess;
+    if (st == DV_OK)
+        e = dv::visibility_prune(keys, n, center, root_size, ic.data(), n_cam, z_min, out, n_out, ar, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the camera array is read from host memory
+    ar.release();
+    if (st != DV_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "visibility pruning");
+    return DV_OK;
+}
+
 dv_status dv_corner_gather(dv_ctx* ctx, const uint32_t* index, int64_t n, const float* corner, float* dens,
                            void* stream) {
     if (!ctx) return DV_ERR_INVALID_ARG;

@@ -231,7 +231,86 @@ __global__ void k_levels(const uint64_t* __restrict__ keys, int64_t n, uint32_t*
     atomicOr(levels, 1u << ((keys[t] >> 57) & 31));
 }
 
+// a leaf is kept if its box top reaches z_min and some camera sees it (see the header)
+__global__ void k_visible(const uint64_t* __restrict__ keys, int64_t n, Frame f, double root_size,
+                          const InitCam* __restrict__ cams, int n_cam, double z_min, uint32_t* __restrict__ keep) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const uint64_t k = keys[v];
+    const int lev = (int)((k >> 57) & 31);
+    const double s = ldexp(root_size, -lev);
+    const double lo[3] = {f.root_min[0] + (double)(k & kIMask) * s, f.root_min[1] + (double)((k >> 19) & kIMask) * s,
+                          f.root_min[2] + (double)((k >> 38) & kIMask) * s};
+    uint32_t vis = 0;
+    if (lo[2] + s >= z_min) {
+        for (int c = 0; c < n_cam && !vis; ++c) {
+            const InitCam& C = cams[c];
+            int behind = 0, beyond = 0;
+            double u0 = INFINITY, u1 = -INFINITY, w0 = INFINITY, w1 = -INFINITY;
+            for (int q = 0; q < 8; ++q) {
+                const double p[3] = {lo[0] + ((q & 1) ? s : 0.0) - C.t[0], lo[1] + ((q & 2) ? s : 0.0) - C.t[1],
+                                     lo[2] + ((q & 4) ? s : 0.0) - C.t[2]};
+                // camera frame: R^T (p - t), R row-major camera -> world
+                const double x = C.R[0] * p[0] + C.R[3] * p[1] + C.R[6] * p[2];
+                const double y = C.R[1] * p[0] + C.R[4] * p[1] + C.R[7] * p[2];
+                const double z = C.R[2] * p[0] + C.R[5] * p[1] + C.R[8] * p[2];
+                behind += z < C.near_;
+                beyond += z > C.far_;
+                if (z >= C.near_) {
+                    const double u = C.fx * x / z + C.cx, w = C.fy * y / z + C.cy;
+                    u0 = fmin(u0, u);
+                    u1 = fmax(u1, u);
+                    w0 = fmin(w0, w);
+                    w1 = fmax(w1, w);
+                }
+            }
+            if (behind == 8 || beyond == 8) continue;
+            if (behind > 0)
+                vis = 1;
+            else
+                vis = (u1 >= 0.0 && u0 <= (double)C.W && w1 >= 0.0 && w0 <= (double)C.H) ? 1u : 0u;
+        }
+    }
+    keep[v] = vis;
+}
+
+__global__ void k_compact_keys(const uint64_t* __restrict__ keys, int64_t n, const uint32_t* __restrict__ keep,
+                               const uint32_t* __restrict__ pos, uint64_t* __restrict__ out) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n || !keep[v]) return;
+    out[pos[v]] = keys[v];
+}
+
 }  // namespace
+
+static Frame make_frame(const double* center, double root_size, int max_level);
+
+cudaError_t visibility_prune(const uint64_t* keys, int64_t n, const double* center, double root_size,
+                             const InitCam* cams_host, int n_cam, double z_min, uint64_t* out, int64_t* n_out,
+                             Arena& ar, cudaStream_t s) {
+    *n_out = 0;
+    if (n <= 0) return cudaSuccess;
+    const Frame f = make_frame(center, root_size, 0);
+    InitCam* cams = ar.alloc<InitCam>((size_t)(n_cam > 0 ? n_cam : 1));
+    uint32_t* keep = ar.alloc<uint32_t>(n);
+    uint32_t* pos = ar.alloc<uint32_t>(n);
+    uint32_t* tot = ar.alloc<uint32_t>(1);
+    if (ar.err != cudaSuccess) return ar.err;
+    cudaError_t e = cudaSuccess;
+    if (n_cam > 0) e = cudaMemcpyAsync(cams, cams_host, sizeof(InitCam) * n_cam, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_visible<<<nb(n), 256, 0, s>>>(keys, n, f, root_size, cams, n_cam, z_min, keep);
+    count_launches(1);
+    e = scan_u32_to_u32(keep, pos, n, tot, ar, s);
+    if (e != cudaSuccess) return e;
+    k_compact_keys<<<nb(n), 256, 0, s>>>(keys, n, keep, pos, out);
+    count_launches(1);
+    uint32_t h = 0;
+    e = cudaMemcpyAsync(&h, tot, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *n_out = h;
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
 
 cudaError_t corner_gather(const uint32_t* index, int64_t n, const float* corner, float* dens, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

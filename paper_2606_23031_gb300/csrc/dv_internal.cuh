@@ -182,6 +182,15 @@ cudaError_t soft_prior(const uint64_t* grid, int64_t n_corners, const double* ce
 cudaError_t subdivide_round(const uint64_t* keys, int64_t n, const double* center, double root_size, int max_level,
                             const float* cloud, int64_t m, float thr, uint64_t* out, int64_t* n_out, Arena& ar,
                             cudaStream_t s);
+// a camera of the visibility pruning (double precision, camera -> world rotation row-major)
+struct InitCam {
+    double R[9], t[3];
+    double fx, fy, cx, cy, near_, far_;
+    int32_t W, H;
+};
+cudaError_t visibility_prune(const uint64_t* keys, int64_t n, const double* center, double root_size,
+                             const InitCam* cams_host, int n_cam, double z_min, uint64_t* out, int64_t* n_out,
+                             Arena& ar, cudaStream_t s);
 cudaError_t corner_gather(const uint32_t* index, int64_t n, const float* corner, float* dens, cudaStream_t s);
 cudaError_t corner_scatter(const uint32_t* index, int64_t n, const float* d_dens, float* d_corner, cudaStream_t s);
 

@@ -88,3 +88,29 @@ def test_subdivision_round():
             assert split[v]
         if dmin > thr + 1e-9:
             assert not split[v]
+
+
+def test_visibility_pruning_reading():
+    # a camera at (0.5, 0.5, 0.5) looking along +x, far plane 2: leaves behind it, outside its field of
+    # view, beyond its far plane or below the height threshold are pruned; leaves in view or around
+    # the camera are kept
+    from types import SimpleNamespace
+    eye = np.array([0.5, 0.5, 0.5])
+    cam_pose = synth.look_at(eye, eye + np.array([1.0, 0.0, 0.0]))
+    cam = SimpleNamespace(W=64, H=48, fx=40.0, fy=40.0, cx=32.0, cy=24.0, near=0.1, far=2.0,
+                          pose=SimpleNamespace(R=np.asarray(cam_pose.R, np.float64), t=eye))
+    L = 3   # root 8 m centred at 0: 1 m leaves
+    n = 8
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    keys = synth.pack_keys(np.full(n ** 3, L), i.ravel(), j.ravel(), k.ravel())
+    keep = oi.visible_from(keys, (0.0, 0.0, 0.0), 8.0, [cam], z_min=-2.5)
+    lo = np.stack([i.ravel(), j.ravel(), k.ravel()], 1) - 4.0       # leaf min corners (1 m leaves)
+    at = lambda x, y, z: int(np.where((lo[:, 0] == x) & (lo[:, 1] == y) & (lo[:, 2] == z))[0][0])
+    assert keep[at(2, 0, 0)]            # ahead on the axis, partly within the far plane
+    assert keep[at(0, 0, 0)]            # contains the camera (straddles the near plane)
+    assert not keep[at(-4, 0, 0)]       # behind
+    assert not keep[at(3, 0, 0)]        # entirely beyond the far plane
+    assert not keep[at(2, 0, -4)]       # top at z = -3, below the height threshold
+    # the horizontal field of view is 2 atan(32/40) ~ 77 deg: a leaf far to the side of the axis is pruned
+    assert not keep[at(2, 3, 0)]
+    assert 0 < keep.sum() < len(keys)

@@ -100,3 +100,17 @@ def test_level_above_max_level_is_rejected(dv):
     keys = synth.pack_keys([3], [1], [2], [3])
     with pytest.raises(RuntimeError):
         m.dv_shared_corners(_keys_t(keys), 2)
+
+
+def test_visibility_pruning(dv):
+    import paper_2606_23031_gb300 as m
+    rng = np.random.default_rng(73)
+    L = 4   # 16^3 leaves of a 16 m root centred at (0, 0, 4)
+    keys = _grid_keys(L)
+    center, root = (0.0, 0.0, 4.0), 16.0
+    cams = [synth.vehicle_camera(64, 48, 70.0, yaw, position=(0.3, -0.2, 1.8), pitch_deg=5.0, near=0.2, far=9.0)
+            for yaw in (0.0, 130.0)]
+    gpu = m.dv_visibility_prune(_keys_t(keys), L, center, root, cams, z_min=-1.0).cpu().numpy().view(np.uint64)
+    keep = oi.visible_from(keys, center, root, cams, -1.0)
+    assert 0 < keep.sum() < len(keys)
+    np.testing.assert_array_equal(gpu, keys[keep])
