@@ -571,16 +571,16 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     B.pmask = pool_alloc<uint8_t>(ctx, s, (size_t)P, own, e);
     {
         Prof p(ctx, KP_RANGES, s);
-        if (e == cudaSuccess) e = launch_pair_mask(bp, pk, B.pval, rect_sorted, P, B.pmask, s);
-        if (e == cudaSuccess) e = launch_ranges(pk, P, B.range, (int)tiles, s);
+        if (e == cudaSuccess)
+            e = launch_pair_mask_ranges(bp, pk, B.pval, rect_sorted, P, B.pmask, B.range, (int)tiles, s);
         uint32_t* tscr = ar.alloc<uint32_t>(64);
         if (e == cudaSuccess) e = tscr ? launch_tile_order(B.range, (int)tiles, tscr, B.tile_order, s) : ar.err;
     }
     {
         Prof p(ctx, KP_FWD, s);
         if (e == cudaSuccess)
-            e = launch_composite_fwd(bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, nullptr,
-                                     nullptr, nullptr, B.n_seg, B.t_final, B.work, s);
+            e = launch_composite_fwd(bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, B.n_seg,
+                                     B.t_final, B.work, s);
     }
     ar.release();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render");
@@ -599,8 +599,8 @@ dv_status backward_batch(dv_ctx* ctx, dv_state* st, const float* d_rgb, const fl
     {
         Prof p(ctx, KP_BWD, s);
         if (e == cudaSuccess)
-            e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, nullptr,
-                                         nullptr, B.t_final, d_rgb, d_depth, d_alpha, d_normal, grad, s);
+            e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, B.t_final,
+                                         d_rgb, d_depth, d_alpha, d_normal, grad, s);
     }
     {
         Prof p(ctx, KP_SHBWD, s);

@@ -444,8 +444,7 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
                                                         const uint2* __restrict__ tile_range,
                                                         const uint32_t* __restrict__ vis_start,
                                                         const uint32_t* __restrict__ tile_order,
-                                                        float* __restrict__ out_rgb, float* __restrict__ out_depth,
-                                                        float* __restrict__ out_alpha, uint32_t* __restrict__ n_seg,
+                                                        uint32_t* __restrict__ n_seg,
                                                         float* __restrict__ t_final, const float* __restrict__ g_rgb,
                                                         const float* __restrict__ g_depth,
                                                         const float* __restrict__ g_alpha,
@@ -1161,33 +1160,33 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
 
 template <bool NRM>
 void composite_fwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val, const uint8_t* pair_mask,
-                     const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, float* rgb,
-                     float* depth, float* alpha, uint32_t* n_seg, float* t_final, unsigned long long* work,
-                     cudaStream_t s) {
+                     const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, uint32_t* n_seg,
+                     float* t_final, unsigned long long* work, cudaStream_t s) {
     if (bp.K == 1)
         k_composite<false, 1, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha, n_seg, t_final,
-            nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr,
+            nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
     else
         k_composite<false, 0, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha, n_seg, t_final,
-            nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr,
+            nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
 }
 
 template <bool NRM>
 void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val, const uint8_t* pair_mask,
-                     const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, const float* rgb,
-                     const float* depth, const float* t_final, const float* g_rgb, const float* g_depth,
-                     const float* g_alpha, const float* g_normal, float* grad_rec, cudaStream_t s) {
+                     const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
+                     const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
+                     const float* g_normal, float* grad_rec, cudaStream_t s) {
+    // the kernel's per-pixel forward results (final T here, C, D, N through the view parameters)
+    // are only read in the backward
+    float* tf = const_cast<float*>(t_final);
     if (bp.K == 1)
         k_composite<true, 1, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
-            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha,
             g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
     else
         k_composite<true, 0, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, const_cast<float*>(rgb),
-            const_cast<float*>(depth), nullptr, nullptr, const_cast<float*>(t_final), g_rgb, g_depth, g_alpha,
+            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha,
             g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
 }
 
@@ -1195,31 +1194,31 @@ void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* p
 
 cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
-                                 const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
-                                 float* t_final, unsigned long long* work, cudaStream_t s) {
+                                 const uint32_t* tile_order, uint32_t* n_seg, float* t_final,
+                                 unsigned long long* work, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
     if (bp.normals)
-        composite_fwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha,
-                              n_seg, t_final, work, s);
+        composite_fwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, work,
+                              s);
     else
-        composite_fwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, alpha,
-                               n_seg, t_final, work, s);
+        composite_fwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, work,
+                               s);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
-                                 const uint32_t* tile_order, const float* rgb, const float* depth,
-                                 const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
-                                 const float* g_normal, float* grad_rec, cudaStream_t s) {
+                                 const uint32_t* tile_order, const float* t_final, const float* g_rgb,
+                                 const float* g_depth, const float* g_alpha, const float* g_normal, float* grad_rec,
+                                 cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
     if (g_normal)
-        composite_bwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, t_final,
-                              g_rgb, g_depth, g_alpha, g_normal, grad_rec, s);
+        composite_bwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, t_final, g_rgb,
+                              g_depth, g_alpha, g_normal, grad_rec, s);
     else
-        composite_bwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, rgb, depth, t_final,
-                               g_rgb, g_depth, g_alpha, nullptr, grad_rec, s);
+        composite_bwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, t_final, g_rgb,
+                               g_depth, g_alpha, nullptr, grad_rec, s);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1232,11 +1231,11 @@ cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, co
     if (bp.K == 1)
         k_composite<false, 1, false, true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
             bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr,
-            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
+            nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
     else
         k_composite<false, 0, false, true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
             bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr,
-            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
+            nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
     count_launches(1);
     return cudaGetLastError();
 }

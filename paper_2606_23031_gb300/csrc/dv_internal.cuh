@@ -139,23 +139,25 @@ cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, 
 cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64_t* rect_sorted,
                         const uint32_t* sorted_g, int64_t n_vis, int64_t n_pairs, uint32_t* pair_key,
                         uint32_t* pair_val, cudaStream_t s);
-cudaError_t launch_pair_mask(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
-                             const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, cudaStream_t s);
-cudaError_t launch_ranges(const uint32_t* pair_key, int64_t n_pairs, uint2* tile_range, int n_tiles, cudaStream_t s);
+// per tile-sorted pair: its 8x4-block mask; per tile: its [first, end) range of the pair list
+cudaError_t launch_pair_mask_ranges(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
+                                    const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, uint2* tile_range,
+                                    int n_tiles, cudaStream_t s);
 // tiles ordered by decreasing pair-list length (log2 buckets); scratch: 64 words
 cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* scratch64, uint32_t* order,
                               cudaStream_t s);
+// outputs go to the views' buffers (ViewParams); n_seg and t_final per pixel are kept for the backward
 cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
-                                 const uint32_t* tile_order, float* rgb, float* depth, float* alpha, uint32_t* n_seg,
-                                 float* t_final, unsigned long long* work, cudaStream_t s);
+                                 const uint32_t* tile_order, uint32_t* n_seg, float* t_final,
+                                 unsigned long long* work, cudaStream_t s);
 // with g_normal (the call rendered normals): gradient rows of 16 floats (8 densities, 3 colour, 3 normal, 2 pad),
 // else of 12 (8 densities, 3 colour, 1 pad)
 cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
-                                 const uint32_t* tile_order, const float* rgb, const float* depth,
-                                 const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
-                                 const float* g_normal, float* grad_rec, cudaStream_t s);
+                                 const uint32_t* tile_order, const float* t_final, const float* g_rgb,
+                                 const float* g_depth, const float* g_alpha, const float* g_normal, float* grad_rec,
+                                 cudaStream_t s);
 // replay of the forward that writes, for pixel p, the (voxel, weight T alpha) of each composited
 // segment into slots [offsets[p], offsets[p+1]) (voxel index within the view's concatenated octrees)
 cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,

@@ -379,12 +379,17 @@ __device__ __forceinline__ int view_of_tile(const BatchParams& bp, int t) {
     return lo;
 }
 
+// one thread per tile-sorted pair: the 8x4-pixel blocks of its tile the voxel's pixel rectangle
+// touches (bit sy * 2 + sx), and the tile's list range from the key boundaries
 __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32_t* __restrict__ pkey,
                             const uint32_t* __restrict__ pval, const uint64_t* __restrict__ rect_sorted,
-                            int64_t n_pairs, uint8_t* __restrict__ mask) {
+                            int64_t n_pairs, uint8_t* __restrict__ mask, uint2* __restrict__ range) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
-    const int view = view_of_tile(bp, (int)pkey[p]);
+    const uint32_t key = pkey[p];
+    if (p == 0 || pkey[p - 1] != key) range[key].x = (uint32_t)p;
+    if (p == n_pairs - 1 || pkey[p + 1] != key) range[key].y = (uint32_t)(p + 1);
+    const int view = view_of_tile(bp, (int)key);
     const uint32_t t = pkey[p] - (uint32_t)bp.tile_base[view];
     const uint32_t tiles_x = (uint32_t)bp.views[view].tiles_x;
     const uint64_t rc = __ldg(rect_sorted + pval[p]);
@@ -398,14 +403,6 @@ __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32
         for (int sx = 0; sx < 2; ++sx)
             if (u0 <= 8 * sx + 7 && u1 >= 8 * sx && v0 <= 4 * sy + 3 && v1 >= 4 * sy) m |= 1u << (sy * 2 + sx);
     mask[p] = (uint8_t)m;
-}
-
-__global__ void k_ranges(const uint32_t* __restrict__ key, int64_t n, uint2* __restrict__ range) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = key[i];
-    if (i == 0 || key[i - 1] != t) range[t].x = (uint32_t)i;
-    if (i == n - 1 || key[i + 1] != t) range[t].y = (uint32_t)(i + 1);
 }
 
 // Heaviest tiles first: counting sort of tiles by floor(log2(list length + 1)),
@@ -524,18 +521,12 @@ cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_mask(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
-                             const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, cudaStream_t s) {
-    if (n_pairs <= 0) return cudaSuccess;
-    k_pair_mask<<<nblk(n_pairs, 256), 256, 0, s>>>(bp, pair_key, pair_val, rect_sorted, n_pairs, mask);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ranges(const uint32_t* pair_key, int64_t n_pairs, uint2* tile_range, int n_tiles, cudaStream_t s) {
+cudaError_t launch_pair_mask_ranges(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
+                                    const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, uint2* tile_range,
+                                    int n_tiles, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(tile_range, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
-    k_ranges<<<nblk(n_pairs, 256), 256, 0, s>>>(pair_key, n_pairs, tile_range);
+    k_pair_mask<<<nblk(n_pairs, 256), 256, 0, s>>>(bp, pair_key, pair_val, rect_sorted, n_pairs, mask, tile_range);
     count_launches(1);
     return cudaGetLastError();
 }
