@@ -157,7 +157,7 @@ dv_status dv_render_views(dv_ctx* ctx, const dv_octree* oct, int32_t n_oct, cons
                           void* stream);
 
 /*
- * Backward of dv_render (gradients flow through every voxel segment, Sec. 3.4).
+ * Backward of dv_render (the gradient passes through every voxel segment, Sec. 3.4).
  * Given dL/dRGB [sum H*W][3], dL/ddepth and dL/dalpha [sum H*W] (device; any of
  * the three may be NULL = zero), ADDS dL/d dens into d_dens[i] ([n_vox][8]) and
  * dL/d SH into d_sh[i] ([n_vox][nsh][3]) for every octree i (host arrays of
@@ -170,7 +170,7 @@ dv_status dv_render_backward(dv_ctx* ctx, dv_state* state, const float* d_rgb, c
 
 /*
  * dv_render plus the normal state N of Algorithm 1 (Sec. 3.4: the pixel state
- * aggregates voxel normals): N = sum over the composited segments of
+ * also sums voxel normals): N = sum over the composited segments of
  * T_k alpha_k n_k, with n the voxel's normal in world coordinates -- minus the
  * normalised gradient of the voxel's trilinear raw density at its centre
  * (per axis: the four corners on the high side minus the four on the low

@@ -35,7 +35,7 @@
  *   the camera centre to the voxel centre in the octree's local frame;
  *   overlapping actor boxes: the box entered first owns the overlap;
  *   the garbled "D = 1" of Alg. 1's initial state is read as T = 1;
- *   the normal state N of Alg. 1 (Sec. 3.4: N aggregates voxel normals) is
+ *   the normal state N of Alg. 1 (Sec. 3.4: the pixel state sums voxel normals) is
  *   N = sum_k T_k alpha_k n_k with n the voxel's normal in world coordinates:
  *   minus the normalised gradient of the voxel's trilinear raw density at its
  *   centre, rotated by the octree's pose (zero where that gradient is zero).

@@ -560,7 +560,7 @@ def test_backward_through_the_colour_clamp():
 
 
 # ---------------------------------------------------------------------------
-# normal state N (Alg. 1: N aggregates voxel normals)
+# normal state N (Alg. 1: the pixel state sums voxel normals)
 # ---------------------------------------------------------------------------
 
 def _linear_field(u, k0=3.0, scale=0.7):

@@ -1,4 +1,4 @@
-"""Normal state N (Alg. 1: the pixel state aggregates voxel normals) on the GPU vs the FP64
+"""Normal state N (Alg. 1: the pixel state sums voxel normals) on the GPU vs the FP64
 oracle: forward values and the backward through N, on scenes that exercise every compositing
 path (lockstep actor partials, stops inside an actor, more actors per tile than lockstep slots,
 the 1080p compositional frame).
