@@ -2,6 +2,7 @@
 // saved state and per-kernel event timing.  Declarations and the contract of
 // every entry point are in include/dv.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -134,13 +135,21 @@ void prof_end(dv_ctx* ctx, int k, cudaStream_t s, cudaEvent_t a) {
     ctx->pending.push_back({k, a, b});
 }
 
+// A pipeline stage: an NVTX range named after the stage (seen by profilers; a no-op without one)
+// and, while profiling is enabled, a pair of CUDA events on the stage's stream.
 struct Prof {
     dv_ctx* ctx;
     int k;
     cudaStream_t s;
     cudaEvent_t a;
-    Prof(dv_ctx* c, int kk, cudaStream_t ss) : ctx(c), k(kk), s(ss) { prof_begin(c, kk, ss, &a); }
-    ~Prof() { prof_end(ctx, k, s, a); }
+    Prof(dv_ctx* c, int kk, cudaStream_t ss) : ctx(c), k(kk), s(ss) {
+        nvtxRangePushA(kKernelNames[kk]);
+        prof_begin(c, kk, ss, &a);
+    }
+    ~Prof() {
+        prof_end(ctx, k, s, a);
+        nvtxRangePop();
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -1195,6 +1204,11 @@ dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, doub
 }  // extern "C"
 
 namespace dv {
+// Camera and pose checks of one render request (the serving loop's admission).
+dv_status validate_request(const dv_camera& cam, const dv_pose* poses, int n_oct) {
+    return validate_view(nullptr, cam, poses, n_oct);
+}
+
 // Render of views whose outputs live in separate buffers (used by the serving loop).
 dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
                             const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,

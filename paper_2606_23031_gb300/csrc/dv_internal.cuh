@@ -207,6 +207,9 @@ cudaError_t launch_sky_fwd(const SkyView& v, const float* env, int He, int We, c
 cudaError_t launch_sky_bwd(const SkyView& v, const float* env, int He, int We, const float* alpha, const float* d_out,
                            float* d_env, float* d_alpha, cudaStream_t s);
 
+// camera and pose checks of one render request (the same as dv_render's); no context needed
+dv_status validate_request(const dv_camera& cam, const dv_pose* poses, int n_oct);
+
 // render of views whose outputs live in separate device buffers (serving loop)
 dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
                             const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,

@@ -182,6 +182,14 @@ dv_status dv_serve_submit(dv_server* S, const dv_camera* cam, const dv_pose* pos
     if (!S || !cam || !poses || !ticket) return DV_ERR_INVALID_ARG;
     const int64_t px = (int64_t)cam->W * cam->H;
     if (cam->W < 0 || cam->H < 0 || (px > 0 && (!rgb || !depth || !alpha))) return DV_ERR_INVALID_ARG;
+    // a request that would fail its render (non-finite or non-rigid pose, bad intrinsics) is rejected
+    // here, before it can join a batch and fail the requests batched with it
+    const dv_status vs = dv::validate_request(*cam, poses, (int)S->oct.size());
+    if (vs != DV_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->err = "request rejected at admission (bad camera or pose)";
+        return vs;
+    }
     auto r = std::make_shared<Request>();
     r->cam = *cam;
     r->poses.assign(poses, poses + S->oct.size());

@@ -80,3 +80,26 @@ def test_bounded_wait_times_out_and_budget_admits_everything(dv):
     srv.close()
     assert st["requests"] == len(reqs)
     assert st["max_batch"] == 1
+
+
+def test_poisoned_request_is_rejected_at_admission(dv):
+    # a non-finite or non-rigid actor pose is refused by submit itself, so it cannot join a batch and
+    # fail the requests batched with it; the others are served as usual
+    sc = small_comp_scene(seed=31, n_actors=2)
+    ds = device_scene(sc)
+    reqs = _requests(sc, 6, seed=2)
+    srv = dv.Server(ds, max_views=8, n_workers=1, max_batch_pixels=10 ** 7, max_inflight_pixels=10 ** 8,
+                    opts=dv.make_opts(1, 1e-4))
+    tickets = [srv.submit(cam, poses, _outputs(cam)) for cam, poses in reqs[:3]]
+    cam, poses = reqs[3]
+    bad_nan = [poses[0], synth.Pose(poses[1].R, np.array([np.nan, 0.0, 0.0])), poses[2]]
+    bad_scale = [poses[0], synth.Pose(2.0 * np.asarray(poses[1].R), poses[1].t), poses[2]]
+    for bad in (bad_nan, bad_scale):
+        with pytest.raises(RuntimeError):
+            srv.submit(cam, bad, _outputs(cam))
+    tickets += [srv.submit(c, p, _outputs(c)) for c, p in reqs[4:]]
+    lat = [srv.wait(t, 60000.0) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert all(x >= 0 for x in lat)
+    assert st["requests"] == 5
