@@ -58,7 +58,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-normals", action="store_true", help="skip the fwd+bwd timing with the normal state N")
+    p.add_argument("--core-only", action="store_true",
+                   help="time only the rendering path: skip the normals, sky, feature-field and initialisation sections")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     p.add_argument("--seed", type=int, default=0)
@@ -441,7 +442,7 @@ def run_ours(args):
     # ---- timed fwd+bwd with the normal state N (rendered and differentiated as well) ----
     g_n = None
     ms_n = 0.0
-    if not args.no_normals:
+    if not args.core_only:
         g_n = torch.randn((n_pix, 3), generator=torch.Generator(dev).manual_seed(args.seed + 7), device=dev)
 
         def step_n():
@@ -466,7 +467,7 @@ def run_ours(args):
 
     # ---- sky composite of Eq. 2 on the frame (1024 x 2048 equirectangular map): forward and backward ----
     ms_sky_f = ms_sky_b = 0.0
-    if not args.no_normals:
+    if not args.core_only:
         env = torch.rand((1024, 2048, 3), generator=torch.Generator(dev).manual_seed(args.seed + 9), device=dev)
         rgb0, _, alpha0, _ = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx)
         sky_out = torch.empty_like(rgb0)
@@ -491,7 +492,7 @@ def run_ours(args):
 
     # ---- feature fields: weights export of the frame, 64-channel feature render and fusion ----
     feats = None
-    if not args.no_normals:
+    if not args.core_only:
         rgb0, _, alpha0, st0 = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
         nv = sum(o.n for o in sc.octrees)
         fe = torch.randn((nv, 64), generator=torch.Generator(dev).manual_seed(args.seed + 11), device=dev)
@@ -525,7 +526,7 @@ def run_ours(args):
     # ---- LiDAR-guided initialisation (Sec. 3.3) of the frame's background: shared corners, Eq. 1
     # prior from a 1.4M-point synthetic sweep, one proximity-subdivision round ----
     init = None
-    if not args.no_normals:
+    if not args.core_only:
         import synth as _sy
         rng_i = np.random.default_rng(args.seed + 13)
         lay = _sy.city_layout(rng_i, 100.0, 30.0, 20)
@@ -689,13 +690,13 @@ def run_ours(args):
                 "fwd": {"value": value_fwd, "unit": "Mpix/s", "ms_per_step": ms_fwd},
                 "features": feats,
                 "init": init,
-                "sky": None if args.no_normals else {
+                "sky": None if args.core_only else {
                     "what": "sky composite of Eq. 2 on the frame, 1024x2048 equirectangular map",
                     "fwd_us": 1e3 * ms_sky_f / args.steps, "bwd_us": 1e3 * ms_sky_b / args.steps,
                     "fwd_gbs": 28.0 * n_pix / (ms_sky_f / args.steps * 1e-3) / 1e9,
                     "fwd_frac": 28.0 * n_pix / (ms_sky_f / args.steps * 1e-3) / 1e9 / pk["hbm_gbs"],
                     "bytes_per_pixel": {"fwd": 28, "bwd": 24}},
-                "normals": None if args.no_normals else {
+                "normals": None if args.core_only else {
                     "value": whole_job_mpix_s(world, n_pix, ms_nrm), "unit": "Mpix/s", "ms_per_step": ms_nrm,
                     "what": "fwd+bwd also rendering the normal state N and back-propagating a gradient on it"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,

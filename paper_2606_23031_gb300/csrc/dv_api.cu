@@ -894,7 +894,13 @@ dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, c
     if (n_pix < 0 || C < 1 || C > 65536) return fail(ctx, DV_ERR_INVALID_ARG, "bad pixel or channel count");
     if (n_pix > 0 && (!offsets || !feat2d || !accum)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
-    cudaError_t e = dv::launch_feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::Arena ar;
+    ar.pool = ctx->pool;
+    ar.stream = s;
+    cudaError_t e = dv::feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, ar, s);
+    ar.release();
+    if (e == cudaErrorInvalidValue) return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 - 1 slots");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "feature fusion");
     return DV_OK;
 }

@@ -831,8 +831,17 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
                 ps.n += pn;
             }
         } else {
-            walk_actor_lane<BWD, KS, NRM, WEX>(ps, bw, bp, vo, it, pval, pmask, wbit, rec, s_sub[it.o],
-                                               s_sub[it.o + 1], dc, grad_rec, &ex);
+            // the out-of-line walk takes copies: an object whose address reaches a call stays in
+            // local memory everywhere, so the hot-path state (ps, bw, dc, nxt, ex) never does
+            Pix<NRM> pl = ps;
+            const Bwd<NRM> bl = bw;
+            const ActInt il = it;
+            const float dl[3] = {dc[0], dc[1], dc[2]};
+            ExportSink xl = ex;
+            walk_actor_lane<BWD, KS, NRM, WEX>(pl, bl, bp, vo, il, pval, pmask, wbit, rec, s_sub[il.o],
+                                               s_sub[il.o + 1], dl, grad_rec, &xl);
+            ps = pl;
+            ex = xl;
         }
     };
 

@@ -112,18 +112,38 @@ __global__ void k_soft_prior(const uint64_t* __restrict__ grid, int64_t n_corner
     int64_t c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) c[a] = (int64_t)floor((q[a] - f.root_min[a]) / h);
+    // x is the key's low field, so the three cells x-1..x+1 of one (y, z) row are one run of keys:
+    // one search per row.  The centre row goes first; another row is skipped when its box is
+    // no nearer than the best point so far, so the minimum is still the one over all 27 cells.
+    // The row's lower bound takes a slack of 1e-9 h off each axis gap: a point's cell comes from
+    // a quotient below 2^21 in FP64, so it can sit at most ~5e-10 h across a cell boundary.
+    double gap_lo[3], gap_hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double lo = f.root_min[a] + (double)c[a] * h;
+        gap_lo[a] = fmax(0.0, q[a] - lo - 1e-9 * h);
+        gap_hi[a] = fmax(0.0, lo + h - q[a] - 1e-9 * h);
+    }
     double best = INFINITY;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const uint64_t key = cell_key(c[0] + dx, c[1] + dy, c[2] + dz);
-                for (int64_t e = lower_bound(ckey, m, key); e < m && ckey[e] == key; ++e) {
-                    const uint32_t p = cidx[e];
-                    const double ex = (double)cloud[p * 3 + 0] - q[0], ey = (double)cloud[p * 3 + 1] - q[1],
-                                 ez = (double)cloud[p * 3 + 2] - q[2];
-                    best = fmin(best, ex * ex + ey * ey + ez * ez);
-                }
+    for (int it = 0; it < 9; ++it) {
+        const int r = (it + 4) % 9;  // it = 0: the centre row
+        const int dy = r % 3 - 1, dz = r / 3 - 1;
+        {
+            const double gy = dy < 0 ? gap_lo[1] : (dy > 0 ? gap_hi[1] : 0.0);
+            const double gz = dz < 0 ? gap_lo[2] : (dz > 0 ? gap_hi[2] : 0.0);
+            if (gy * gy + gz * gz >= best) continue;
+        }
+        {
+            const uint64_t k_lo = cell_key(c[0] - 1, c[1] + dy, c[2] + dz);
+            const uint64_t k_hi = cell_key(c[0] + 1, c[1] + dy, c[2] + dz);
+            for (int64_t e = lower_bound(ckey, m, k_lo); e < m && ckey[e] <= k_hi; ++e) {
+                const uint32_t p = cidx[e];
+                const double ex = (double)cloud[p * 3 + 0] - q[0], ey = (double)cloud[p * 3 + 1] - q[1],
+                             ez = (double)cloud[p * 3 + 2] - q[2];
+                best = fmin(best, ex * ex + ey * ey + ez * ez);
             }
+        }
+    }
     // Eq. 1 (beyond the 27-cell radius the exponential is below float resolution at v_far)
     const double ss = (double)s * (double)s;
     const double e = best < INFINITY ? exp(-2.0 * best / ss) : 0.0;

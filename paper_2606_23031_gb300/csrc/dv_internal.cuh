@@ -171,8 +171,9 @@ cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64
 // feature fields over a weights export (see dv_features.cu)
 cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
                                const float* feat, int C, float* out, cudaStream_t s);
-cudaError_t launch_feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
-                             const float* f2d, int C, float* acc, float* wsum, cudaStream_t s);
+// sorts the slots by voxel (scratch from ar; reads the slot count back, so it synchronises s)
+cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt, const float* f2d,
+                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s);
 
 // LiDAR-guided initialisation (see dv_init.cu); the calls that return a size synchronise the stream
 cudaError_t key_levels(const uint64_t* keys, int64_t n, uint32_t* levels_host, Arena& ar, cudaStream_t s);

@@ -116,3 +116,60 @@ def test_colour_features_reproduce_the_render(dv):
     st.free()
     err = np.abs(F - rgb.cpu().numpy()).max()
     assert err <= 1e-5, f"colour features vs RGB: {err:.3g}"
+
+
+@pytest.mark.parametrize("Cc", [1, 4, 8, 16, 32, 40, 64, 100, 128, 300])
+def test_feature_kernels_on_synthetic_slots(dv, Cc):
+    # Slot lists with the export's layout but chosen to reach every kernel path: a skewed voxel
+    # mix (a few voxels own thousands of slots, so their runs cross the 256-slot chunks of the
+    # fusion), empty pixels, zero weights, and channel counts for the 16-byte and the scalar
+    # render paths and for one, two and four channels per lane (300: several passes).  The
+    # sums are plain definitions, compared with FP64 numpy.
+    import torch
+    import paper_2606_23031_gb300 as m
+    rng = np.random.default_rng(70 + Cc)
+    P, nv = 3000, 5000
+    cnt = rng.integers(0, 40, size=P)
+    cnt[rng.random(P) < 0.1] = 0
+    off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    n = int(off[-1])
+    heavy = rng.integers(0, nv, size=4)
+    vox = np.where(rng.random(n) < 0.3, heavy[rng.integers(0, 4, size=n)], rng.integers(0, nv, size=n))
+    w = np.float32(rng.random(n))
+    w[rng.random(n) < 0.05] = 0.0
+    feat = np.float32(rng.normal(size=(nv, Cc)))
+    f2d = np.float32(rng.normal(size=(P, Cc)))
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    W = m.Weights(dev(off), dev(vox.astype(np.int32)), dev(w))
+    F = m.dv_features_render(W, dev(feat)).cpu().numpy()
+    acc = torch.zeros((nv, Cc), device="cuda")
+    wsum = torch.zeros(nv, device="cuda")
+    m.dv_features_fuse(W, dev(f2d), acc, wsum)
+    torch.cuda.synchronize()
+    w64 = np.float64(w)
+    F_ref = np.zeros((P, Cc))
+    for p in range(P):
+        s = slice(off[p], off[p + 1])
+        F_ref[p] = w64[s] @ np.float64(feat[vox[s]])
+    pix = np.repeat(np.arange(P), cnt)
+    acc_ref = np.zeros((nv, Cc))
+    np.add.at(acc_ref, vox, w64[:, None] * np.float64(f2d[pix]))
+    ws_ref = np.bincount(vox, weights=w64, minlength=nv)
+    assert np.bincount(vox).max() > 1000
+    err = np.abs(F - F_ref).max()
+    assert err <= 1e-5 * max(1.0, np.abs(F_ref).max()), f"feature render, C={Cc}: {err:.3g}"
+    check_grad(acc.cpu().numpy(), acc_ref, f"fused features, C={Cc}")
+    check_grad(wsum.cpu().numpy(), ws_ref, f"fused weights, C={Cc}")
+
+
+def test_feature_fusion_without_slots(dv):
+    # every pixel empty: nothing is added, and a NULL weight sum is accepted
+    import torch
+    import paper_2606_23031_gb300 as m
+    W = m.Weights(torch.zeros(101, dtype=torch.int64, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"),
+                  torch.zeros(0, device="cuda"))
+    acc = torch.zeros((10, 64), device="cuda")
+    m.dv_features_fuse(W, torch.ones((100, 64), device="cuda"), acc)
+    assert float(acc.abs().sum()) == 0.0
+    F = m.dv_features_render(W, torch.ones((10, 64), device="cuda"))
+    assert F.shape == (100, 64) and float(F.abs().sum()) == 0.0

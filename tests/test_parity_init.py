@@ -76,6 +76,28 @@ def test_soft_prior_matches_eq1_from_nearest_points(dv):
     assert np.all(empty == np.float32(-10.0))
 
 
+def test_soft_prior_with_dense_clusters(dv):
+    # Dense blobs put hundreds of points into a few cells, so the search's row pruning decides
+    # most corners near them; corners on every third grid line sit exactly on cell boundaries
+    # (cell = 3 finest voxels).  Still the brute-force nearest point of the oracle.
+    import torch
+    import paper_2606_23031_gb300 as m
+    rng = np.random.default_rng(73)
+    centres = rng.uniform(-0.7, 0.7, size=(6, 3))
+    blobs = centres[rng.integers(0, 6, size=3000)] + 0.02 * rng.normal(size=(3000, 3))
+    cloud = np.float32(np.concatenate([blobs, _surface_cloud(rng, 400)]))
+    center, root, L = (0.0, 0.0, 0.0), 2.0, 5
+    keys = _grid_keys(L)
+    grid_g, _ = m.dv_shared_corners(_keys_t(keys), L)
+    s_min = root / 2 ** L
+    dens = m.dv_soft_prior(grid_g, center, root, L, torch.as_tensor(cloud, device="cuda"), s_min).cpu().numpy()
+    pts, _ = oi.shared_corners(keys, L)
+    world = oi.grid_to_world(pts, center, root, L)
+    ref = oi.soft_prior(oi.nearest_distance(world, np.float64(cloud)), s_min)
+    assert (ref > -5.0).sum() > 100
+    np.testing.assert_allclose(dens, ref, rtol=0, atol=1e-5)
+
+
 def test_corner_gather_and_scatter(dv):
     import torch
     import paper_2606_23031_gb300 as m
