@@ -120,6 +120,17 @@ void dv_destroy(dv_ctx* ctx);
 const char* dv_last_error(const dv_ctx* ctx);
 /* Library version string. */
 const char* dv_version(void);
+/*
+ * Bounded waits.  The one-sweep radix sort's look-back is the library's only
+ * wait on other thread blocks (it waits only on tiles that started earlier, so
+ * it ends); each spin is bounded, and a bound that runs out sets a per-device
+ * error word.  Every dv_render call takes and clears that word in its size
+ * read-back and then fails with DV_ERR_TIMEOUT: the sorts of an earlier call on
+ * the device gave wrong orders, and that call's results must be discarded.
+ * dv_debug_flag_spin_timeout sets the word from the host (a test hook: no
+ * kernel is made to wait), so the report path can be checked.  Synchronous.
+ */
+dv_status dv_debug_flag_spin_timeout(dv_ctx* ctx);
 
 /*
  * Forward render (Sec. 3.4, Algorithm 1).  For each pixel of each camera the

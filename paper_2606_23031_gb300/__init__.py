@@ -127,6 +127,8 @@ def load(path: str | None = None):
     lib.dv_destroy.restype = None
     lib.dv_last_error.argtypes = [C.c_void_p]
     lib.dv_last_error.restype = C.c_char_p
+    lib.dv_debug_flag_spin_timeout.argtypes = [C.c_void_p]
+    lib.dv_debug_flag_spin_timeout.restype = C.c_int
     lib.dv_version.restype = C.c_char_p
     lib.dv_render.argtypes = [C.c_void_p, C.POINTER(dv_octree), C.c_int32, C.POINTER(dv_pose), C.POINTER(dv_camera),
                               C.c_int32, C.POINTER(dv_opts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -243,6 +245,10 @@ class Context:
     def check(self, st):
         if st != DV_OK:
             raise DVError(st, load().dv_last_error(self.handle).decode())
+
+    def debug_flag_spin_timeout(self):
+        """Test hook: marks this device's wait-error word, so the next render reports DV_ERR_TIMEOUT."""
+        self.check(load().dv_debug_flag_spin_timeout(self.handle))
 
     def close(self):
         if self.handle:

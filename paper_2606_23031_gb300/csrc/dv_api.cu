@@ -46,6 +46,7 @@ struct dv_ctx {
     uint64_t* h_scalars_dev = nullptr;  // the same host words as the device sees them
     uint64_t* d_scalars = nullptr;  // device counters
     cudaEvent_t ev_sizes = nullptr;  // the scalars have reached the host
+    uint32_t* d_spin_err = nullptr;  // the device's wait-error word
     bool profiling = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> spare;
@@ -488,7 +489,7 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     // visibility scan, which needs none of them
     // a kernel stores the counters into mapped host memory: no copy engine is involved, so a large
     // device-to-host transfer queued by the caller on another stream cannot delay this read-back
-    if (e == cudaSuccess) e = launch_publish(ctx->d_scalars, ctx->h_scalars_dev, 3, s);
+    if (e == cudaSuccess) e = launch_publish(ctx->d_scalars, ctx->h_scalars_dev, 3, ctx->d_spin_err, 2, s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_sizes, s);
     {
         Prof p(ctx, KP_SCAN, s);
@@ -502,6 +503,11 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     const int64_t n_vis = (int64_t)(uint32_t)ctx->h_scalars[0];
     const int64_t P = (int64_t)ctx->h_scalars[1];
     const uint32_t flags = (uint32_t)ctx->h_scalars[2];
+    if (flags & DV_FLAG_SPIN_TIMEOUT) {
+        ar.release();
+        return fail(ctx, DV_ERR_TIMEOUT, "a radix-sort pass on this device ran out of its bounded look-back wait in an "
+                                         "earlier call; that call's results are invalid");
+    }
     if (flags & DV_FLAG_BAD_LEVEL) {
         ar.release();
         return fail(ctx, DV_ERR_INVALID_ARG, "a leaf key has a level above its octree's max_level or an index "
@@ -663,7 +669,8 @@ dv_status dv_create(dv_ctx** out, int32_t device) {
         cudaMemPoolDestroy(ctx->pool);
         return DV_ERR_NOMEM;
     }
-    if (cudaEventCreateWithFlags(&ctx->ev_sizes, cudaEventDisableTiming) != cudaSuccess) {
+    ctx->d_spin_err = dv::spin_error_word();
+    if (!ctx->d_spin_err || cudaEventCreateWithFlags(&ctx->ev_sizes, cudaEventDisableTiming) != cudaSuccess) {
         cudaFree(ctx->d_scalars);
         cudaFreeHost(ctx->h_scalars);
         cudaMemPoolDestroy(ctx->pool);
@@ -671,6 +678,14 @@ dv_status dv_create(dv_ctx** out, int32_t device) {
     }
     *out = ctx.release();
     return DV_OK;
+}
+
+dv_status dv_debug_flag_spin_timeout(dv_ctx* ctx) {
+    if (!ctx || !ctx->d_spin_err) return DV_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const uint32_t one = 1u;
+    const cudaError_t e = cudaMemcpy(ctx->d_spin_err, &one, sizeof(one), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? DV_OK : cuda_fail(ctx, e, "flag spin timeout");
 }
 
 void dv_destroy(dv_ctx* ctx) {

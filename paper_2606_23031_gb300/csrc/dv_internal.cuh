@@ -83,6 +83,7 @@ void count_launches(long long n);
 
 // error flags written by kernels (bitmask in device memory)
 #define DV_FLAG_BAD_LEVEL 1u
+#define DV_FLAG_SPIN_TIMEOUT 2u  // a bounded wait of a sort ran out (folded in from the device's error word)
 
 namespace dv {
 
@@ -127,7 +128,12 @@ cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt,
 cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
                            uint32_t* flags, unsigned long long* totals, cudaStream_t s);
 // n (<= 32) counters from device memory into mapped host memory, by a kernel (no copy engine)
-cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, cudaStream_t s);
+// copies n words into mapped host memory; with spin_err, takes (and clears) the device's wait-error
+// word and sets DV_FLAG_SPIN_TIMEOUT in word flag_idx
+cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, uint32_t* spin_err, int flag_idx,
+                           cudaStream_t s);
+// device address of this device's wait-error word (bounded waits that run out set it); nullptr on failure
+uint32_t* spin_error_word();
 cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
                            uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
 cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,

@@ -466,14 +466,20 @@ cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* sc
 
 // copies n counters into mapped host memory (system-scope stores, visible to the host once the
 // stream has passed this kernel)
-__global__ void k_publish(const uint64_t* __restrict__ src, volatile uint64_t* dst, int n) {
+__global__ void k_publish(const uint64_t* __restrict__ src, volatile uint64_t* dst, int n, uint32_t* spin_err,
+                          int flag_idx) {
     const int t = threadIdx.x;
-    if (t < n) dst[t] = src[t];
+    if (t < n) {
+        uint64_t v = src[t];
+        if (t == flag_idx && spin_err && atomicExch(spin_err, 0u)) v |= DV_FLAG_SPIN_TIMEOUT;
+        dst[t] = v;
+    }
     __threadfence_system();
 }
 
-cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, cudaStream_t s) {
-    k_publish<<<1, 32, 0, s>>>(src, host_mapped_dst, n);
+cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, uint32_t* spin_err, int flag_idx,
+                           cudaStream_t s) {
+    k_publish<<<1, 32, 0, s>>>(src, host_mapped_dst, n, spin_err, flag_idx);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -247,8 +247,13 @@ cudaError_t radix_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_al
 // inclusive predecessor (flag INC) ends the walk -- publishes its inclusive
 // count and scatters.  A tile only waits on tiles that took their index
 // earlier, so every wait ends; each spin is still bounded, and a bound that
-// runs out sets an error flag.
+// runs out ends the tile's walk and sets the device's wait-error word, which
+// the next render's size read-back reports as a timeout.
 // ---------------------------------------------------------------------------
+
+// this device's wait-error word: a pass whose look-back bound runs out sets it (as well as the
+// call's own flag); the render's size read-back takes it and reports a timeout
+__device__ uint32_t g_spin_error = 0u;
 
 constexpr int OS_THREADS = 256;
 constexpr int OS_MAX_PASSES = 8;
@@ -370,6 +375,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
                 while ((v[i] & ~OS_VAL) == 0 && ++spins < OS_SPIN_LIMIT) v[i] = os_load(sp);
                 if ((v[i] & ~OS_VAL) == 0) {
                     atomicOr(err, 1u);
+                    atomicOr(&g_spin_error, 1u);
                     fin = true;
                     break;
                 }
@@ -452,6 +458,11 @@ cudaError_t onesweep(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt,
 }
 
 }  // namespace
+
+uint32_t* spin_error_word() {
+    void* p = nullptr;
+    return cudaGetSymbolAddress(&p, g_spin_error) == cudaSuccess ? static_cast<uint32_t*>(p) : nullptr;
+}
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
                             cudaStream_t s) {
