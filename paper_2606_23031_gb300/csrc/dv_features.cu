@@ -85,23 +85,36 @@ __global__ void __launch_bounds__(FT_WARPS * 32) k_feat_render4(int64_t n_pix, c
 
 constexpr int FZ_CHUNK = 256;  // sorted slots per warp
 
-// key = voxel, value = slot, pw[slot] = (pixel, weight bits); one thread per pixel; the largest
-// voxel index goes to *vmax
-__global__ void __launch_bounds__(256) k_fuse_prep(int64_t n_pix, const int64_t* __restrict__ off,
-                                                   const uint32_t* __restrict__ vox, const float* __restrict__ wgt,
-                                                   uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-                                                   uint2* __restrict__ pw, uint32_t* __restrict__ vmax) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// key = voxel, value = slot, pw[slot] = (pixel, weight bits); the largest voxel index goes to *vmax.
+// A block takes FZ_PREP consecutive pixels, whose slots are one contiguous range, and strides over
+// that range with coalesced loads and stores; a slot's pixel is the last of the block's offsets at
+// or below it (binary search in shared memory).
+constexpr int FZ_PREP = 256;
+__global__ void __launch_bounds__(FZ_PREP) k_fuse_prep(int64_t n_pix, const int64_t* __restrict__ off,
+                                                       const uint32_t* __restrict__ vox, const float* __restrict__ wgt,
+                                                       uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                                                       uint2* __restrict__ pw, uint32_t* __restrict__ vmax) {
+    __shared__ int64_t s_off[FZ_PREP + 1];
+    const int64_t p0 = (int64_t)blockIdx.x * FZ_PREP;
+    const int np = (int)min((int64_t)FZ_PREP, n_pix - p0);
+    for (int i = threadIdx.x; i <= np; i += FZ_PREP) s_off[i] = off[p0 + i];
+    __syncthreads();
     uint32_t m = 0;
-    if (p < n_pix) {
-        const int64_t e1 = off[p + 1];
-        for (int64_t e = off[p]; e < e1; ++e) {
-            const uint32_t v = __ldg(vox + e);
-            key[e] = v;
-            val[e] = (uint32_t)e;
-            pw[e] = make_uint2((uint32_t)p, __float_as_uint(__ldg(wgt + e)));
-            m = max(m, v);
+    const int64_t e1 = s_off[np];
+    for (int64_t e = s_off[0] + threadIdx.x; e < e1; e += FZ_PREP) {
+        int lo = 0, hi = np - 1;  // the owner i has s_off[i] <= e < s_off[i + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e)
+                lo = mid;
+            else
+                hi = mid - 1;
         }
+        const uint32_t v = __ldg(vox + e);
+        key[e] = v;
+        val[e] = (uint32_t)e;
+        pw[e] = make_uint2((uint32_t)(p0 + lo), __float_as_uint(__ldg(wgt + e)));
+        m = max(m, v);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -175,8 +188,9 @@ __global__ void __launch_bounds__(256) k_fuse_runs(int64_t n, const uint32_t* __
 // at a time gathers their rows (R loads in flight per lane) and sums them in slot order into
 // the running voxel's quads; at a run's end the S partial quads are added across the groups and
 // the run is added once.
-template <int Q, int R = (Q < 8 ? Q : 8)>
-__global__ void __launch_bounds__(256) k_fuse_runs4(int64_t n, const uint32_t* __restrict__ skey,
+// (4 rows in flight and 5 resident blocks per SM measured best: 8 rows held 3 blocks, more blocks spilled)
+template <int Q, int R = (Q < 4 ? Q : 4)>
+__global__ void __launch_bounds__(256, 5) k_fuse_runs4(int64_t n, const uint32_t* __restrict__ skey,
                                                     const uint32_t* __restrict__ sval, const uint2* __restrict__ pw,
                                                     const float4* __restrict__ f2d, float4* __restrict__ acc,
                                                     float* __restrict__ wsum) {
@@ -281,7 +295,7 @@ cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, co
     if (ar.err != cudaSuccess) return ar.err;
     e = cudaMemsetAsync(vmax, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_fuse_prep<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(n_pix, off, vox, wgt, k0, v0, pw, vmax);
+    k_fuse_prep<<<(unsigned)((n_pix + FZ_PREP - 1) / FZ_PREP), FZ_PREP, 0, s>>>(n_pix, off, vox, wgt, k0, v0, pw, vmax);
     count_launches(1);
     uint32_t vm = 0;
     e = cudaMemcpyAsync(&vm, vmax, sizeof(vm), cudaMemcpyDeviceToHost, s);
