@@ -453,6 +453,8 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
                                                         unsigned long long* __restrict__ work,
                                                         const int64_t* __restrict__ ex_off,
                                                         uint32_t* __restrict__ ex_vid, float* __restrict__ ex_w) {
+    pdl_wait();
+    pdl_launch_dependents();
     constexpr bool REPLAY = BWD || WEX;  // phase 3 replays every actor interval the ray reached
     __shared__ float4 s_rec[2][CT_THREADS][4];
     __shared__ float4 s_nv[NRM ? 2 : 1][NRM ? CT_THREADS : 1];  // voxel normals of the staged records
@@ -1057,6 +1059,8 @@ template <bool NRM>
 __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdParams sp,
                                                 const uint32_t* __restrict__ sorted_g, int64_t n_vis,
                                                 const VoxRec* __restrict__ rec, const float* __restrict__ grad_rec) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
     const BatchParams& bp = sp.bp;
@@ -1172,13 +1176,9 @@ void composite_fwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* p
                      const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, uint32_t* n_seg,
                      float* t_final, unsigned long long* work, cudaStream_t s) {
     if (bp.K == 1)
-        k_composite<false, 1, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr,
-            nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
+        launch_pdl(k_composite<false, 1, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
     else
-        k_composite<false, 0, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr,
-            nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
+        launch_pdl(k_composite<false, 0, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
 }
 
 template <bool NRM>
@@ -1190,13 +1190,9 @@ void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* p
     // are only read in the backward
     float* tf = const_cast<float*>(t_final);
     if (bp.K == 1)
-        k_composite<true, 1, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha,
-            g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
+        launch_pdl(k_composite<true, 1, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha, g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
     else
-        k_composite<true, 0, NRM, false><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha,
-            g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
+        launch_pdl(k_composite<true, 0, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha, g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
 }
 
 }  // namespace
@@ -1238,13 +1234,9 @@ cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, co
                                     cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
     if (bp.K == 1)
-        k_composite<false, 1, false, true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr,
-            nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
+        launch_pdl(k_composite<false, 1, false, true>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
     else
-        k_composite<false, 0, false, true><<<2 * bp.n_tiles, CT_THREADS, 0, s>>>(
-            bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr,
-            nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
+        launch_pdl(k_composite<false, 0, false, true>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1260,9 +1252,9 @@ cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64
         sp.d_sh[o] = (d_sh && o < bp.n_oct) ? d_sh[o] : nullptr;
     }
     if (with_normals)
-        k_sh_bwd<true><<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(sp, sorted_g, n_vis, rec, grad_rec);
+        launch_pdl(k_sh_bwd<true>, dim3((unsigned)((n_vis + 255) / 256)), dim3(256), s, sp, sorted_g, n_vis, rec, grad_rec);
     else
-        k_sh_bwd<false><<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(sp, sorted_g, n_vis, rec, grad_rec);
+        launch_pdl(k_sh_bwd<false>, dim3((unsigned)((n_vis + 255) / 256)), dim3(256), s, sp, sorted_g, n_vis, rec, grad_rec);
     count_launches(1);
     return cudaGetLastError();
 }

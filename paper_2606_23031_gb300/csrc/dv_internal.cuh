@@ -78,6 +78,32 @@ struct __align__(16) VoxRec {
 
 // process-wide count of kernel launches issued by this library (all contexts)
 namespace dv {
+
+// Programmatic dependent launch.  The kernels of the rendering path are launched with
+// programmatic stream serialisation: a kernel's blocks may be dispatched while the previous
+// kernel of the stream drains.  Each of them starts with pdl_wait(), which returns once the
+// previous kernel has completed and its memory is visible (a no-op for an ordinary launch), and
+// then signals with pdl_launch_dependents() that the next kernel may be dispatched, which the
+// hardware does only once every block of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 void count_launches(long long n);
 }
 

@@ -181,6 +181,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
                                                  uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
                                                  uint32_t* __restrict__ vis, uint32_t* __restrict__ flags,
                                                  unsigned long long* __restrict__ totals) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // view * n_vox + voxel
     uint32_t c = 0;
     if (g < bp.n_vox * bp.n_view) c = project_voxel(bp, g, cnt, rect, skey, vis, flags);
@@ -210,6 +212,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
 __global__ void k_compact(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ pos,
                           const uint64_t* __restrict__ skey, int64_t n, uint64_t* __restrict__ out_key,
                           uint32_t* __restrict__ out_val) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n || !vis[g]) return;
     const uint32_t p = pos[g];
@@ -250,6 +254,8 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
                                                  VoxRec* __restrict__ rec, float4* __restrict__ nrm,
                                                  uint32_t* __restrict__ cnt_sorted,
                                                  uint64_t* __restrict__ rect_sorted) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
     const uint32_t g = sorted_g[r];
@@ -329,6 +335,8 @@ __device__ __forceinline__ int key_group(const BatchParams& bp, uint64_t k) {
 
 __global__ void k_vis_start(const __grid_constant__ BatchParams bp, const uint64_t* __restrict__ key, int64_t n_vis,
                             uint32_t* __restrict__ vis_start) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_vis) return;
     const int grp = key_group(bp, key[r]);
@@ -344,6 +352,8 @@ __global__ void k_vis_start(const __grid_constant__ BatchParams bp, const uint64
 __global__ void k_emit(const __grid_constant__ BatchParams bp, const uint64_t* __restrict__ off,
                        const uint64_t* __restrict__ rect_sorted, const uint32_t* __restrict__ sorted_g,
                        int64_t n_vis, int64_t n_pairs, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
     int64_t lo = 0, hi = n_vis - 1;
@@ -384,6 +394,8 @@ __device__ __forceinline__ int view_of_tile(const BatchParams& bp, int t) {
 __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32_t* __restrict__ pkey,
                             const uint32_t* __restrict__ pval, const uint64_t* __restrict__ rect_sorted,
                             int64_t n_pairs, uint8_t* __restrict__ mask, uint2* __restrict__ range) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
     const uint32_t key = pkey[p];
@@ -411,6 +423,8 @@ __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32
 __device__ __forceinline__ int tile_bucket(uint2 r) { return 31 - __clz((int)(r.y - r.x) + 1); }
 
 __global__ void k_tile_count(const uint2* __restrict__ range, int n_tiles, uint32_t* __restrict__ cnt) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ uint32_t h[32];
     if (threadIdx.x < 32) h[threadIdx.x] = 0;
     __syncthreads();
@@ -421,6 +435,8 @@ __global__ void k_tile_count(const uint2* __restrict__ range, int n_tiles, uint3
 }
 
 __global__ void k_tile_offsets(uint32_t* __restrict__ cnt_off) {
+    pdl_wait();
+    pdl_launch_dependents();
     // cnt_off[0..31] counts -> cnt_off[32..63] start of each bucket, heaviest bucket first
     if (threadIdx.x == 0) {
         uint32_t run = 0;
@@ -433,6 +449,8 @@ __global__ void k_tile_offsets(uint32_t* __restrict__ cnt_off) {
 
 __global__ void k_tile_scatter(const uint2* __restrict__ range, int n_tiles, uint32_t* __restrict__ off,
                                uint32_t* __restrict__ order) {
+    pdl_wait();
+    pdl_launch_dependents();
     // block-local ranks first, then one global reservation per (block, bucket)
     __shared__ uint32_t h[32], base[32];
     if (threadIdx.x < 32) h[threadIdx.x] = 0;
@@ -455,11 +473,11 @@ cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* sc
     if (n_tiles <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(scratch64, 0, 64 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_tile_count<<<nblk(n_tiles, 256), 256, 0, s>>>(tile_range, n_tiles, scratch64);
+    launch_pdl(k_tile_count, dim3(nblk(n_tiles, 256)), dim3(256), s, tile_range, n_tiles, scratch64);
     count_launches(1);
-    k_tile_offsets<<<1, 32, 0, s>>>(scratch64);
+    launch_pdl(k_tile_offsets, dim3(1), dim3(32), s, scratch64);
     count_launches(1);
-    k_tile_scatter<<<nblk(n_tiles, 256), 256, 0, s>>>(tile_range, n_tiles, scratch64 + 32, order);
+    launch_pdl(k_tile_scatter, dim3(nblk(n_tiles, 256)), dim3(256), s, tile_range, n_tiles, scratch64 + 32, order);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -468,6 +486,8 @@ cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* sc
 // stream has passed this kernel)
 __global__ void k_publish(const uint64_t* __restrict__ src, volatile uint64_t* dst, int n, uint32_t* spin_err,
                           int flag_idx) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int t = threadIdx.x;
     if (t < n) {
         uint64_t v = src[t];
@@ -479,7 +499,7 @@ __global__ void k_publish(const uint64_t* __restrict__ src, volatile uint64_t* d
 
 cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, uint32_t* spin_err, int flag_idx,
                            cudaStream_t s) {
-    k_publish<<<1, 32, 0, s>>>(src, host_mapped_dst, n, spin_err, flag_idx);
+    launch_pdl(k_publish, dim3(1), dim3(32), s, src, host_mapped_dst, n, spin_err, flag_idx);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -488,7 +508,7 @@ cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect,
                            uint32_t* flags, unsigned long long* totals, cudaStream_t s) {
     const int64_t n = bp.n_vox * bp.n_view;
     if (n <= 0) return cudaSuccess;
-    k_project<<<nblk(n, 256), 256, 0, s>>>(bp, cnt, rect, skey, vis, flags, totals);
+    launch_pdl(k_project, dim3(nblk(n, 256)), dim3(256), s, bp, cnt, rect, skey, vis, flags, totals);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -496,7 +516,7 @@ cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect,
 cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
                            uint64_t* out_key, uint32_t* out_val, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_compact<<<nblk(n, 256), 256, 0, s>>>(vis, pos, skey, n, out_key, out_val);
+    launch_pdl(k_compact, dim3(nblk(n, 256)), dim3(256), s, vis, pos, skey, n, out_key, out_val);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -505,7 +525,7 @@ cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int6
                            const uint64_t* rect, VoxRec* rec, float4* nrm, uint32_t* cnt_sorted,
                            uint64_t* rect_sorted, cudaStream_t s) {
     if (n_vis <= 0) return cudaSuccess;
-    k_records<<<nblk(n_vis, 256), 256, 0, s>>>(bp, sorted_g, n_vis, cnt, rect, rec, nrm, cnt_sorted, rect_sorted);
+    launch_pdl(k_records, dim3(nblk(n_vis, 256)), dim3(256), s, bp, sorted_g, n_vis, cnt, rect, rec, nrm, cnt_sorted, rect_sorted);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -513,7 +533,7 @@ cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int6
 cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, int64_t n_vis, uint32_t* vis_start,
                              cudaStream_t s) {
     if (n_vis <= 0) return cudaMemsetAsync(vis_start, 0, sizeof(uint32_t) * (bp.n_view * bp.n_oct + 1), s);
-    k_vis_start<<<nblk(n_vis, 256), 256, 0, s>>>(bp, sorted_key, n_vis, vis_start);
+    launch_pdl(k_vis_start, dim3(nblk(n_vis, 256)), dim3(256), s, bp, sorted_key, n_vis, vis_start);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -522,7 +542,7 @@ cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64
                         const uint32_t* sorted_g, int64_t n_vis, int64_t n_pairs, uint32_t* pair_key,
                         uint32_t* pair_val, cudaStream_t s) {
     if (n_vis <= 0 || n_pairs <= 0) return cudaSuccess;
-    k_emit<<<nblk(n_pairs, 256), 256, 0, s>>>(bp, off, rect_sorted, sorted_g, n_vis, n_pairs, pair_key, pair_val);
+    launch_pdl(k_emit, dim3(nblk(n_pairs, 256)), dim3(256), s, bp, off, rect_sorted, sorted_g, n_vis, n_pairs, pair_key, pair_val);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -532,7 +552,7 @@ cudaError_t launch_pair_mask_ranges(const BatchParams& bp, const uint32_t* pair_
                                     int n_tiles, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(tile_range, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
-    k_pair_mask<<<nblk(n_pairs, 256), 256, 0, s>>>(bp, pair_key, pair_val, rect_sorted, n_pairs, mask, tile_range);
+    launch_pdl(k_pair_mask, dim3(nblk(n_pairs, 256)), dim3(256), s, bp, pair_key, pair_val, rect_sorted, n_pairs, mask, tile_range);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -58,6 +58,8 @@ __device__ __forceinline__ T block_excl_scan(T x, T* total) {
 
 template <typename Tin, typename Tout>
 __global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, Tout* __restrict__ bsum) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     Tout s = 0;
 #pragma unroll
@@ -71,6 +73,8 @@ __global__ void k_scan_reduce(const Tin* __restrict__ in, int64_t n, Tout* __res
 // single block: in-place exclusive scan of the block sums, writes the grand total
 template <typename Tout>
 __global__ void k_scan_top(Tout* __restrict__ bsum, int64_t nb, Tout* __restrict__ total) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ Tout carry_s;
     __shared__ Tout tot;
     if (threadIdx.x == 0) carry_s = 0;
@@ -91,6 +95,8 @@ __global__ void k_scan_top(Tout* __restrict__ bsum, int64_t nb, Tout* __restrict
 template <typename Tin, typename Tout>
 __global__ void k_scan_down(const Tin* __restrict__ in, int64_t n, const Tout* __restrict__ bsum,
                             Tout* __restrict__ out) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     Tout v[SCAN_ITEMS];
     Tout s = 0;
@@ -117,12 +123,12 @@ cudaError_t scan_impl(const Tin* in, Tout* out, int64_t n, Tout* total_dev, Aren
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     Tout* bsum = ar.alloc<Tout>((size_t)nb);
     if (!bsum) return ar.err;
-    k_scan_reduce<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
+    launch_pdl(k_scan_reduce<Tin, Tout>, dim3((unsigned)nb), dim3(SCAN_THREADS), s, in, n, bsum);
     count_launches(1);
-    k_scan_top<Tout><<<1, SCAN_THREADS, 0, s>>>(bsum, nb, total_dev);
+    launch_pdl(k_scan_top<Tout>, dim3(1), dim3(SCAN_THREADS), s, bsum, nb, total_dev);
     count_launches(1);
     if (out) {
-        k_scan_down<Tin, Tout><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum, out);
+        launch_pdl(k_scan_down<Tin, Tout>, dim3((unsigned)nb), dim3(SCAN_THREADS), s, in, n, bsum, out);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -141,6 +147,8 @@ template <typename K>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__ keys, int64_t n, int shift,
                                                             uint32_t mask, uint32_t* __restrict__ hist,
                                                             int64_t nblocks, int rounds) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ uint32_t h[RS_RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -161,6 +169,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
                                                                const uint32_t* __restrict__ offs, int64_t nblocks,
                                                                K* __restrict__ okeys, uint32_t* __restrict__ ovals,
                                                                int rounds) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ uint32_t run[RS_RADIX];       // next free slot per digit (global index)
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -218,12 +228,11 @@ cudaError_t radix_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_al
     for (int shift = 0; shift < n_bits; shift += 8) {
         int bits = n_bits - shift < 8 ? n_bits - shift : 8;
         uint32_t mask = (1u << bits) - 1u;
-        k_radix_hist<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, n, shift, mask, hist, nblocks, rounds);
+        launch_pdl(k_radix_hist<K>, dim3((unsigned)nblocks), dim3(RS_THREADS), s, src_k, n, shift, mask, hist, nblocks, rounds);
         count_launches(1);
         cudaError_t e = scan_impl<uint32_t, uint32_t>(hist, offs, nblocks * RS_RADIX, nullptr, ar, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<K><<<(unsigned)nblocks, RS_THREADS, 0, s>>>(src_k, src_v, n, shift, mask, offs, nblocks,
-                                                                     dst_k, dst_v, rounds);
+        launch_pdl(k_radix_scatter<K>, dim3((unsigned)nblocks), dim3(RS_THREADS), s, src_k, src_v, n, shift, mask, offs, nblocks, dst_k, dst_v, rounds);
         count_launches(1);
         K* tk = src_k;
         src_k = dst_k;
@@ -264,6 +273,8 @@ constexpr int OS_LOOK = 8;  // predecessors read per look-back step
 template <typename K>
 __global__ void __launch_bounds__(OS_THREADS) k_os_hist(const K* __restrict__ keys, int64_t n, int n_passes,
                                                          int n_bits, uint32_t* __restrict__ ghist) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ uint32_t h[OS_MAX_PASSES][RS_RADIX];
     for (int p = 0; p < n_passes; ++p) h[p][threadIdx.x] = 0;
     __syncthreads();
@@ -282,6 +293,8 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_hist(const K* __restrict__ ke
 
 // exclusive scan of each pass's 256 digit counts (one block per pass)
 __global__ void k_os_bins(uint32_t* __restrict__ ghist) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ uint32_t tot;
     uint32_t* h = ghist + blockIdx.x * RS_RADIX;
     const uint32_t x = h[threadIdx.x];
@@ -298,6 +311,8 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
                                                          uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
                                                          uint32_t* __restrict__ err, K* __restrict__ okeys,
                                                          uint32_t* __restrict__ ovals) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ uint32_t s_tile;
     __shared__ uint32_t run[RS_RADIX];
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
@@ -418,9 +433,9 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
     if (e != cudaSuccess) return e;
     int64_t hist_blocks = (n + OS_THREADS * 4 - 1) / (OS_THREADS * 4);  // ~4 keys per thread, at most 8 CTAs per SM
     if (hist_blocks > 152 * 8) hist_blocks = 152 * 8;
-    k_os_hist<K><<<(unsigned)(hist_blocks < 1 ? 1 : hist_blocks), OS_THREADS, 0, s>>>(keys, n, passes, n_bits, ghist);
+    launch_pdl(k_os_hist<K>, dim3((unsigned)(hist_blocks < 1 ? 1 : hist_blocks)), dim3(OS_THREADS), s, keys, n, passes, n_bits, ghist);
     count_launches(1);
-    k_os_bins<<<passes, RS_RADIX, 0, s>>>(ghist);
+    launch_pdl(k_os_bins, dim3(passes), dim3(RS_RADIX), s, ghist);
     count_launches(1);
     K* src_k = keys;
     uint32_t* src_v = vals;
@@ -429,9 +444,7 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int bits = n_bits - shift < 8 ? n_bits - shift : 8;
-        k_os_pass<K, ROUNDS><<<(unsigned)n_tiles, OS_THREADS, 0, s>>>(
-            src_k, src_v, n, shift, (1u << bits) - 1u, ghist + p * RS_RADIX, status + (size_t)p * n_tiles * RS_RADIX,
-            counters + p, err, dst_k, dst_v);
+        launch_pdl(k_os_pass<K, ROUNDS>, dim3((unsigned)n_tiles), dim3(OS_THREADS), s, src_k, src_v, n, shift, (1u << bits) - 1u, ghist + p * RS_RADIX, status + (size_t)p * n_tiles * RS_RADIX, counters + p, err, dst_k, dst_v);
         count_launches(1);
         K* tk = src_k;
         src_k = dst_k;
