@@ -247,7 +247,7 @@ dv_status dv_features_render(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets,
  * by voxel in scratch memory (about 20 bytes per slot from the context's pool)
  * and each voxel's run is summed in slot order before one atomic add per run
  * and channel.  Reads the slot count offsets[n_pix] back, so it synchronises
- * the stream.  DV_ERR_CAPACITY beyond 2^32 - 1 slots.
+ * the stream.  DV_ERR_CAPACITY beyond 2^32 - 1 slots or pixels.
  */
 dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, const uint32_t* voxel,
                            const float* weight, const float* feat2d, int32_t C, float* accum, float* wsum,

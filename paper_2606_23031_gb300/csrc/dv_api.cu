@@ -915,7 +915,7 @@ dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, c
     ar.stream = s;
     cudaError_t e = dv::feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, ar, s);
     ar.release();
-    if (e == cudaErrorInvalidValue) return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 - 1 slots");
+    if (e == cudaErrorInvalidValue) return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 - 1 slots or pixels");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "feature fusion");
     return DV_OK;
 }

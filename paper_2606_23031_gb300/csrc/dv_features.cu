@@ -285,7 +285,7 @@ cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, co
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
-    if (n > (int64_t)UINT32_MAX) return cudaErrorInvalidValue;  // slot indices are 32-bit
+    if (n > (int64_t)UINT32_MAX || n_pix > (int64_t)UINT32_MAX) return cudaErrorInvalidValue;  // 32-bit slot and pixel indices
     uint32_t* k0 = ar.alloc<uint32_t>(n);
     uint32_t* k1 = ar.alloc<uint32_t>(n);
     uint32_t* v0 = ar.alloc<uint32_t>(n);
