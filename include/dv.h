@@ -385,6 +385,10 @@ dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* state, const float* d
  * counters.  Stages: "project", "scan", "compact", "sort_vox", "records",
  * "emit", "sort_pairs", "ranges", "composite_fwd", "composite_bwd", "sh_bwd". */
 dv_status dv_profile_enable(dv_ctx* ctx, int32_t on);
+/* The same for a subset of the stages: bit k of `mask` brackets stage k (names
+ * order above); 0 turns profiling off.  Fewer events, less overhead in the
+ * timed stream. */
+dv_status dv_profile_enable_stages(dv_ctx* ctx, uint32_t mask);
 dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, double* ms, int64_t* launches);
 
 /* ------------------------------------------------------------------------

@@ -127,6 +127,8 @@ def load(path: str | None = None):
     lib.dv_destroy.restype = None
     lib.dv_last_error.argtypes = [C.c_void_p]
     lib.dv_last_error.restype = C.c_char_p
+    lib.dv_profile_enable_stages.argtypes = [C.c_void_p, C.c_uint32]
+    lib.dv_profile_enable_stages.restype = C.c_int
     lib.dv_debug_flag_spin_timeout.argtypes = [C.c_void_p]
     lib.dv_debug_flag_spin_timeout.restype = C.c_int
     lib.dv_version.restype = C.c_char_p
@@ -261,8 +263,15 @@ class Context:
         except Exception:
             pass
 
-    def profile(self, on: bool):
-        self.check(load().dv_profile_enable(self.handle, 1 if on else 0))
+    def profile(self, on: bool, stages=None):
+        """Per-stage event timing on (all stages, or only the named ones) or off."""
+        if stages is None or not on:
+            self.check(load().dv_profile_enable(self.handle, 1 if on else 0))
+        else:
+            mask = 0
+            for name in stages:
+                mask |= 1 << KERNELS.index(name)
+            self.check(load().dv_profile_enable_stages(self.handle, mask))
 
     def profile_read(self, names=KERNELS):
         n = len(names)

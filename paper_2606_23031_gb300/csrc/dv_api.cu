@@ -48,6 +48,7 @@ struct dv_ctx {
     cudaEvent_t ev_sizes = nullptr;  // the scalars have reached the host
     uint32_t* d_spin_err = nullptr;  // the device's wait-error word
     bool profiling = false;
+    uint32_t prof_mask = ~0u;  // stages bracketed by events while profiling (bit k: stage k)
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> spare;
     double ms[kNK] = {};
@@ -110,7 +111,7 @@ dv_status cuda_fail(dv_ctx* ctx, cudaError_t e, const char* where) {
 
 void prof_begin(dv_ctx* ctx, int k, cudaStream_t s, cudaEvent_t* ev) {
     *ev = nullptr;
-    if (!ctx->profiling) return;
+    if (!ctx->profiling || !((ctx->prof_mask >> k) & 1u)) return;
     cudaEvent_t e;
     if (!ctx->spare.empty()) {
         e = ctx->spare.back();
@@ -1192,6 +1193,14 @@ long long dv_launch_count(int32_t reset) {
 dv_status dv_profile_enable(dv_ctx* ctx, int32_t on) {
     if (!ctx) return DV_ERR_INVALID_ARG;
     ctx->profiling = on != 0;
+    ctx->prof_mask = ~0u;
+    return DV_OK;
+}
+
+dv_status dv_profile_enable_stages(dv_ctx* ctx, uint32_t mask) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->profiling = mask != 0;
+    ctx->prof_mask = mask;
     return DV_OK;
 }
 
