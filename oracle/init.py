@@ -146,3 +146,26 @@ def visible_from(keys, center, root_size, cams, z_min):
                 keep[v] = True
                 break
     return keep
+
+
+ASSET_MARGIN = 1.2   # an asset's cubic bound: its largest box dimension scaled outward by 20% (Sec. 3.3, assets)
+V_INIT_ASSET = -10.0  # every corner of a new asset grid starts empty, whatever its size or category
+
+
+def asset_init(box_dims, level, v_init=V_INIT_ASSET):
+    """Initial octree of a dynamic asset (Sec. 3.3, "Assets"): a uniform voxel grid in the asset's
+    canonical frame (origin at the box centre, axes along the box's), bounded by a cube whose edge is
+    the largest box dimension scaled by 1.2, every corner density at v_init.  Leaves are listed with
+    i fastest, then j, then k.  Returns (keys uint64 [8^level], dens float64 [8^level, 8], root_size,
+    center)."""
+    dims = [float(x) for x in box_dims]
+    root_size = ASSET_MARGIN * max(dims)
+    n = 1 << int(level)
+    keys = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                keys.append(int(_pack(level, i, j, k)))
+    keys = np.array(keys, np.uint64)
+    dens = np.full((len(keys), 8), float(v_init))
+    return keys, dens, root_size, (0.0, 0.0, 0.0)

@@ -114,3 +114,65 @@ def test_visibility_pruning_reading():
     # the horizontal field of view is 2 atan(32/40) ~ 77 deg: a leaf far to the side of the axis is pruned
     assert not keep[at(2, 3, 0)]
     assert 0 < keep.sum() < len(keys)
+
+
+# ---------------------------------------------------------------------------
+# asset initialisation (Sec. 3.3, "Assets")
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,level", [((4.5, 1.9, 1.6), 3), ((1.0, 2.5, 0.8), 2), ((3.0, 3.0, 3.0), 0)])
+def test_asset_grid_tiles_its_cubic_bound(dims, level):
+    keys, dens, root, center = oi.asset_init(dims, level)
+    n = 1 << level
+    assert len(keys) == n ** 3 and dens.shape == (n ** 3, 8)
+    lev, i, j, k = synth.unpack_keys(keys)
+    assert np.all(lev == level)
+    # every cell of the n^3 grid appears exactly once: the leaves tile the cube without gaps or overlaps
+    cells = np.unique(np.stack([i, j, k], 1), axis=0)
+    assert cells.shape[0] == n ** 3 and cells.min() == 0 and cells.max() == n - 1
+    # the box grown by 20% fits inside the cube centred on the box, and touches it along its largest axis
+    assert center == (0.0, 0.0, 0.0)
+    grown = 0.5 * 1.2 * np.asarray(dims, np.float64)
+    assert np.all(grown <= 0.5 * root + 1e-12)
+    assert grown.max() == pytest.approx(0.5 * root, rel=1e-15)
+    # one empty density everywhere, whatever the size
+    assert np.all(dens == -10.0)
+
+
+def test_asset_grid_renders_as_a_uniform_empty_medium():
+    """A fresh asset placed by a rigid pose renders, through the compositing oracle, exactly like one
+    homogeneous medium of density explin(-10) filling its clip box: alpha = 1 - exp(-sigma l) with l the
+    ray's chord through the clip box within the grid's cube (found by bisection of a point-in-box test).  A missing or doubled
+    leaf would change l; alpha stays far below visible (the paper's 'empty' initial density)."""
+    import oracle
+    from helpers import pose64
+    from test_oracle_pins import cam_looking, chord_bisect, ray_of
+
+    dims = (4.5, 1.9, 1.6)
+    keys, dens, root, _ = oi.asset_init(dims, 3)
+    clip = tuple(0.6 * d for d in dims)
+    act = synth.Octree(keys, np.float32(dens), np.zeros((len(keys), 1, 3), np.float32), 0, (0.0, 0.0, 0.0), root,
+                       role=synth.ACTOR, clip_half=clip)
+    bg = synth.Octree(np.zeros(0, np.uint64), np.zeros((0, 8), np.float32), np.zeros((0, 1, 3), np.float32), 0,
+                      (0.0, 0.0, 0.0), 8.0)
+    # the pose as the renderers receive it (float32)
+    R = np.float32(synth.rot_z(0.7)).astype(np.float64)
+    t = np.float32([0.3, -0.2, 0.1]).astype(np.float64)
+    cam = cam_looking((7.0, 3.0, 2.0), (0.2, -0.1, 0.0), W=12, H=9, fov=40.0)
+    rgb, depth, alpha, nseg = oracle.render([bg, act], [pose64(), pose64(R, t)], cam, oracle.Opts(K=1, eps_stop=0.0))
+    sigma = 1.1 * math.exp(-10.0 / 1.1 - 1.0)
+    hits = 0
+    for v in range(cam.H):
+        for u in range(cam.W):
+            o, d = ray_of(cam, u, v)
+            # the medium fills the clip box (as the renderers receive it, float32) within the grid's cube
+            c32 = np.minimum(np.float32(clip).astype(np.float64), 0.5 * root)
+            ch = chord_bisect(R.T @ (o - t), R.T @ d, -c32, c32, tmax=20.0)
+            if ch is None:
+                assert alpha[v, u] == 0.0
+                continue
+            hits += 1
+            a = 1.0 - math.exp(-sigma * (ch[1] - ch[0]))
+            assert alpha[v, u] == pytest.approx(a, rel=1e-9)
+            assert alpha[v, u] < 1e-3
+    assert hits >= 20
