@@ -20,8 +20,9 @@
  *    given stream has finished.  Structs passed by host pointer are read
  *    during the call only.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *    All work is enqueued on it.  A render call synchronises that stream once
- *    per camera to size its pair buffers (the only host wait on the path).
+ *    All work is enqueued on it.  A render call waits once on the host for the
+ *    sizes its projection kernel reports (an event, not a stream
+ *    synchronisation) to size its buffers: the only host wait on the path.
  *  - Leaf keys: bits [0,19) = i, [19,38) = j, [38,57) = k, [57,62) = level.
  *    A leaf spans min = center - root_size/2 + (i,j,k) * s to min + s with
  *    s = root_size / 2^level, in its octree's local frame (Sec. 3.1, where each
@@ -51,7 +52,7 @@ typedef enum {
     DV_ERR_INVALID_POSE = 2, /* a rotation is not orthonormal with det +1 (tol 1e-5) */
     DV_ERR_CAPACITY = 3,     /* a size exceeds the library's fixed limits */
     DV_ERR_CUDA = 4,         /* a CUDA runtime call failed (message has the CUDA error) */
-    DV_ERR_TIMEOUT = 5,      /* a bounded wait ran out (serving loop) */
+    DV_ERR_TIMEOUT = 5,      /* a bounded wait ran out (a sort's look-back, or a serving wait) */
     DV_ERR_NOMEM = 6         /* device or host allocation failed */
 } dv_status;
 
@@ -123,14 +124,67 @@ const char* dv_version(void);
 /*
  * Bounded waits.  The one-sweep radix sort's look-back is the library's only
  * wait on other thread blocks (it waits only on tiles that started earlier, so
- * it ends); each spin is bounded, and a bound that runs out sets a per-device
- * error word.  Every dv_render call takes and clears that word in its size
- * read-back and then fails with DV_ERR_TIMEOUT: the sorts of an earlier call on
- * the device gave wrong orders, and that call's results must be discarded.
- * dv_debug_flag_spin_timeout sets the word from the host (a test hook: no
- * kernel is made to wait), so the report path can be checked.  Synchronous.
+ * it ends); each spin is bounded, and a bound that runs out marks two words:
+ *  - the call's own flag.  Calls that sort and synchronise anyway (feature
+ *    fusion, the initialisation calls) read it before they return and fail
+ *    with DV_ERR_TIMEOUT.  A render publishes it, after its last sort, into a
+ *    host word of its saved state: dv_state_check reports it, the backward of
+ *    that state refuses to run once it is known, and the serving loop fails
+ *    the batch's requests.
+ *  - a device-wide word shared by every context on the device (a sticky
+ *    fallback for a timeout nobody checked): the next dv_render on the device
+ *    takes and clears it in its size read-back and fails with DV_ERR_TIMEOUT.
+ * dv_debug_flag_spin_timeout sets the device word from the host, so the
+ * fallback path can be checked.  Synchronous.
  */
 dv_status dv_debug_flag_spin_timeout(dv_ctx* ctx);
+
+/*
+ * Test hook of the bounded wait itself: launches one tile of a sort pass
+ * whose predecessor tile never publishes, with at most `spin_limit` reads
+ * (1 .. 2^20) per wait, and returns the tile's call flag and the device-wide
+ * word as the kernel left them (both 1 when the wait ran out), then clears the
+ * device-wide word.  Synchronous; the kernel ends after its bounded waits.
+ */
+dv_status dv_debug_sort_timeout(dv_ctx* ctx, int32_t spin_limit, uint32_t* call_flag, uint32_t* device_flag);
+
+/*
+ * Workspace reservation (the CAPACITY contract).  By default a context takes
+ * whatever scratch a call needs from its pool.  dv_reserve(ctx, bytes) limits
+ * each render call to `bytes` of workspace (its saved state plus its scratch)
+ * and grows the pool to that size now, so calls within the reservation do not
+ * allocate new device memory; bytes = 0 removes the limit.  A render that needs
+ * more fails with DV_ERR_CAPACITY, either before any work is enqueued (the part
+ * that follows from the octree, camera and tile counts) or after the
+ * projection reported its sizes (visible voxels and pairs; the outputs are then
+ * untouched).  dv_workspace_need returns the bytes the last render needed, or
+ * the part known when it failed: reserve that and retry (a second failure, if
+ * any, then reports the whole need).  DV_ERR_NOMEM if the device cannot hold
+ * the reservation.
+ */
+dv_status dv_reserve(dv_ctx* ctx, int64_t bytes);
+dv_status dv_workspace_need(const dv_ctx* ctx, int64_t* bytes);
+
+/*
+ * Asset initialisation (Sec. 3.3, "Assets"): the octree of a new actor is a
+ * uniform leaf grid in its canonical frame (origin at the centre of its 3-D
+ * box, axes along the box's), whose cubic bound is the largest box dimension
+ * scaled by 1.2, with every corner density at one value (the paper's -10,
+ * empty space, for every size and category).
+ *   box_dims[3]   host, the box's dimensions (> 0, any order of axes)
+ *   level         leaf level of the grid, 0..10 (8^level leaves)
+ *   capacity      leaves keys/dens can hold; DV_ERR_CAPACITY below 8^level,
+ *                 before any work is enqueued
+ *   keys, dens    device outputs [8^level] (layout of dv_octree: leaf (i, j, k)
+ *                 at index (k 2^level + j) 2^level + i) and [8^level][8]
+ *                 (16-byte aligned), every entry v_init
+ *   root_size     host output: 1.2 * max(box_dims); the grid's centre is the
+ *                 local origin (0, 0, 0)
+ *   n_leaves      host output: 8^level
+ * The SH coefficients are the caller's (zero gives a colour of 0.5 grey).
+ */
+dv_status dv_asset_init(dv_ctx* ctx, const float* box_dims, int32_t level, float v_init, int64_t capacity,
+                        uint64_t* keys, float* dens, double* root_size, int64_t* n_leaves, void* stream);
 
 /*
  * Forward render (Sec. 3.4, Algorithm 1).  For each pixel of each camera the
@@ -208,6 +262,12 @@ dv_status dv_render_backward_normals(dv_ctx* ctx, dv_state* state, const float* 
 
 /* Releases a saved state (stream-ordered on the stream of its render call). */
 void dv_state_free(dv_state* state);
+
+/* DV_ERR_TIMEOUT if a sort of the state's render ran out of its bounded wait
+ * (the state's results are then invalid), else DV_OK.  With wait = 0 it only
+ * reads what the render has published so far (DV_OK while unknown); with
+ * wait != 0 it first synchronises the state's stream. */
+dv_status dv_state_check(const dv_state* state, int32_t wait);
 
 /*
  * Compositing weights of a saved render, for feature fields (Sec. 4, "3D
@@ -357,6 +417,14 @@ dv_status dv_state_stats(const dv_state* state, int32_t view, int64_t* n_visible
 dv_status dv_state_work(const dv_state* state, int32_t view, uint64_t* tests, uint64_t* box_tests,
                         uint64_t* segments);
 
+/* FP32 FMA rate of device `device` (a measurement utility, no counterpart in
+ * the paper): launches a kernel of independent dependent-FMA chains on every SM
+ * `reps` times (after one warm-up launch), each thread running 8 x 16 x
+ * `iters` FMAs, and returns the FP32 operations counted (FMA = 2) and the
+ * milliseconds between CUDA events around the timed launches.  Synchronous.
+ * The compositing kernels' ALU roofline divides by flops / ms. */
+dv_status dv_measure_fp32_fma(int32_t device, int32_t iters, int32_t reps, double* flops, double* ms);
+
 /* Number of kernel launches this library has issued in this process (all
  * contexts); reset to zero when `reset` is non-zero (returns the old value). */
 long long dv_launch_count(int32_t reset);
@@ -374,6 +442,9 @@ long long dv_launch_count(int32_t reset);
  * All calls on a device share that array and clear the part they use first:
  * calls whose GPU work overlaps (unordered streams) race on it.  The first call
  * on a device looks up the array's address; make it before any stream capture.
+ * That address is kept per device ordinal for the life of the process: a
+ * caller that resets a device (cudaDeviceReset) must not use this entry point
+ * on that device afterwards.
  */
 dv_status dv_render_backward_static(dv_ctx* ctx, dv_state* state, const float* d_rgb, const float* d_depth,
                                     const float* d_alpha, float* const* d_dens, float* const* d_sh, void* stream);
@@ -403,6 +474,15 @@ dv_status dv_profile_read(dv_ctx* ctx, const char* const* names, int32_t n, doub
  * (dv_render_views); requests arriving meanwhile join the next batch a worker
  * forms, and the batches of different workers overlap on the GPU.  Results are
  * identical to rendering each request alone.
+ *
+ * Admission by device memory: each request is charged the device memory its
+ * render takes from the worker's pool (the model behind dv_workspace_need: the
+ * per-voxel projection arrays, per-pixel and per-tile state, and the records,
+ * pairs and sort scratch of its visible voxels), with the visible fraction of
+ * the scene's voxels and the pairs per tile taken from the batches already
+ * rendered (conservative values before the first), plus 25%.  A request joins
+ * a batch only while the charges of everything in flight stay within
+ * max_inflight_bytes (a request above the budget on its own runs alone).
  * ------------------------------------------------------------------------ */
 typedef struct dv_server dv_server;
 
@@ -410,8 +490,10 @@ typedef struct {
     int32_t max_views;           /* requests per batch, 1..DV_MAX_VIEWS (1 = one request per launch) */
     int32_t n_workers;           /* batches in flight at once, each on its own stream, 1..8 */
     int64_t max_batch_pixels;    /* pixels per batch (a larger single request still runs, alone) */
-    int64_t max_inflight_pixels; /* pixels rendering at once over all workers: the device-memory budget */
+    int64_t max_inflight_pixels; /* pixels rendering at once over all workers */
     dv_opts opts;
+    int64_t max_inflight_bytes;  /* device memory charged to the requests in flight, over all workers
+                                    (0: no byte limit) */
 } dv_serve_config;
 
 /* Starts a server on `device` over the octrees oct[n_oct] (device buffers
@@ -430,6 +512,14 @@ dv_status dv_serve_wait(dv_server* srv, int64_t ticket, double timeout_ms, doubl
 dv_status dv_serve_release(dv_server* srv, int64_t ticket);
 /* Batches run, requests rendered, largest batch so far. */
 dv_status dv_serve_stats(dv_server* srv, int64_t* batches, int64_t* views, int64_t* max_batch);
+/* Device memory charged to the requests in flight now, the largest such total
+ * since the server started or the last reset, and the charge of the last
+ * request admitted (bytes).  reset_peak != 0 restarts the peak from now. */
+dv_status dv_serve_memory(dv_server* srv, int32_t reset_peak, int64_t* inflight_bytes, int64_t* peak_inflight_bytes,
+                          int64_t* last_request_bytes);
+/* Holds (paused != 0) or resumes admission: queued requests wait while paused
+ * (dv_serve_destroy still finishes them). */
+dv_status dv_serve_pause(dv_server* srv, int32_t paused);
 const char* dv_serve_last_error(const dv_server* srv);
 /* Finishes every queued request, stops the workers and frees the server. */
 void dv_serve_destroy(dv_server* srv);

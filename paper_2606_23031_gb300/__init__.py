@@ -23,7 +23,8 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libdv.so")
-SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu", "dv_features.cu", "dv_init.cu"]
+SOURCES = ["dv_api.cu", "dv_scan_sort.cu", "dv_project.cu", "dv_composite.cu", "dv_serve.cu", "dv_sky.cu", "dv_features.cu",
+           "dv_init.cu", "dv_measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV_ERR_TIMEOUT, DV_ERR_NOMEM = range(7)
@@ -103,7 +104,7 @@ class dv_opts(C.Structure):
 
 class dv_serve_config(C.Structure):
     _fields_ = [("max_views", C.c_int32), ("n_workers", C.c_int32), ("max_batch_pixels", C.c_int64),
-                ("max_inflight_pixels", C.c_int64), ("opts", dv_opts)]
+                ("max_inflight_pixels", C.c_int64), ("opts", dv_opts), ("max_inflight_bytes", C.c_int64)]
 
 
 _lib = None
@@ -131,6 +132,23 @@ def load(path: str | None = None):
     lib.dv_profile_enable_stages.restype = C.c_int
     lib.dv_debug_flag_spin_timeout.argtypes = [C.c_void_p]
     lib.dv_debug_flag_spin_timeout.restype = C.c_int
+    lib.dv_debug_sort_timeout.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    lib.dv_debug_sort_timeout.restype = C.c_int
+    lib.dv_measure_fp32_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]
+    lib.dv_measure_fp32_fma.restype = C.c_int
+    lib.dv_reserve.argtypes = [C.c_void_p, C.c_int64]
+    lib.dv_reserve.restype = C.c_int
+    lib.dv_workspace_need.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+    lib.dv_workspace_need.restype = C.c_int
+    lib.dv_state_check.argtypes = [C.c_void_p, C.c_int32]
+    lib.dv_state_check.restype = C.c_int
+    lib.dv_asset_init.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.c_float, C.c_int64, C.c_void_p,
+                                  C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_void_p]
+    lib.dv_asset_init.restype = C.c_int
+    lib.dv_render_backward_static.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]
+    lib.dv_render_backward_static.restype = C.c_int
     lib.dv_version.restype = C.c_char_p
     lib.dv_render.argtypes = [C.c_void_p, C.POINTER(dv_octree), C.c_int32, C.POINTER(dv_pose), C.POINTER(dv_camera),
                               C.c_int32, C.POINTER(dv_opts), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -209,6 +227,11 @@ def load(path: str | None = None):
     lib.dv_serve_release.restype = C.c_int
     lib.dv_serve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.dv_serve_stats.restype = C.c_int
+    lib.dv_serve_memory.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)]
+    lib.dv_serve_memory.restype = C.c_int
+    lib.dv_serve_pause.argtypes = [C.c_void_p, C.c_int32]
+    lib.dv_serve_pause.restype = C.c_int
     lib.dv_serve_last_error.argtypes = [C.c_void_p]
     lib.dv_serve_last_error.restype = C.c_char_p
     lib.dv_serve_destroy.argtypes = [C.c_void_p]
@@ -251,6 +274,23 @@ class Context:
     def debug_flag_spin_timeout(self):
         """Test hook: marks this device's wait-error word, so the next render reports DV_ERR_TIMEOUT."""
         self.check(load().dv_debug_flag_spin_timeout(self.handle))
+
+    def debug_sort_timeout(self, spin_limit=1000):
+        """Test hook: one sort tile whose predecessor never publishes; returns (call flag, device flag)
+        as the kernel left them after its bounded waits ran out."""
+        a, b = C.c_uint32(), C.c_uint32()
+        self.check(load().dv_debug_sort_timeout(self.handle, int(spin_limit), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def reserve(self, nbytes: int):
+        """Limit each render call's workspace to ``nbytes`` and grow the pool to it (0: no limit)."""
+        self.check(load().dv_reserve(self.handle, int(nbytes)))
+
+    def workspace_need(self) -> int:
+        """Bytes the last render call needed (or the part known when it failed with DV_ERR_CAPACITY)."""
+        n = C.c_int64()
+        self.check(load().dv_workspace_need(self.handle, C.byref(n)))
+        return n.value
 
     def close(self):
         if self.handle:
@@ -389,6 +429,11 @@ class State:
         self.ctx.check(load().dv_state_stats(self.handle, view, C.byref(a), C.byref(b), C.byref(c)))
         return {"n_visible": a.value, "n_pairs": b.value, "n_tiles": c.value}
 
+    def check(self, wait=True):
+        """Raises DVError(DV_ERR_TIMEOUT) if a sort of this state's render ran out of its bounded wait;
+        ``wait`` first synchronises the render's stream (else an unfinished render passes)."""
+        self.ctx.check(load().dv_state_check(self.handle, 1 if wait else 0))
+
     def work(self, view=-1):
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
         self.ctx.check(load().dv_state_work(self.handle, view, C.byref(a), C.byref(b), C.byref(c)))
@@ -486,6 +531,8 @@ def dv_render_backward(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_d
     """Adds dL/d dens and dL/d sh into the given per-octree tensors (lists; None entries skipped).
     ``d_normal`` [P,3] is dL/dN of a render with normals."""
     lib = load()
+    if d_dens is None and d_sh is None:
+        raise DVError(DV_ERR_INVALID_ARG, "give d_dens or d_sh (per-octree lists; None entries skip an octree)")
     n = len(d_dens) if d_dens is not None else len(d_sh)
     pd = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_dens or [None] * n)])
     ps = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_sh or [None] * n)])
@@ -501,6 +548,48 @@ def dv_render_backward(state: State, d_rgb=None, d_depth=None, d_alpha=None, d_d
 
 def dv_state_free(state: State):
     state.free()
+
+
+def dv_measure_fp32_fma(device=0, iters=4096, reps=10):
+    """(FP32 operations, milliseconds) of the library's FMA-rate kernel on ``device`` (FMA = 2 operations)."""
+    f, ms = C.c_double(), C.c_double()
+    st = load().dv_measure_fp32_fma(int(device), int(iters), int(reps), C.byref(f), C.byref(ms))
+    if st != DV_OK:
+        raise DVError(st, "dv_measure_fp32_fma failed")
+    return f.value, ms.value
+
+
+# ---------------------------------------------------------------------------
+# cameras split across ranks (the one exchange of a multi-GPU forward + backward)
+# ---------------------------------------------------------------------------
+
+def camera_shard(cams, rank: int, world: int):
+    """The cameras rank ``rank`` of ``world`` renders: every world-th camera from ``rank`` (the octrees
+    are replicated on every rank, so cameras are independent units of the forward)."""
+    return list(cams)[rank::world]
+
+
+def allreduce_gradients(tensors, group=None):
+    """Sums per-octree gradient tensors (d_dens, d_sh, ...) over the ranks of ``group`` in place, as one
+    collective over a flat buffer: the exchange a forward + backward over cameras split across ranks
+    needs, each rank having added the gradients of its own cameras.  CUDA tensors are reduced on the
+    device with NCCL; with a CPU backend (gloo) they travel through host memory."""
+    import torch
+    import torch.distributed as dist
+    ts = [t for t in tensors if t is not None and t.numel()]
+    if not ts or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return
+    flat = torch.cat([t.reshape(-1) for t in ts])
+    on_host = dist.get_backend(group) == "gloo" and flat.is_cuda
+    buf = flat.cpu() if on_host else flat
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    if on_host:
+        flat.copy_(buf)
+    off = 0
+    for t in ts:
+        n = t.numel()
+        t.copy_(flat[off:off + n].view_as(t))
+        off += n
 
 
 def dv_launch_count(reset: bool = False) -> int:
@@ -711,6 +800,26 @@ def dv_visibility_prune(keys, max_level, center, root_size, cams, z_min, *, ctx:
     return out[:n_out.value]
 
 
+def dv_asset_init(box_dims, level, v_init=-10.0, *, ctx: Context | None = None, stream=None, device=None):
+    """Initial octree of an actor (Sec. 3.3, assets): a uniform grid of 8^level leaves in the actor's
+    canonical frame whose cubic bound is 1.2 x the largest box dimension, every corner density at
+    ``v_init``.  Returns (keys int64 tensor of the uint64 key bits [8^level], dens [8^level, 8],
+    root_size); the grid's centre is the local origin."""
+    import torch
+    lib = load()
+    ctx = ctx or default_context()
+    n = 1 << (3 * int(level)) if 0 <= int(level) <= 10 else 0
+    dev = torch.device("cuda", ctx.device if device is None else device)
+    keys = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    dens = torch.empty((max(n, 1), 8), dtype=torch.float32, device=dev)
+    dims = (C.c_float * 3)(*[float(x) for x in box_dims])
+    root = C.c_double()
+    n_out = C.c_int64()
+    ctx.check(lib.dv_asset_init(ctx.handle, dims, int(level), float(v_init), n, C.c_void_p(keys.data_ptr()),
+                                C.c_void_p(dens.data_ptr()), C.byref(root), C.byref(n_out), _stream_ptr(stream)))
+    return keys[:n_out.value], dens[:n_out.value], root.value
+
+
 def dv_corner_gather(index, corner, *, ctx: Context | None = None, stream=None):
     import torch
     lib = load()
@@ -765,13 +874,12 @@ def dv_render_backward_static(state: State, d_rgb=None, d_depth=None, d_alpha=No
     """Allocation-free variant of :func:`dv_render_backward` for callers that may not allocate device
     memory while the backward runs (graph capture without allocation nodes, real-time loops, a device
     whose memory belongs to another allocator).  Its scratch is a static device array for at most
-    ``STATIC_MAX_VISIBLE`` visible voxels per camera; calls that overlap on the GPU race on it, and the
-    first call on a device should precede any stream capture."""
+    ``STATIC_MAX_VISIBLE`` visible voxels per render call, summed over its views; calls that overlap on
+    the GPU race on it, and the first call on a device should precede any stream capture."""
     lib = load()
     fn = lib.dv_render_backward_static
-    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p),
-                   C.POINTER(C.c_void_p), C.c_void_p]
-    fn.restype = C.c_int
+    if d_dens is None and d_sh is None:
+        raise DVError(DV_ERR_INVALID_ARG, "give d_dens or d_sh (per-octree lists; None entries skip an octree)")
     n = len(d_dens) if d_dens is not None else len(d_sh)
     pd = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_dens or [None] * n)])
     ps = (C.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in (d_sh or [None] * n)])
@@ -787,7 +895,7 @@ class Server:
     ticket; ``wait`` blocks at most ``timeout_ms``; results are written into the given tensors."""
 
     def __init__(self, octrees, max_views=16, n_workers=2, max_batch_pixels=8 * 1920 * 1080,
-                 max_inflight_pixels=16 * 1920 * 1080, opts=None, device=None):
+                 max_inflight_pixels=16 * 1920 * 1080, opts=None, device=None, max_inflight_bytes=0):
         import torch
         lib = load()
         self.octrees = octrees  # keep the device buffers alive
@@ -797,6 +905,7 @@ class Server:
         cfg.max_views, cfg.n_workers = int(max_views), int(n_workers)
         cfg.max_batch_pixels, cfg.max_inflight_pixels = int(max_batch_pixels), int(max_inflight_pixels)
         cfg.opts = opts or make_opts()
+        cfg.max_inflight_bytes = int(max_inflight_bytes)
         h = C.c_void_p()
         dev = torch.cuda.current_device() if device is None else device
         st = lib.dv_serve_create(C.byref(h), int(dev), arr, self.n_oct, C.byref(cfg))
@@ -838,6 +947,18 @@ class Server:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(load().dv_serve_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)))
         return {"batches": a.value, "requests": b.value, "max_batch": c.value}
+
+    def memory(self, reset_peak=False):
+        """Device memory charged to the requests in flight, its peak since the start or the last reset, and
+        the last request's charge; ``reset_peak`` restarts the peak from now."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(load().dv_serve_memory(self.handle, 1 if reset_peak else 0, C.byref(a), C.byref(b),
+                                           C.byref(c)))
+        return {"inflight_bytes": a.value, "peak_inflight_bytes": b.value, "last_request_bytes": c.value}
+
+    def pause(self, paused=True):
+        """Hold (or resume) admission of queued requests."""
+        self._check(load().dv_serve_pause(self.handle, 1 if paused else 0))
 
     def close(self):
         if self.handle:

@@ -38,10 +38,72 @@ namespace dv {
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace dv
 
+// Mapped (zero-copy) host words, one per live render state: the render's sorts publish their own
+// wait flag into it, so a timeout is reported to the call that had it.
+struct StatusSlots {
+    static constexpr int kBlock = 512;
+    std::mutex mu;
+    std::vector<uint64_t*> host, dev;  // blocks of kBlock words: host pointers and their device aliases
+    std::vector<int> free_list;        // block * kBlock + word
+    std::vector<int> deferred;         // given back before their render's last kernel wrote them
+    uint64_t* word(int id) { return host[id / kBlock] + id % kBlock; }
+    bool take(uint64_t** h, uint64_t** d, int* id) {
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = 0; i < deferred.size();) {
+            if (*(volatile uint64_t*)word(deferred[i]) != ~0ull) {
+                free_list.push_back(deferred[i]);
+                deferred[i] = deferred.back();
+                deferred.pop_back();
+            } else {
+                ++i;
+            }
+        }
+        if (free_list.empty()) {
+            uint64_t* hb = nullptr;
+            uint64_t* db = nullptr;
+            if (cudaHostAlloc(&hb, kBlock * sizeof(uint64_t), cudaHostAllocMapped) != cudaSuccess) return false;
+            if (cudaHostGetDevicePointer((void**)&db, hb, 0) != cudaSuccess) {
+                cudaFreeHost(hb);
+                return false;
+            }
+            const int b = (int)host.size();
+            host.push_back(hb);
+            dev.push_back(db);
+            for (int i = kBlock - 1; i >= 0; --i) free_list.push_back(b * kBlock + i);
+        }
+        const int s = free_list.back();
+        free_list.pop_back();
+        *h = host[s / kBlock] + s % kBlock;
+        *d = dev[s / kBlock] + s % kBlock;
+        *id = s;
+        return true;
+    }
+    // a slot still waiting for its render's write is reused only once that write has landed
+    void give(int id) {
+        if (id < 0) return;
+        std::lock_guard<std::mutex> lk(mu);
+        if (*(volatile uint64_t*)word(id) == ~0ull)
+            deferred.push_back(id);
+        else
+            free_list.push_back(id);
+    }
+    ~StatusSlots() {
+        for (uint64_t* h : host) cudaFreeHost(h);
+    }
+};
+
+// written into a state's status slot before its render is enqueued; the render's last kernel
+// overwrites it with the call's sort flag (0 or 1)
+constexpr uint64_t kStatusPending = ~0ull;
+
 struct dv_ctx {
     int device = 0;
     cudaMemPool_t pool = nullptr;
     std::string err;
+    StatusSlots slots;
+    dv::Fork fork;          // extra streams and events of the three-launch compositing passes
+    int64_t budget = 0;     // bytes one call may take from the pool (0: no limit), set by dv_reserve
+    int64_t last_need = 0;  // bytes the last render call needed (or the part known when it failed)
     uint64_t* h_scalars = nullptr;  // pinned, mapped: [0] n_vis, [1] n_pairs, [2] flags
     uint64_t* h_scalars_dev = nullptr;  // the same host words as the device sees them
     uint64_t* d_scalars = nullptr;  // device counters
@@ -75,6 +137,11 @@ struct BatchState {
     uint32_t* n_seg = nullptr;
     float* t_final = nullptr;
     unsigned long long* work = nullptr;  // [tests, box tests, segments] of the forward
+    uint64_t* d_sort_err = nullptr;      // device word: a sort of this call ran out of its bounded wait
+    uint64_t* h_status = nullptr;        // mapped host slot the call publishes d_sort_err into
+    uint64_t* h_status_dev = nullptr;
+    int status_id = -1;
+    bool published = false;  // the kernel that writes the status slot has been enqueued
 };
 
 }  // namespace
@@ -398,6 +465,54 @@ T* pool_alloc(dv_ctx* ctx, cudaStream_t s, size_t count, std::vector<void*>& own
     return (T*)p;
 }
 
+// ---------------------------------------------------------------------------
+// Device memory one render call takes from the context's pool (an upper bound of its peak: the
+// saved state plus the scratch released at the end of the call).  Every allocation is counted
+// rounded up to 512 bytes.
+// ---------------------------------------------------------------------------
+
+int64_t rounded(int64_t bytes) { return ((std::max<int64_t>(bytes, 16) + 511) / 512) * 512; }
+
+// one-sweep radix sort scratch of n keys on n_bits (at most one tile per 256 keys)
+int64_t sort_need(int64_t n, int n_bits) {
+    const int64_t passes = (n_bits + 7) / 8;
+    const int64_t tiles = (n + 255) / 256;
+    return rounded(4 * (passes * (256 + 1 + tiles * 256) + 1));
+}
+
+// the part known before any work is enqueued: per-view constants, per-pixel and per-tile state,
+// the projection's per-(view, voxel) arrays and their scan
+int64_t need_before(int64_t n_view, int64_t n_oct, int64_t NT, int64_t tiles, int64_t pix) {
+    int64_t b = rounded((int64_t)sizeof(ViewParams) * n_view) + rounded((int64_t)sizeof(OctParams) * n_view * n_oct);
+    b += 2 * rounded(4 * pix) + rounded(8 * tiles) + rounded(4 * (n_view * n_oct + 1)) + rounded(4 * tiles);
+    b += rounded(32) + rounded(8);                                          // work counters, sort flag
+    b += 2 * rounded(4 * NT) + 2 * rounded(8 * NT) + rounded(4 * NT);       // cnt, vis, rect, skey, pos
+    b += rounded(4 * ((NT + 2047) / 2048));                                 // scan block sums
+    return b;
+}
+
+// the part that follows from the sizes the projection reports: visible voxels and pairs
+int64_t need_after(int64_t n_vis, int64_t P, int key_bits, int tile_bits, bool normals) {
+    int64_t b = 2 * rounded(8 * n_vis) + 2 * rounded(4 * n_vis) + sort_need(n_vis, key_bits);  // depth sort
+    b += rounded(64 * n_vis) + (normals ? rounded(16 * n_vis) : 0);                         // records
+    b += rounded(4 * n_vis) + 2 * rounded(8 * n_vis) + rounded(8 * ((n_vis + 2047) / 2048));  // cnt, rect, offsets
+    b += 4 * rounded(4 * P) + sort_need(P, tile_bits) + rounded(P) + rounded(768);          // pairs, mask, order
+    return b;
+}
+
+}  // namespace
+
+namespace dv {
+int64_t render_need_before(int64_t n_view, int64_t n_oct, int64_t NT, int64_t tiles, int64_t pix) {
+    return need_before(n_view, n_oct, NT, tiles, pix);
+}
+int64_t render_need_after(int64_t n_vis, int64_t P, int key_bits, int tile_bits, bool normals) {
+    return need_after(n_vis, P, key_bits, tile_bits, normals);
+}
+}  // namespace dv
+
+namespace {
+
 // The forward of one render call over all its views.  State buffers go to `st`
 // (freed by the caller when no state is wanted).
 dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_pose* const* view_poses,
@@ -445,7 +560,38 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     for (int v = n_view; v <= DV_MAX_VIEWS; ++v) bp.tile_base[v] = (int32_t)tiles;
     if (tiles >= ((int64_t)1 << 31)) return fail(ctx, DV_ERR_CAPACITY, "too many tiles in one call");
     bp.n_tiles = (int32_t)tiles;
+    // tiles by the number of actor clip boxes that cover them (none, 1 to 4, 5 or more): the three
+    // groups of the compositing launches; the tile-order kernel classifies each tile by the same rectangles
+    {
+        int64_t n_large = 0, n_small = 0;
+        std::vector<uint8_t> cov;
+        for (int v = 0; v < n_view; ++v) {
+            const ViewParams& vp = B.h_views[v];
+            cov.assign((size_t)vp.tiles_x * vp.tiles_y, 0);
+            for (int o = 1; o < n_oct; ++o) {
+                const OctParams& Q = h_octs[(size_t)v * n_oct + o];
+                if (Q.role != DV_ROLE_ACTOR) continue;
+                for (int ty = std::max<int>(Q.rect[1], 0); ty <= std::min<int>(Q.rect[3], vp.tiles_y - 1); ++ty)
+                    for (int tx = std::max<int>(Q.rect[0], 0); tx <= std::min<int>(Q.rect[2], vp.tiles_x - 1); ++tx) {
+                        uint8_t& c = cov[(size_t)ty * vp.tiles_x + tx];
+                        if (c < 5) ++c;
+                    }
+            }
+            for (uint8_t c : cov) {
+                n_large += c >= 5;
+                n_small += c > 0 && c < 5;
+            }
+        }
+        bp.n_tiles_large = (int32_t)n_large;
+        bp.n_tiles_small = (int32_t)n_small;
+    }
     B.n_pix = pix;
+    const int64_t need0 = need_before(n_view, n_oct, bp.n_vox * n_view, tiles, pix);
+    ctx->last_need = need0;
+    if (ctx->budget > 0 && need0 > ctx->budget)
+        return fail(ctx, DV_ERR_CAPACITY, "the call needs at least " + std::to_string(need0) +
+                                              " bytes of workspace, above the reserved " +
+                                              std::to_string(ctx->budget) + " (dv_reserve)");
     cudaError_t e = cudaSuccess;
     std::vector<void*>& own = st->owned;
     B.d_views = pool_alloc<ViewParams>(ctx, s, (size_t)n_view, own, e);
@@ -464,8 +610,14 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     B.vis_start = pool_alloc<uint32_t>(ctx, s, (size_t)n_view * n_oct + 1, own, e);
     B.tile_order = pool_alloc<uint32_t>(ctx, s, (size_t)tiles, own, e);
     B.work = pool_alloc<unsigned long long>(ctx, s, 4, own, e);
+    B.d_sort_err = pool_alloc<uint64_t>(ctx, s, 1, own, e);
     if (e == cudaSuccess) e = cudaMemsetAsync(B.work, 0, 4 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.d_sort_err, 0, sizeof(uint64_t), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate state");
+    if (!ctx->slots.take(&B.h_status, &B.h_status_dev, &B.status_id))
+        return fail(ctx, DV_ERR_NOMEM, "mapped host memory for the call's status word");
+    *(volatile uint64_t*)B.h_status = kStatusPending;
+    uint32_t* sort_err = reinterpret_cast<uint32_t*>(B.d_sort_err);
 
     Arena ar;
     ar.pool = ctx->pool;
@@ -518,6 +670,19 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         ar.release();
         return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 (tile, voxel) pairs in one call");
     }
+    {
+        const int64_t need = need0 + need_after(n_vis, P, bp.view_shift + bits_for(n_view), bits_for(tiles),
+                                                bp.normals != 0);
+        ctx->last_need = need;
+        if (ctx->budget > 0 && need > ctx->budget) {
+            ar.release();
+            return fail(ctx, DV_ERR_CAPACITY, "the call needs " + std::to_string(need) +
+                                                  " bytes of workspace (" + std::to_string(n_vis) +
+                                                  " visible voxels, " + std::to_string(P) +
+                                                  " pairs), above the reserved " + std::to_string(ctx->budget) +
+                                                  " (dv_reserve); no output was written");
+        }
+    }
     B.n_vis = n_vis;
     B.n_pairs = P;
     // depth-order sort of the visible (view, voxel)s
@@ -539,7 +704,8 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     uint32_t* gg = g0;
     {
         Prof p(ctx, KP_SORT_VOX, s);
-        if (e == cudaSuccess) e = radix_sort_u64(kk, gg, k1, g1, n_vis, bp.view_shift + bits_for(n_view), ar, s);
+        if (e == cudaSuccess)
+            e = radix_sort_u64(kk, gg, k1, g1, n_vis, bp.view_shift + bits_for(n_view), ar, s, sort_err);
     }
     if (e == cudaSuccess && gg != B.sorted_g)
         e = cudaMemcpyAsync(B.sorted_g, gg, sizeof(uint32_t) * (size_t)n_vis, cudaMemcpyDeviceToDevice, s);
@@ -579,8 +745,12 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     uint32_t* pv = pv0;
     {
         Prof p(ctx, KP_SORT_PAIRS, s);
-        if (e == cudaSuccess) e = radix_sort_u32(pk, pv, pk1, pv1, P, bits_for(tiles), ar, s);
+        if (e == cudaSuccess) e = radix_sort_u32(pk, pv, pk1, pv1, P, bits_for(tiles), ar, s, sort_err);
     }
+    // the call's own sort flag goes to its status slot (read by dv_state_check, the backward and the
+    // serving loop), so a timeout is reported to the call that had it
+    if (e == cudaSuccess) e = launch_publish(B.d_sort_err, B.h_status_dev, 1, nullptr, -1, s);
+    if (e == cudaSuccess) B.published = true;
     if (e == cudaSuccess && pv != pv0)
         e = cudaMemcpyAsync(pv0, pv, sizeof(uint32_t) * (size_t)P, cudaMemcpyDeviceToDevice, s);
     B.pval = pv0;
@@ -589,14 +759,14 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         Prof p(ctx, KP_RANGES, s);
         if (e == cudaSuccess)
             e = launch_pair_mask_ranges(bp, pk, B.pval, rect_sorted, P, B.pmask, B.range, (int)tiles, s);
-        uint32_t* tscr = ar.alloc<uint32_t>(64);
-        if (e == cudaSuccess) e = tscr ? launch_tile_order(B.range, (int)tiles, tscr, B.tile_order, s) : ar.err;
+        uint32_t* tscr = ar.alloc<uint32_t>(192);
+        if (e == cudaSuccess) e = tscr ? launch_tile_order(bp, B.range, (int)tiles, tscr, B.tile_order, s) : ar.err;
     }
     {
         Prof p(ctx, KP_FWD, s);
         if (e == cudaSuccess)
             e = launch_composite_fwd(bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, B.n_seg,
-                                     B.t_final, B.work, s);
+                                     B.t_final, B.work, &ctx->fork, s);
     }
     ar.release();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render");
@@ -616,7 +786,7 @@ dv_status backward_batch(dv_ctx* ctx, dv_state* st, const float* d_rgb, const fl
         Prof p(ctx, KP_BWD, s);
         if (e == cudaSuccess)
             e = dv::launch_composite_bwd(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order, B.t_final,
-                                         d_rgb, d_depth, d_alpha, d_normal, grad, s);
+                                         d_rgb, d_depth, d_alpha, d_normal, grad, &ctx->fork, s);
     }
     {
         Prof p(ctx, KP_SHBWD, s);
@@ -631,8 +801,17 @@ void free_state(dv_state* st) {
     if (st->ctx) {
         DeviceGuard g(st->ctx->device);
         for (void* p : st->owned) cudaFreeAsync(p, st->stream);
+        if (st->b.status_id >= 0 && !st->b.published) *(volatile uint64_t*)st->b.h_status = 0;  // nothing will write it
+        st->ctx->slots.give(st->b.status_id);
     }
     delete st;
+}
+
+// The call's sort flag as published into its status slot: 1 timed out, 0 fine, kStatusPending
+// not yet known (the render has not finished).
+uint64_t state_sort_flag(const dv_state* st) {
+    if (!st || st->b.status_id < 0) return 0;
+    return *(volatile const uint64_t*)st->b.h_status;
 }
 
 }  // namespace
@@ -640,6 +819,15 @@ void free_state(dv_state* st) {
 extern "C" {
 
 const char* dv_version(void) { return "dv 0.1 (sm_103a)"; }
+
+// The extra streams of the three-launch compositing passes get the device's highest priority: their
+// launches hold the tiles that actor boxes cover, the heaviest of a frame, so their CTAs are
+// dispatched ahead of the plain launch's and start at once instead of forming a tail behind them.
+static int side_priority() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+    return greatest;
+}
 
 dv_status dv_create(dv_ctx** out, int32_t device) {
     if (!out) return DV_ERR_INVALID_ARG;
@@ -671,7 +859,17 @@ dv_status dv_create(dv_ctx** out, int32_t device) {
         return DV_ERR_NOMEM;
     }
     ctx->d_spin_err = dv::spin_error_word();
-    if (!ctx->d_spin_err || cudaEventCreateWithFlags(&ctx->ev_sizes, cudaEventDisableTiming) != cudaSuccess) {
+    if (!ctx->d_spin_err || cudaEventCreateWithFlags(&ctx->ev_sizes, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->fork.side, cudaStreamNonBlocking, side_priority()) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->fork.side2, cudaStreamNonBlocking, side_priority()) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork.ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork.ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+        if (ctx->ev_sizes) cudaEventDestroy(ctx->ev_sizes);
+        if (ctx->fork.ev_fork) cudaEventDestroy(ctx->fork.ev_fork);
+        if (ctx->fork.ev_join) cudaEventDestroy(ctx->fork.ev_join);
+        if (ctx->fork.side) cudaStreamDestroy(ctx->fork.side);
+        if (ctx->fork.side2) cudaStreamDestroy(ctx->fork.side2);
         cudaFree(ctx->d_scalars);
         cudaFreeHost(ctx->h_scalars);
         cudaMemPoolDestroy(ctx->pool);
@@ -699,6 +897,11 @@ void dv_destroy(dv_ctx* ctx) {
     }
     for (auto e : ctx->spare) cudaEventDestroy(e);
     cudaEventDestroy(ctx->ev_sizes);
+    if (ctx->fork.ev_fork) cudaEventDestroy(ctx->fork.ev_fork);
+    if (ctx->fork.ev_join) cudaEventDestroy(ctx->fork.ev_join);
+    if (ctx->fork.ev_join2) cudaEventDestroy(ctx->fork.ev_join2);
+    if (ctx->fork.side) cudaStreamDestroy(ctx->fork.side);
+    if (ctx->fork.side2) cudaStreamDestroy(ctx->fork.side2);
     cudaFree(ctx->d_scalars);
     cudaFreeHost(ctx->h_scalars);
     cudaMemPoolDestroy(ctx->pool);
@@ -805,6 +1008,9 @@ static dv_status backward_common(dv_ctx* ctx, dv_state* st, const float* d_rgb, 
     if (st->ctx != ctx) return fail(ctx, DV_ERR_INVALID_ARG, "state belongs to another context");
     if (d_normal && !st->b.bp.normals)
         return fail(ctx, DV_ERR_INVALID_ARG, "a normal gradient for a render without normals");
+    if (state_sort_flag(st) == 1)
+        return fail(ctx, DV_ERR_TIMEOUT, "the render of this state had a sort whose bounded wait ran out; its "
+                                         "results are invalid");
     if (st->b.n_vis == 0) return DV_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -885,7 +1091,7 @@ dv_status dv_state_weights(dv_ctx* ctx, dv_state* st, const int64_t* offsets, ui
     if (!offsets || !voxel || !weight) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
     cudaError_t e = dv::launch_composite_export(B.bp, B.rec, B.pval, B.pmask, B.range, B.vis_start, B.tile_order,
-                                                offsets, voxel, weight, (cudaStream_t)stream);
+                                                offsets, voxel, weight, &ctx->fork, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "weights export");
     return DV_OK;
 }
@@ -914,10 +1120,12 @@ dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, c
     dv::Arena ar;
     ar.pool = ctx->pool;
     ar.stream = s;
-    cudaError_t e = dv::feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, ar, s);
+    bool timeout = false;
+    cudaError_t e = dv::feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, ar, s, &timeout);
     ar.release();
     if (e == cudaErrorInvalidValue) return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 - 1 slots or pixels");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "feature fusion");
+    if (timeout) return fail(ctx, DV_ERR_TIMEOUT, "the fusion's slot sort ran out of its bounded wait; sums invalid");
     return DV_OK;
 }
 
@@ -950,10 +1158,12 @@ dv_status dv_shared_corners(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32_
     ar.stream = s;
     dv_status st = init_begin(ctx, keys, n, max_level, ar, s);
     cudaError_t e = cudaSuccess;
-    if (st == DV_OK) e = dv::shared_corners(keys, n, max_level, grid, index, n_corners, ar, s);
+    bool timeout = false;
+    if (st == DV_OK) e = dv::shared_corners(keys, n, max_level, grid, index, n_corners, ar, s, &timeout);
     ar.release();
     if (st != DV_OK) return st;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "shared corners");
+    if (timeout) return fail(ctx, DV_ERR_TIMEOUT, "the corner sort ran out of its bounded wait; output invalid");
     return DV_OK;
 }
 
@@ -972,10 +1182,12 @@ dv_status dv_soft_prior(dv_ctx* ctx, const uint64_t* grid, int64_t n_corners, co
     dv::Arena ar;
     ar.pool = ctx->pool;
     ar.stream = s;
+    bool timeout = false;
     cudaError_t e = dv::soft_prior(grid, n_corners, center, root_size, max_level, cloud, n_points, s_min, v_close, v_far,
-                                   dens, ar, s);
+                                   dens, ar, s, &timeout);
     ar.release();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "soft prior");
+    if (timeout) return fail(ctx, DV_ERR_TIMEOUT, "the point-cell sort ran out of its bounded wait; output invalid");
     return DV_OK;
 }
 
@@ -996,11 +1208,17 @@ dv_status dv_subdivide_round(dv_ctx* ctx, const uint64_t* keys, int64_t n, int32
     ar.stream = s;
     dv_status st = init_begin(ctx, keys, n, max_level, ar, s);
     cudaError_t e = cudaSuccess;
+    bool timeout = false;
     if (st == DV_OK)
-        e = dv::subdivide_round(keys, n, center, root_size, max_level, cloud, n_points, threshold, out, n_out, ar, s);
+        e = dv::subdivide_round(keys, n, center, root_size, max_level, cloud, n_points, threshold, out, n_out, ar, s,
+                                &timeout);
     ar.release();
     if (st != DV_OK) return st;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "subdivision");
+    if (timeout) {
+        *n_out = 0;
+        return fail(ctx, DV_ERR_TIMEOUT, "the leaf-key sort ran out of its bounded wait; nothing was written");
+    }
     return DV_OK;
 }
 
@@ -1190,6 +1408,86 @@ long long dv_launch_count(int32_t reset) {
     return reset ? g_launches.exchange(0) : g_launches.load();
 }
 
+dv_status dv_state_check(const dv_state* st, int32_t wait) {
+    if (!st) return DV_ERR_INVALID_ARG;
+    uint64_t f = state_sort_flag(st);
+    if (f == kStatusPending && wait) {
+        DeviceGuard g(st->ctx->device);
+        if (cudaStreamSynchronize(st->stream) != cudaSuccess) return DV_ERR_CUDA;
+        f = state_sort_flag(st);
+    }
+    return f == 1 ? DV_ERR_TIMEOUT : DV_OK;
+}
+
+dv_status dv_debug_sort_timeout(dv_ctx* ctx, int32_t spin_limit, uint32_t* call_flag, uint32_t* device_flag) {
+    if (!ctx || !call_flag || !device_flag || spin_limit < 1 || spin_limit > (1 << 20)) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = dv::debug_sort_timeout(spin_limit, call_flag, device_flag, s);
+    if (s) cudaStreamDestroy(s);
+    return e == cudaSuccess ? DV_OK : cuda_fail(ctx, e, "debug sort timeout");
+}
+
+dv_status dv_reserve(dv_ctx* ctx, int64_t bytes) {
+    if (!ctx || bytes < 0) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    ctx->budget = bytes;
+    if (bytes == 0) return DV_OK;
+    // grow the pool to the reservation now (it keeps freed memory: release threshold unlimited), so
+    // the calls within it take their workspace without new device allocations
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = nullptr;
+    void* p = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p, (size_t)bytes, ctx->pool, s);
+    if (e == cudaSuccess) e = cudaFreeAsync(p, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (s) cudaStreamDestroy(s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        ctx->budget = 0;
+        return fail(ctx, DV_ERR_NOMEM, "the device cannot hold a reservation of " + std::to_string(bytes) + " bytes");
+    }
+    return e == cudaSuccess ? DV_OK : cuda_fail(ctx, e, "reserve");
+}
+
+dv_status dv_workspace_need(const dv_ctx* ctx, int64_t* bytes) {
+    if (!ctx || !bytes) return DV_ERR_INVALID_ARG;
+    *bytes = ctx->last_need;
+    return DV_OK;
+}
+
+dv_status dv_asset_init(dv_ctx* ctx, const float* box_dims, int32_t level, float v_init, int64_t capacity,
+                        uint64_t* keys, float* dens, double* root_size, int64_t* n_leaves, void* stream) {
+    if (!ctx) return DV_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!box_dims || !root_size || !n_leaves) return fail(ctx, DV_ERR_INVALID_ARG, "NULL argument");
+    *n_leaves = 0;
+    *root_size = 0.0;
+    double m = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if (!(box_dims[k] > 0.0f) || !std::isfinite(box_dims[k]))
+            return fail(ctx, DV_ERR_INVALID_ARG, "box dimensions must be finite and > 0");
+        m = std::max(m, (double)box_dims[k]);
+    }
+    if (level < 0 || level > 10) return fail(ctx, DV_ERR_INVALID_ARG, "level out of range (0..10)");
+    if (!std::isfinite(v_init)) return fail(ctx, DV_ERR_INVALID_ARG, "non-finite initial density");
+    const int64_t n = (int64_t)1 << (3 * level);
+    if (capacity < n)
+        return fail(ctx, DV_ERR_CAPACITY, "the grid has " + std::to_string(n) + " leaves, above the capacity of " +
+                                              std::to_string(capacity));
+    if (!keys || !dens) return fail(ctx, DV_ERR_INVALID_ARG, "NULL output buffer");
+    if ((uintptr_t)dens & 15) return fail(ctx, DV_ERR_INVALID_ARG, "dens must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = dv::asset_grid(level, v_init, keys, dens, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "asset grid");
+    *root_size = 1.2 * m;
+    *n_leaves = n;
+    return DV_OK;
+}
+
 dv_status dv_profile_enable(dv_ctx* ctx, int32_t on) {
     if (!ctx) return DV_ERR_INVALID_ARG;
     ctx->profiling = on != 0;
@@ -1242,7 +1540,7 @@ dv_status validate_request(const dv_camera& cam, const dv_pose* poses, int n_oct
 // Render of views whose outputs live in separate buffers (used by the serving loop).
 dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
                             const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,
-                            void* stream) {
+                            dv_state** saved, void* stream) {
     std::vector<const dv_pose*> vp((size_t)std::max(n_view, 1), nullptr);
     std::vector<dv_camera> cams((size_t)std::max(n_view, 1));
     for (int v = 0; v < n_view; ++v) {
@@ -1250,7 +1548,7 @@ dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const 
         cams[v] = views[v].camera;
     }
     return render_common(ctx, oct, n_oct, vp.data(), cams.data(), n_view, opts, nullptr, nullptr, nullptr, rgbs, depths,
-                         alphas, nullptr, stream);
+                         alphas, saved, stream);
 }
 }  // namespace dv
 

@@ -36,8 +36,9 @@
 //    the prefix state at its entry; phase 3 then replays every reached actor
 //    interval with gradients from that state.  Gradients of records visited in
 //    lockstep are reduced across the warp before the atomics.
-//  * Tiles with more than NTA actors handle the extra actors with a per-lane
-//    walk of the actor's sub-list (correct, but divergent).
+//  * Tiles with more actors than lockstep slots (4, or 16 where 5 or more boxes
+//    cover the tile) handle the extra actors with a per-lane walk of the actor's
+//    sub-list (correct, but divergent).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,7 +57,10 @@ struct GradLayout {
     static constexpr int NV = NRM ? 14 : 11;      // values per record
     static constexpr int STRIDE = NRM ? 16 : 12;  // floats per record row
 };
-constexpr int NTA = 4;           // tile actors with lockstep partials
+// lockstep actor slots of the two actor variants: tiles that 1 to 4 actor boxes cover, and tiles
+// that 5 or more cover (beyond 8, the remaining actors take the per-thread walk)
+constexpr int NTA_SMALL = 4;
+constexpr int NTA_LARGE = 8;
 
 struct PixBase {
     float C0, C1, C2, D, T;
@@ -98,16 +102,28 @@ struct ActInt {
     float a, b;
 };
 
-// exponential-linear activation: x above 1.1, 1.1 exp(x/1.1 - 1) below (C1 at 1.1); the
-// exponential goes to the SFU (__expf), whose relative error here is ~1e-6
+// 2^x on the SFU (ex2.approx.ftz: relative error about 2^-22)
+__device__ __forceinline__ float ex2_sfu(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// exponential-linear activation: x above 1.1, 1.1 exp(x/1.1 - 1) below (C1 at 1.1).  The exponential
+// branch is one SFU power of two, 1.1 exp(x/1.1 - 1) = 2^(x / (1.1 ln 2) + (ln 1.1 - 1) / ln 2), and
+// its slope exp(x/1.1 - 1) is the same power divided by 1.1.
+__device__ __forceinline__ float explin_low(float x) {
+    return ex2_sfu(fmaf(x, 1.3115409462626941f, -1.3051915171390283f));
+}
+
 __device__ __forceinline__ float act_fn(float x, int act) {
     if (act == DV_ACT_IDENTITY) return x;
-    return x > 1.1f ? x : 1.1f * __expf(fmaf(x, 0.90909090909090909f, -1.0f));
+    return x > 1.1f ? x : explin_low(x);
 }
 
 __device__ __forceinline__ float act_grad(float x, int act) {
     if (act == DV_ACT_IDENTITY) return 1.0f;
-    return x > 1.1f ? 1.0f : __expf(fmaf(x, 0.90909090909090909f, -1.0f));
+    return x > 1.1f ? 1.0f : explin_low(x) * 0.90909090909090909f;
 }
 
 __device__ __forceinline__ void rotate(const float* A, const float* x, float* y) {
@@ -180,18 +196,20 @@ __device__ __forceinline__ bool slab_box(const float* o, const float* inv, const
     return a < b;
 }
 
-__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-// optical depth of the segment [t0, t1] through one voxel; optionally d tau / d dens[c]
-// KS > 0: K known at compile time (KS); KS == 0: K from the launch.
+// optical depth of the segment [t0, t1] through one voxel (da, db: the record's density polynomial);
+// optionally d tau / d dens[c] for the raw corner densities
+// KS > 0: K known at compile time (KS); KS == 0: K from the launch.  With GRAD and a single sample
+// (KS == 1), d tau / d dens[c] = s w_c(x, y, z) is left factored: sxyz receives (s, x, y, z), the
+// activation's slope times the step and the sample's voxel coordinates, and dtd is not written.
 template <bool GRAD, int KS>
 __device__ __forceinline__ float seg_tau(float4 da, float4 db, float is, const float* rel, const float* d, float t0,
-                                         float t1, int K_rt, float inv_k_rt, int act, float* dtd) {
+                                         float t1, int K_rt, float inv_k_rt, int act, float* dtd, float* sxyz) {
     const int K = KS > 0 ? KS : K_rt;
     const float inv_k = KS == 1 ? 1.0f : inv_k_rt;
     const float h = (t1 - t0) * inv_k;
     float tau = 0.0f;
-    if (GRAD) {
+    if (GRAD && KS != 1) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) dtd[c] = 0.0f;
     }
@@ -201,11 +219,18 @@ __device__ __forceinline__ float seg_tau(float4 da, float4 db, float is, const f
         const float x = __saturatef(fmaf(t, d[0], -rel[0]) * is);
         const float y = __saturatef(fmaf(t, d[1], -rel[1]) * is);
         const float z = __saturatef(fmaf(t, d[2], -rel[2]) * is);
-        const float e00 = lerpf(da.x, da.y, x), e10 = lerpf(da.z, da.w, x);
-        const float e01 = lerpf(db.x, db.y, x), e11 = lerpf(db.z, db.w, x);
-        const float rho = lerpf(lerpf(e00, e10, y), lerpf(e01, e11, y), z);
+        // the record holds the trilinear field as a polynomial (da = (c0, c1, c2, c4), db = (c3, c5, c6,
+        // c7)): rho = (c0 + c1 x) + y (c2 + c4 x) + z ((c3 + c5 x) + y (c6 + c7 x))
+        const float p0 = fmaf(da.y, x, da.x), p1 = fmaf(da.w, x, da.z);
+        const float p2 = fmaf(db.y, x, db.x), p3 = fmaf(db.w, x, db.z);
+        const float rho = fmaf(fmaf(p3, y, p2), z, fmaf(p1, y, p0));
         tau += act_fn(rho, act);
-        if (GRAD) {
+        if (GRAD && KS == 1) {
+            sxyz[0] = act_grad(rho, act) * h;
+            sxyz[1] = x;
+            sxyz[2] = y;
+            sxyz[3] = z;
+        } else if (GRAD) {
             const float s = act_grad(rho, act) * h;
             const float x0 = 1.0f - x, y0 = 1.0f - y, z0 = 1.0f - z;
             dtd[0] = fmaf(s, x0 * y0 * z0, dtd[0]);
@@ -255,8 +280,8 @@ template <bool GRAD, bool STOP, int KS, bool NRM, bool WEX = false>
 __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp, float4 da, float4 db,
                                             float4 col, float4 nv, const float* rel, const float* d, float t0,
                                             float t1, float* acc, uint32_t r = 0, ExportSink* ex = nullptr) {
-    float dtd[8];
-    const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd);
+    float dtd[8], sxyz[4];
+    const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd, sxyz);
     const float w = composite_step<NRM>(ps, tau, col, nv, t0, t1);
     if constexpr (WEX) {
         if (ex->n < ex->lim) {
@@ -281,8 +306,25 @@ __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, co
             acc[12] = fmaf(bw.gN1, w, acc[12]);
             acc[13] = fmaf(bw.gN2, w, acc[13]);
         }
+        if constexpr (KS == 1) {
+            // d L / d dens[c] = gt s w_c(x, y, z): the trilinear weights with gt s folded into the y-z products
+            const float a = gt * sxyz[0];
+            const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
+            const float x0 = 1.0f - x;
+            const float ay0 = a * (1.0f - y), ay1 = a * y;
+            const float c00 = ay0 * (1.0f - z), c10 = ay1 * (1.0f - z), c01 = ay0 * z, c11 = ay1 * z;
+            acc[0] = fmaf(x0, c00, acc[0]);
+            acc[1] = fmaf(x, c00, acc[1]);
+            acc[2] = fmaf(x0, c10, acc[2]);
+            acc[3] = fmaf(x, c10, acc[3]);
+            acc[4] = fmaf(x0, c01, acc[4]);
+            acc[5] = fmaf(x, c01, acc[5]);
+            acc[6] = fmaf(x0, c11, acc[6]);
+            acc[7] = fmaf(x, c11, acc[7]);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = fmaf(gt, dtd[c], acc[c]);
+            for (int c = 0; c < 8; ++c) acc[c] = fmaf(gt, dtd[c], acc[c]);
+        }
         acc[8] = fmaf(bw.g0, w, acc[8]);
         acc[9] = fmaf(bw.g1, w, acc[9]);
         acc[10] = fmaf(bw.g2, w, acc[10]);
@@ -328,53 +370,37 @@ __device__ __forceinline__ void atomic_grad(float* grad_rec, uint32_t r, const f
         if (acc[c] != 0.0f) atomicAdd(gp + c, acc[c]);
 }
 
-// Sum of acc[0..NV-1] (NV <= 16) over the warp, transposed: each butterfly level keeps
-// half of the values and exchanges the other half, so 16 shuffles reduce all of them
-// (instead of 5 per value).  Afterwards even lanes hold the totals, value index
-// ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1) for lane l, and each of
-// the NV lanes owning a real value adds it to the record's gradient slot.
+// Sum of acc[0..NV-1] over the warp, transposed.  Each butterfly level (lane distance 16, 8, 4, 2,
+// 1) splits the values the lane still holds into a first half (kept by the lanes without that
+// distance's bit) and the rest (kept by the others), exchanging the half it gives up: NV = 11 takes
+// 6 + 3 + 2 + 1 + 1 = 13 shuffles (14 values: 15).  Afterwards every value's total sits in exactly
+// one lane, which adds it to the record's gradient slot.
+template <int N, int D>
+__device__ __forceinline__ void fold_level(float* v, int lane, int& idx, int& nreal) {
+    if constexpr (D >= 1) {
+        constexpr int H = (N + 1) / 2;
+        const bool up = lane & D;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const float lo = v[i];
+            const float hi = (H + i < N) ? v[H + i] : 0.0f;
+            v[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, D);
+        }
+        idx += up ? H : 0;
+        nreal = up ? max(nreal - H, 0) : min(nreal, H);
+        fold_level<H, D / 2>(v, lane, idx, nreal);
+    }
+}
+
 template <int NV>
 __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
     const int lane = threadIdx.x & 31;
-    float v[16];
+    float v[NV];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = c < NV ? acc[c] : 0.0f;
-    {
-        const bool up = lane & 16;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float send = up ? v[i] : v[i + 8];
-            const float keep = up ? v[i + 8] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
-    }
-    {
-        const bool up = lane & 8;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float send = up ? v[i] : v[i + 4];
-            const float keep = up ? v[i + 4] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-    }
-    {
-        const bool up = lane & 4;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float send = up ? v[i] : v[i + 2];
-            const float keep = up ? v[i + 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-        }
-    }
-    {
-        const bool up = lane & 2;
-        const float send = up ? v[0] : v[1];
-        const float keep = up ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-    const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-    if (!(lane & 1) && idx < NV && v[0] != 0.0f) atomicAdd(gp + idx, v[0]);
+    for (int c = 0; c < NV; ++c) v[c] = acc[c];
+    int idx = 0, nreal = NV;
+    fold_level<NV, 16>(v, lane, idx, nreal);
+    if (nreal > 0 && v[0] != 0.0f) atomicAdd(gp + idx, v[0]);
 }
 
 // Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
@@ -433,11 +459,19 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 #ifndef DV_BWD_MIN_BLOCKS
 #define DV_BWD_MIN_BLOCKS 4
 #endif
+#ifndef DV_PLAIN_MIN_BLOCKS
+#define DV_PLAIN_MIN_BLOCKS 8  // the variant for tiles without actors (64 registers)
+#endif
 
 // BWD: replay with gradients.  WEX: replay that writes every composited segment's (voxel,
 // weight) into the pixel's slots of the weights export (no outputs, no gradients).
-template <bool BWD, int KS, bool NRM, bool WEX>
-__global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
+// NTA: lockstep actor slots (0: the tile is covered by no actor clip box).  Tiles that no box covers
+// (most of a frame) run the variant without the actor machinery: no interval walk, partials or
+// replays, no per-pixel actor state in shared memory, and about half the registers, so about twice
+// the resident warps per SM.  Tiles that many boxes cover get 16 slots, the others 4.
+template <bool BWD, int KS, bool NRM, bool WEX, int NTA>
+__global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_BLOCKS : DV_FWD_MIN_BLOCKS)
+                                                  : DV_PLAIN_MIN_BLOCKS) k_composite(const __grid_constant__ BatchParams bp,
                                                         const VoxRec* __restrict__ rec,
                                                         const uint32_t* __restrict__ pval,
                                                         const uint8_t* __restrict__ pmask,
@@ -462,10 +496,11 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
     __shared__ uint8_t s_m[2][CT_THREADS];
     __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];  // sub-list of octree o: [s_sub[o], s_sub[o+1])
     __shared__ uint32_t s_vs[DV_MAX_OCTREES + 1];   // first record of octree o in this view
-    __shared__ bool s_flag[DV_MAX_OCTREES];         // actor o's box covers this tile
-    __shared__ int16_t s_act[DV_MAX_OCTREES];
-    __shared__ float s_iv[NTA][2][CT_THREADS];
-    __shared__ float s_st[NTA][NRM ? 9 : 6][CT_THREADS];
+    constexpr bool ACT = NTA > 0;
+    __shared__ bool s_flag[ACT ? DV_MAX_OCTREES : 1];  // actor o's box covers this tile
+    __shared__ int16_t s_act[ACT ? DV_MAX_OCTREES : 1];
+    __shared__ float s_iv[ACT ? NTA : 1][2][ACT ? CT_THREADS : 1];
+    __shared__ float s_st[ACT ? NTA : 1][NRM ? 9 : 6][ACT ? CT_THREADS : 1];
     __shared__ int s_nact;
 
     const int tid = threadIdx.x;
@@ -562,10 +597,12 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
     // tile set-up, all loads independent of one another: the view's octree boundaries in
     // the record order, and which actor boxes cover this tile
     for (int i = tid; i <= n_oct; i += CT_THREADS) s_vs[i] = __ldg(vis_start + view * n_oct + i);
-    for (int o = tid; o < n_oct; o += CT_THREADS) {
-        const OctParams& P = vo[o];
-        s_flag[o] = o > 0 && P.role == DV_ROLE_ACTOR && P.rect[0] <= tx && tx <= P.rect[2] && P.rect[1] <= ty &&
-                    ty <= P.rect[3];
+    if (ACT) {
+        for (int o = tid; o < n_oct; o += CT_THREADS) {
+            const OctParams& P = vo[o];
+            s_flag[ACT ? o : 0] = o > 0 && P.role == DV_ROLE_ACTOR && P.rect[0] <= tx && tx <= P.rect[2] &&
+                                  P.rect[1] <= ty && ty <= P.rect[3];
+        }
     }
     __syncthreads();
     // the tile's list is grouped by octree (records are in depth-key order, octree above
@@ -597,21 +634,21 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
         if (rg.x == rg.y)
             for (int i = tid; i <= n_oct; i += CT_THREADS) s_sub[i] = rg.x;
     }
-    if (tid < 32) {
+    if (ACT && tid < 32) {
         // actor list of the tile in octree order (warp 0, ballot compaction)
         int n = 0;
         for (int o0 = 0; o0 < n_oct; o0 += 32) {
             const int o = o0 + tid;
-            const bool f = o < n_oct && s_flag[o];
+            const bool f = o < n_oct && s_flag[ACT ? o : 0];
             const unsigned b = __ballot_sync(0xffffffffu, f);
-            if (f) s_act[n + __popc(b & ((1u << tid) - 1u))] = (int16_t)o;
+            if (f) s_act[ACT ? n + __popc(b & ((1u << tid) - 1u)) : 0] = (int16_t)o;
             n += __popc(b);
         }
         if (tid == 0) s_nact = n;
     }
     __syncthreads();
 
-    const int n_ta = s_nact;
+    const int n_ta = ACT ? s_nact : 0;  // 0 at compile time without actors: the actor code folds away
     const int n_lock = n_ta < NTA ? n_ta : NTA;
 
     // ---- owned actor intervals of this ray (lockstep slots) ----
@@ -934,9 +971,9 @@ __global__ void __launch_bounds__(CT_THREADS, (BWD || WEX) ? DV_BWD_MIN_BLOCKS :
             const float r0[3] = {g0.x, g0.y, g0.z}, r1[3] = {g1.x, g1.y, g1.z};
             const float u0 = h0 ? a0 : 0.0f, v0 = h0 ? b0 : 0.0f, u1 = h1 ? a1 : 0.0f, v1 = h1 ? b1 : 0.0f;
             const float tau0 = seg_tau<false, KS>(da0, dd0, col0.w, r0, db_, u0, v0, bp.K, bp.inv_k, bp.activation,
-                                                  nullptr);
+                                                  nullptr, nullptr);
             const float tau1 = seg_tau<false, KS>(da1, dd1, col1.w, r1, db_, u1, v1, bp.K, bp.inv_k, bp.activation,
-                                                  nullptr);
+                                                  nullptr, nullptr);
             ps.tests += live ? 1u : 0u;
             if (h0) composite_tau<NRM>(ps, tau0, col0, staged_nv(slot, j0), u0, v0, bp.eps_stop);
             ps.tests += (live && !ps.done) ? 1u : 0u;
@@ -1089,7 +1126,9 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
         // and each corner enters g_a with sign + on the high side of axis a, - on the low side
         const float dw0 = gr[11], dw1 = gr[12], dw2 = gr[13];
         if (d_dens && (dw0 != 0.0f || dw1 != 0.0f || dw2 != 0.0f)) {
-            const float4 da = rec[r].v[1], db = rec[r].v[2];
+            // the raw corner densities, as the records kernel used them for the voxel normal
+            const float4* d4 = reinterpret_cast<const float4*>(P.dens + v * 8);
+            const float4 da = __ldg(d4), db = __ldg(d4 + 1);
             const float gx = (da.y + da.w + db.y + db.w) - (da.x + da.z + db.x + db.z);
             const float gy = (da.z + da.w + db.z + db.w) - (da.x + da.y + db.x + db.y);
             const float gz = (db.x + db.y + db.z + db.w) - (da.x + da.y + da.z + da.w);
@@ -1171,28 +1210,85 @@ __global__ void __launch_bounds__(256) k_sh_bwd(const __grid_constant__ ShBwdPar
     }
 }
 
+// Three launches per compositing pass, two CTAs per tile, over the three groups of the tile order:
+// the tiles that 5 or more actor boxes cover (8 lockstep actor slots), those that 1 to 4 cover (4
+// slots), and the others (no actor machinery).  They run side by side: the two actor launches on the
+// context's two extra streams (the device's highest priority, so their CTAs -- the heaviest tiles of
+// a frame -- are dispatched first), forked from and joined back into the call's stream by events, the
+// plain launch on the call's stream.  Without the extra streams they run one after the other.
+template <bool BWD, int KS, bool NRM, bool WEX>
+void composite_launch(const BatchParams& bp, const VoxRec* rec, const uint32_t* pval, const uint8_t* pmask,
+                      const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
+                      uint32_t* n_seg, float* t_final, const float* g_rgb, const float* g_depth,
+                      const float* g_alpha, const float* g_normal, float* grad_rec, unsigned long long* work,
+                      const int64_t* ex_off, uint32_t* ex_vid, float* ex_w, const Fork* fk, cudaStream_t s) {
+    const int n_large = bp.n_tiles_large, n_small = bp.n_tiles_small;
+    const int n_plain = bp.n_tiles - n_large - n_small;
+    const int groups = (n_large > 0) + (n_small > 0) + (n_plain > 0);
+    const bool fork = fk && fk->side && fk->side2 && groups > 1;
+    cudaStream_t s_large = s, s_small = s;
+    if (fork && cudaEventRecord(fk->ev_fork, s) == cudaSuccess) {
+        if (n_large > 0 && cudaStreamWaitEvent(fk->side, fk->ev_fork, 0) == cudaSuccess) s_large = fk->side;
+        if (n_small > 0 && cudaStreamWaitEvent(fk->side2, fk->ev_fork, 0) == cudaSuccess) s_small = fk->side2;
+    }
+    if (n_large > 0) {
+        launch_pdl(k_composite<BWD, KS, NRM, WEX, NTA_LARGE>, dim3(2 * n_large), dim3(CT_THREADS), s_large, bp, rec,
+                   pval, pmask, tile_range, vis_start, tile_order, n_seg, t_final, g_rgb, g_depth, g_alpha, g_normal,
+                   grad_rec, work, ex_off, ex_vid, ex_w);
+        count_launches(1);
+    }
+    if (n_small > 0) {
+        launch_pdl(k_composite<BWD, KS, NRM, WEX, NTA_SMALL>, dim3(2 * n_small), dim3(CT_THREADS), s_small, bp, rec,
+                   pval, pmask, tile_range, vis_start, tile_order + n_large, n_seg, t_final, g_rgb, g_depth, g_alpha,
+                   g_normal, grad_rec, work, ex_off, ex_vid, ex_w);
+        count_launches(1);
+    }
+    if (n_plain > 0) {
+        launch_pdl(k_composite<BWD, KS, NRM, WEX, 0>, dim3(2 * n_plain), dim3(CT_THREADS), s, bp, rec, pval, pmask,
+                   tile_range, vis_start, tile_order + n_large + n_small, n_seg, t_final, g_rgb, g_depth, g_alpha,
+                   g_normal, grad_rec, work, ex_off, ex_vid, ex_w);
+        count_launches(1);
+    }
+    if (s_large != s) {
+        cudaEventRecord(fk->ev_join, s_large);
+        cudaStreamWaitEvent(s, fk->ev_join, 0);
+    }
+    if (s_small != s) {
+        cudaEventRecord(fk->ev_join2, s_small);
+        cudaStreamWaitEvent(s, fk->ev_join2, 0);
+    }
+}
+
 template <bool NRM>
 void composite_fwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val, const uint8_t* pair_mask,
                      const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order, uint32_t* n_seg,
-                     float* t_final, unsigned long long* work, cudaStream_t s) {
+                     float* t_final, unsigned long long* work, const Fork* fk, cudaStream_t s) {
     if (bp.K == 1)
-        launch_pdl(k_composite<false, 1, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
+        composite_launch<false, 1, NRM, false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg,
+                                               t_final, nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr,
+                                               nullptr, nullptr, fk, s);
     else
-        launch_pdl(k_composite<false, 0, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr, nullptr, nullptr);
+        composite_launch<false, 0, NRM, false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg,
+                                               t_final, nullptr, nullptr, nullptr, nullptr, nullptr, work, nullptr,
+                                               nullptr, nullptr, fk, s);
 }
 
 template <bool NRM>
 void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val, const uint8_t* pair_mask,
                      const uint2* tile_range, const uint32_t* vis_start, const uint32_t* tile_order,
                      const float* t_final, const float* g_rgb, const float* g_depth, const float* g_alpha,
-                     const float* g_normal, float* grad_rec, cudaStream_t s) {
+                     const float* g_normal, float* grad_rec, const Fork* fk, cudaStream_t s) {
     // the kernel's per-pixel forward results (final T here, C, D, N through the view parameters)
     // are only read in the backward
     float* tf = const_cast<float*>(t_final);
     if (bp.K == 1)
-        launch_pdl(k_composite<true, 1, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha, g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
+        composite_launch<true, 1, NRM, false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr,
+                                              tf, g_rgb, g_depth, g_alpha, g_normal, grad_rec, nullptr, nullptr,
+                                              nullptr, nullptr, fk, s);
     else
-        launch_pdl(k_composite<true, 0, NRM, false>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, tf, g_rgb, g_depth, g_alpha, g_normal, grad_rec, nullptr, nullptr, nullptr, nullptr);
+        composite_launch<true, 0, NRM, false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr,
+                                              tf, g_rgb, g_depth, g_alpha, g_normal, grad_rec, nullptr, nullptr,
+                                              nullptr, nullptr, fk, s);
 }
 
 }  // namespace
@@ -1200,15 +1296,14 @@ void composite_bwd_k(const BatchParams& bp, const VoxRec* rec, const uint32_t* p
 cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, uint32_t* n_seg, float* t_final,
-                                 unsigned long long* work, cudaStream_t s) {
+                                 unsigned long long* work, const Fork* fk, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
     if (bp.normals)
         composite_fwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, work,
-                              s);
+                              fk, s);
     else
         composite_fwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, n_seg, t_final, work,
-                               s);
-    count_launches(1);
+                               fk, s);
     return cudaGetLastError();
 }
 
@@ -1216,28 +1311,30 @@ cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, const float* t_final, const float* g_rgb,
                                  const float* g_depth, const float* g_alpha, const float* g_normal, float* grad_rec,
-                                 cudaStream_t s) {
+                                 const Fork* fk, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
     if (g_normal)
         composite_bwd_k<true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, t_final, g_rgb,
-                              g_depth, g_alpha, g_normal, grad_rec, s);
+                              g_depth, g_alpha, g_normal, grad_rec, fk, s);
     else
         composite_bwd_k<false>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, t_final, g_rgb,
-                               g_depth, g_alpha, nullptr, grad_rec, s);
-    count_launches(1);
+                               g_depth, g_alpha, nullptr, grad_rec, fk, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                     const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                     const uint32_t* tile_order, const int64_t* offsets, uint32_t* voxel, float* weight,
-                                    cudaStream_t s) {
+                                    const Fork* fk, cudaStream_t s) {
     if (bp.n_tiles <= 0) return cudaSuccess;
     if (bp.K == 1)
-        launch_pdl(k_composite<false, 1, false, true>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
+        composite_launch<false, 1, false, true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr,
+                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets,
+                                                voxel, weight, fk, s);
     else
-        launch_pdl(k_composite<false, 0, false, true>, dim3(2 * bp.n_tiles), dim3(CT_THREADS), s, bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets, voxel, weight);
-    count_launches(1);
+        composite_launch<false, 0, false, true>(bp, rec, pair_val, pair_mask, tile_range, vis_start, tile_order, nullptr,
+                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, offsets,
+                                                voxel, weight, fk, s);
     return cudaGetLastError();
 }
 

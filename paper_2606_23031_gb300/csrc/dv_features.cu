@@ -278,7 +278,8 @@ cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t
 }
 
 cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt, const float* f2d,
-                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s) {
+                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s, bool* sort_timeout) {
+    *sort_timeout = false;
     if (n_pix <= 0 || C <= 0) return cudaSuccess;
     int64_t n = 0;
     cudaError_t e = cudaMemcpyAsync(&n, off + n_pix, sizeof(n), cudaMemcpyDeviceToHost, s);
@@ -291,9 +292,9 @@ cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, co
     uint32_t* v0 = ar.alloc<uint32_t>(n);
     uint32_t* v1 = ar.alloc<uint32_t>(n);
     uint2* pw = ar.alloc<uint2>(n);
-    uint32_t* vmax = ar.alloc<uint32_t>(1);
+    uint32_t* vmax = ar.alloc<uint32_t>(2);  // [0] largest voxel index, [1] the sort's wait flag
     if (ar.err != cudaSuccess) return ar.err;
-    e = cudaMemsetAsync(vmax, 0, sizeof(uint32_t), s);
+    e = cudaMemsetAsync(vmax, 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_fuse_prep<<<(unsigned)((n_pix + FZ_PREP - 1) / FZ_PREP), FZ_PREP, 0, s>>>(n_pix, off, vox, wgt, k0, v0, pw, vmax);
     count_launches(1);
@@ -305,7 +306,7 @@ cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, co
     while (bits < 32 && (vm >> bits)) ++bits;
     uint32_t* kk = k0;
     uint32_t* vv = v0;
-    e = radix_sort_u32(kk, vv, k1, v1, n, bits, ar, s);
+    e = radix_sort_u32(kk, vv, k1, v1, n, bits, ar, s, vmax + 1);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((n + FZ_CHUNK * 8 - 1) / (FZ_CHUNK * 8));
     const float4* f4 = reinterpret_cast<const float4*>(f2d);
@@ -327,7 +328,13 @@ cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, co
         k_fuse_runs<4><<<grid, 256, 0, s>>>(n, kk, vv, pw, f2d, C, acc, wsum);
     }
     count_launches(1);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    // the sort's own wait flag: a run-out look-back left the slots unsorted and the sums wrong
+    uint32_t flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, vmax + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *sort_timeout = flag != 0;
+    return e;
 }
 
 }  // namespace dv

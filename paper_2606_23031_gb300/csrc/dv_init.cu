@@ -361,8 +361,9 @@ cudaError_t key_levels(const uint64_t* keys, int64_t n, uint32_t* levels_host, A
 }
 
 cudaError_t shared_corners(const uint64_t* keys, int64_t n, int max_level, uint64_t* grid_out, uint32_t* index_out,
-                           int64_t* n_corners, Arena& ar, cudaStream_t s) {
+                           int64_t* n_corners, Arena& ar, cudaStream_t s, bool* sort_timeout) {
     *n_corners = 0;
+    *sort_timeout = false;
     if (n <= 0) return cudaSuccess;
     const int64_t m = n * 8;
     uint64_t* k0 = ar.alloc<uint64_t>(m);
@@ -371,13 +372,15 @@ cudaError_t shared_corners(const uint64_t* keys, int64_t n, int max_level, uint6
     uint32_t* v1 = ar.alloc<uint32_t>(m);
     uint32_t* first = ar.alloc<uint32_t>(m);
     uint32_t* pos = ar.alloc<uint32_t>(m);
-    uint32_t* total = ar.alloc<uint32_t>(1);
+    uint32_t* total = ar.alloc<uint32_t>(2);  // [0] distinct corners, [1] the sort's wait flag
     if (ar.err != cudaSuccess) return ar.err;
+    cudaError_t e = cudaMemsetAsync(total + 1, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
     k_corner_emit<<<nb(m), 256, 0, s>>>(keys, n, max_level, k0, v0);
     count_launches(1);
     uint64_t* kk = k0;
     uint32_t* vv = v0;
-    cudaError_t e = radix_sort_u64(kk, vv, k1, v1, m, 63, ar, s);
+    e = radix_sort_u64(kk, vv, k1, v1, m, 63, ar, s, total + 1);
     if (e != cudaSuccess) return e;
     k_corner_flag<<<nb(m), 256, 0, s>>>(kk, m, first);
     count_launches(1);
@@ -385,10 +388,11 @@ cudaError_t shared_corners(const uint64_t* keys, int64_t n, int max_level, uint6
     if (e != cudaSuccess) return e;
     k_corner_assign<<<nb(m), 256, 0, s>>>(kk, vv, first, pos, m, grid_out, index_out);
     count_launches(1);
-    uint32_t h = 0;
-    e = cudaMemcpyAsync(&h, total, sizeof(h), cudaMemcpyDeviceToHost, s);
+    uint32_t h[2] = {0, 0};
+    e = cudaMemcpyAsync(h, total, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    *n_corners = h;
+    *n_corners = h[0];
+    *sort_timeout = h[1] != 0;
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
@@ -401,32 +405,46 @@ static Frame make_frame(const double* center, double root_size, int max_level) {
 
 cudaError_t soft_prior(const uint64_t* grid, int64_t n_corners, const double* center, double root_size, int max_level,
                        const float* cloud, int64_t m, float s_min, float v_close, float v_far, float* dens, Arena& ar,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool* sort_timeout) {
+    *sort_timeout = false;
     if (n_corners <= 0) return cudaSuccess;
     const Frame f = make_frame(center, root_size, max_level);
     const double h = 3.0 * (double)s_min;
     uint64_t *k0 = nullptr, *k1 = nullptr;
     uint32_t *v0 = nullptr, *v1 = nullptr;
+    uint32_t* flag = nullptr;
     if (m > 0) {
         k0 = ar.alloc<uint64_t>(m);
         k1 = ar.alloc<uint64_t>(m);
         v0 = ar.alloc<uint32_t>(m);
         v1 = ar.alloc<uint32_t>(m);
+        flag = ar.alloc<uint32_t>(1);
         if (ar.err != cudaSuccess) return ar.err;
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return e;
         k_cloud_cells<<<nb(m), 256, 0, s>>>(cloud, m, f, h, k0, v0);
         count_launches(1);
-        cudaError_t e = radix_sort_u64(k0, v0, k1, v1, m, 3 * kCellBits, ar, s);
+        e = radix_sort_u64(k0, v0, k1, v1, m, 3 * kCellBits, ar, s, flag);
         if (e != cudaSuccess) return e;
     }
     k_soft_prior<<<nb(n_corners), 256, 0, s>>>(grid, n_corners, f, h, k0, v0, m, cloud, s_min, v_close, v_far, dens);
     count_launches(1);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (flag) {
+        // the cell sort's own wait flag: a run-out look-back left the cloud unsorted (wrong nearest points)
+        uint32_t hf = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flag, sizeof(hf), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        *sort_timeout = hf != 0;
+    }
+    return e;
 }
 
 cudaError_t subdivide_round(const uint64_t* keys, int64_t n, const double* center, double root_size, int max_level,
                             const float* cloud, int64_t m, float thr, uint64_t* out, int64_t* n_out, Arena& ar,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool* sort_timeout) {
     *n_out = n;
+    *sort_timeout = false;
     if (n <= 0) return cudaSuccess;
     const Frame f = make_frame(center, root_size, max_level);
     uint64_t* k0 = ar.alloc<uint64_t>(n);
@@ -439,22 +457,28 @@ cudaError_t subdivide_round(const uint64_t* keys, int64_t n, const double* cente
     uint32_t* pos_s = ar.alloc<uint32_t>(n);
     uint32_t* pos_k = ar.alloc<uint32_t>(n);
     uint32_t* tot = ar.alloc<uint32_t>(2);
-    uint32_t* lvl = ar.alloc<uint32_t>(1);
+    uint32_t* lvl = ar.alloc<uint32_t>(2);  // [0] levels present, [1] the sort's wait flag
     if (ar.err != cudaSuccess) return ar.err;
     cudaError_t e = cudaMemcpyAsync(k0, keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(split, 0, n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(lvl, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lvl, 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_iota_levels<<<nb(n), 256, 0, s>>>(keys, n, v0, lvl);
     count_launches(1);
     uint64_t* kk = k0;
     uint32_t* vv = v0;
-    e = radix_sort_u64(kk, vv, k1, v1, n, 62, ar, s);
+    e = radix_sort_u64(kk, vv, k1, v1, n, 62, ar, s, lvl + 1);
     if (e != cudaSuccess) return e;
-    uint32_t levels = 0;
-    e = cudaMemcpyAsync(&levels, lvl, sizeof(levels), cudaMemcpyDeviceToHost, s);
+    uint32_t lv[2] = {0, 0};
+    e = cudaMemcpyAsync(lv, lvl, sizeof(lv), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    const uint32_t levels = lv[0];
+    if (lv[1]) {
+        // the key sort's bounded wait ran out: its order is wrong, so no leaf lookup is trusted
+        *sort_timeout = true;
+        return cudaSuccess;
+    }
     if (m > 0) {
         k_subdiv_flags<<<nb(m), 256, 0, s>>>(cloud, m, f, root_size, levels, thr, kk, vv, n, split);
         count_launches(1);
@@ -471,6 +495,34 @@ cudaError_t subdivide_round(const uint64_t* keys, int64_t n, const double* cente
     k_subdiv_write<<<nb(n), 256, 0, s>>>(keys, n, split, pos_k, pos_s, n_keep, n_split, out);
     count_launches(1);
     *n_out = n_keep + 8 * n_split;
+    return cudaGetLastError();
+}
+
+}  // namespace dv
+
+namespace dv {
+
+namespace {
+
+// leaf t of the uniform grid: (i, j, k) = (t mod n, (t / n) mod n, t / n^2), n = 2^level
+__global__ void k_asset_grid(int level, float v_init, int64_t n_leaf, uint64_t* __restrict__ keys,
+                             float4* __restrict__ dens) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_leaf) return;
+    const uint64_t n = 1ull << level;
+    const uint64_t i = (uint64_t)t & (n - 1), j = ((uint64_t)t >> level) & (n - 1), k = (uint64_t)t >> (2 * level);
+    keys[t] = ((uint64_t)level << 57) | (k << 38) | (j << 19) | i;
+    const float4 v = make_float4(v_init, v_init, v_init, v_init);
+    dens[2 * t] = v;
+    dens[2 * t + 1] = v;
+}
+
+}  // namespace
+
+cudaError_t asset_grid(int level, float v_init, uint64_t* keys, float* dens, cudaStream_t s) {
+    const int64_t n = (int64_t)1 << (3 * level);
+    k_asset_grid<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(level, v_init, n, keys, reinterpret_cast<float4*>(dens));
+    count_launches(1);
     return cudaGetLastError();
 }
 

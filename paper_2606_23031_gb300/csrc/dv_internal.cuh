@@ -55,6 +55,8 @@ struct BatchParams {
     int32_t oct_shift;   // 3 * Lkey
     int32_t view_shift;  // oct_shift + bits(n_oct)
     int32_t n_tiles;     // over all views
+    int32_t n_tiles_large;  // tiles that 5 or more actor clip boxes cover (first in the tile order)
+    int32_t n_tiles_small;  // tiles that 1 to 4 actor clip boxes cover (next in the tile order)
     int32_t normals;     // the call renders the normal state N (records carry voxel normals)
     int64_t n_vox;       // voxels of one view (all octrees)
     int64_t vox_offset[DV_MAX_OCTREES + 1];
@@ -69,8 +71,8 @@ static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
 
 // 64-byte per-voxel render record, one per visible (view, voxel) in depth-key order.
 //   v[0] = (min - o, size)   min corner relative to the camera centre o, both in the octree's frame
-//   v[1] = dens[0..3]
-//   v[2] = dens[4..7]
+//   v[1] = (c0, c1, c2, c4)  the trilinear density as a polynomial in the voxel coordinates,
+//   v[2] = (c3, c5, c6, c7)  rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz
 //   v[3] = (r, g, b, 1/size)
 struct __align__(16) VoxRec {
     float4 v[4];
@@ -145,10 +147,17 @@ cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64
 cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, Arena& ar,
                             cudaStream_t s);
 // LSD radix sort of (key, value) pairs on bits [0, n_bits). Returns the buffers holding the result.
+// call_err (device word, may be null): set to 1 if a bounded look-back wait of this sort ran out
+// (the result is then not sorted); the device's wait-error word is set as well.
 cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s);
+                           int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err = nullptr);
 cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s);
+                           int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err = nullptr);
+// streaming multiprocessors of the current device (cached per device)
+int sm_count();
+// test hook: one sort tile whose predecessor never publishes waits `spin_limit` reads and gives up;
+// returns the tile's call flag and the device's wait-error word (which it then clears).  Synchronous.
+cudaError_t debug_sort_timeout(int spin_limit, uint32_t* call_flag, uint32_t* device_flag, cudaStream_t s);
 
 // kernel launchers (one thread per (view, voxel) unless stated)
 cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
@@ -158,7 +167,8 @@ cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect,
 // word and sets DV_FLAG_SPIN_TIMEOUT in word flag_idx
 cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, uint32_t* spin_err, int flag_idx,
                            cudaStream_t s);
-// device address of this device's wait-error word (bounded waits that run out set it); nullptr on failure
+// device address of this device's wait-error word (bounded waits that run out set it; shared by every
+// context on the device); nullptr on failure
 uint32_t* spin_error_word();
 cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
                            uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
@@ -175,27 +185,37 @@ cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64
 cudaError_t launch_pair_mask_ranges(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
                                     const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, uint2* tile_range,
                                     int n_tiles, cudaStream_t s);
-// tiles ordered by decreasing pair-list length (log2 buckets); scratch: 64 words
-cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* scratch64, uint32_t* order,
-                              cudaStream_t s);
+// tiles ordered by decreasing pair-list length (log2 buckets) within three groups, in this order: the
+// tiles that 5 or more actor clip boxes cover (bp.n_tiles_large), those that 1 to 4 cover
+// (bp.n_tiles_small), the others; scratch: 192 words
+cudaError_t launch_tile_order(const BatchParams& bp, const uint2* tile_range, int n_tiles, uint32_t* scratch192,
+                              uint32_t* order, cudaStream_t s);
+// Two more streams of the context with their events: a compositing pass runs its three launches (the
+// tiles that many actor boxes cover, those that a few cover, the others) side by side on these and
+// the call's stream.
+struct Fork {
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+};
+
 // outputs go to the views' buffers (ViewParams); n_seg and t_final per pixel are kept for the backward
 cudaError_t launch_composite_fwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, uint32_t* n_seg, float* t_final,
-                                 unsigned long long* work, cudaStream_t s);
+                                 unsigned long long* work, const Fork* fk, cudaStream_t s);
 // with g_normal (the call rendered normals): gradient rows of 16 floats (8 densities, 3 colour, 3 normal, 2 pad),
 // else of 12 (8 densities, 3 colour, 1 pad)
 cudaError_t launch_composite_bwd(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                  const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                  const uint32_t* tile_order, const float* t_final, const float* g_rgb,
                                  const float* g_depth, const float* g_alpha, const float* g_normal, float* grad_rec,
-                                 cudaStream_t s);
+                                 const Fork* fk, cudaStream_t s);
 // replay of the forward that writes, for pixel p, the (voxel, weight T alpha) of each composited
 // segment into slots [offsets[p], offsets[p+1]) (voxel index within the view's concatenated octrees)
 cudaError_t launch_composite_export(const BatchParams& bp, const VoxRec* rec, const uint32_t* pair_val,
                                     const uint8_t* pair_mask, const uint2* tile_range, const uint32_t* vis_start,
                                     const uint32_t* tile_order, const int64_t* offsets, uint32_t* voxel, float* weight,
-                                    cudaStream_t s);
+                                    const Fork* fk, cudaStream_t s);
 cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const VoxRec* rec,
                           const float* grad_rec, bool with_normals, float* const* d_dens, float* const* d_sh,
                           cudaStream_t s);
@@ -203,20 +223,26 @@ cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64
 // feature fields over a weights export (see dv_features.cu)
 cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
                                const float* feat, int C, float* out, cudaStream_t s);
-// sorts the slots by voxel (scratch from ar; reads the slot count back, so it synchronises s)
+// sorts the slots by voxel (scratch from ar; reads the slot count back, so it synchronises s);
+// *sort_timeout (host) is set when the sort's bounded wait ran out (read after a final synchronisation)
 cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt, const float* f2d,
-                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s);
+                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s, bool* sort_timeout);
 
-// LiDAR-guided initialisation (see dv_init.cu); the calls that return a size synchronise the stream
+// LiDAR-guided initialisation (see dv_init.cu); the calls that return a size synchronise the stream.
+// The calls that sort set *sort_timeout (host) when the sort's bounded wait ran out; they synchronise
+// the stream before they return.
 cudaError_t key_levels(const uint64_t* keys, int64_t n, uint32_t* levels_host, Arena& ar, cudaStream_t s);
 cudaError_t shared_corners(const uint64_t* keys, int64_t n, int max_level, uint64_t* grid_out, uint32_t* index_out,
-                           int64_t* n_corners, Arena& ar, cudaStream_t s);
+                           int64_t* n_corners, Arena& ar, cudaStream_t s, bool* sort_timeout);
 cudaError_t soft_prior(const uint64_t* grid, int64_t n_corners, const double* center, double root_size, int max_level,
                        const float* cloud, int64_t m, float s_min, float v_close, float v_far, float* dens, Arena& ar,
-                       cudaStream_t s);
+                       cudaStream_t s, bool* sort_timeout);
 cudaError_t subdivide_round(const uint64_t* keys, int64_t n, const double* center, double root_size, int max_level,
                             const float* cloud, int64_t m, float thr, uint64_t* out, int64_t* n_out, Arena& ar,
-                            cudaStream_t s);
+                            cudaStream_t s, bool* sort_timeout);
+// uniform leaf grid of an actor (Sec. 3.3, assets): keys of the 8^level leaves (i fastest) and every
+// corner density set to v_init
+cudaError_t asset_grid(int level, float v_init, uint64_t* keys, float* dens, cudaStream_t s);
 // a camera of the visibility pruning (double precision, camera -> world rotation row-major)
 struct InitCam {
     double R[9], t[3];
@@ -243,9 +269,16 @@ cudaError_t launch_sky_bwd(const SkyView& v, const float* env, int He, int We, c
 // camera and pose checks of one render request (the same as dv_render's); no context needed
 dv_status validate_request(const dv_camera& cam, const dv_pose* poses, int n_oct);
 
-// render of views whose outputs live in separate device buffers (serving loop)
+// device memory a render call takes from its context's pool: the part known before any work is
+// enqueued (n_view views of n_oct octrees, NT = views x voxels, tiles and pixels over the views) and
+// the part that follows from the projection's sizes (visible voxels, pairs)
+int64_t render_need_before(int64_t n_view, int64_t n_oct, int64_t NT, int64_t tiles, int64_t pix);
+int64_t render_need_after(int64_t n_vis, int64_t P, int key_bits, int tile_bits, bool normals);
+
+// render of views whose outputs live in separate device buffers (serving loop); the saved state
+// (non-null) lets the caller check the call's sorts once its stream has finished
 dv_status render_views_into(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_view* views, int n_view,
                             const dv_opts* opts, float* const* rgbs, float* const* depths, float* const* alphas,
-                            void* stream);
+                            dv_state** saved, void* stream);
 
 }  // namespace dv

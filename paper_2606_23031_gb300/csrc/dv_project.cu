@@ -303,8 +303,13 @@ __global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchPa
     const float c0 = cc[0], c1 = cc[1], c2 = cc[2];
     VoxRec R;
     R.v[0] = make_float4(rx, ry, rz, L.s);
-    R.v[1] = da;
-    R.v[2] = db;
+    // the trilinear field as a polynomial in the voxel coordinates (x, y, z) in [0, 1]^3:
+    // rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz, from corner c = x + 2y + 4z
+    const float p1 = da.y - da.x, p2 = da.z - da.x, p3 = db.x - da.x;
+    const float p4 = (da.w - da.z) - p1, p5 = (db.y - db.x) - p1, p6 = (db.z - db.x) - p2;
+    const float p7 = ((db.w - db.z) - (db.y - db.x)) - ((da.w - da.z) - p1);
+    R.v[1] = make_float4(da.x, p1, p2, p4);
+    R.v[2] = make_float4(p3, p5, p6, p7);
     R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);
     rec[r] = R;
     if (nrm) {
@@ -419,47 +424,70 @@ __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32
 
 // Heaviest tiles first: counting sort of tiles by floor(log2(list length + 1)),
 // descending, so the longest CTAs start early and the short ones fill in behind
-// them.  The order inside a bucket does not matter (tiles are independent).
-__device__ __forceinline__ int tile_bucket(uint2 r) { return 31 - __clz((int)(r.y - r.x) + 1); }
+// them, within three groups that run as separate launches of the compositing
+// kernel: the tiles that 5 or more actor clip boxes cover (buckets 64..95), those
+// that 1 to 4 cover (32..63), the others (0..31).  The order inside a bucket does
+// not matter (tiles are independent).
+constexpr int TILE_BUCKETS = 96;
 
-__global__ void k_tile_count(const uint2* __restrict__ range, int n_tiles, uint32_t* __restrict__ cnt) {
+__device__ __forceinline__ int tile_bucket(const BatchParams& bp, const uint2* __restrict__ range, int t) {
+    const uint2 r = range[t];
+    const int b = 31 - __clz((int)(r.y - r.x) + 1);
+    const int view = view_of_tile(bp, t);
+    const int tl = t - bp.tile_base[view];
+    const int tiles_x = bp.views[view].tiles_x;
+    const int tx = tl % tiles_x, ty = tl / tiles_x;
+    const OctParams* vo = bp.octs + view * bp.n_oct;
+    int boxes = 0;
+    for (int o = 1; o < bp.n_oct && boxes < 5; ++o) {
+        const OctParams& P = vo[o];
+        if (P.role == DV_ROLE_ACTOR && P.rect[0] <= tx && tx <= P.rect[2] && P.rect[1] <= ty && ty <= P.rect[3])
+            ++boxes;
+    }
+    return b + (boxes >= 5 ? 64 : boxes > 0 ? 32 : 0);
+}
+
+__global__ void k_tile_count(const __grid_constant__ BatchParams bp, const uint2* __restrict__ range, int n_tiles,
+                             uint32_t* __restrict__ cnt) {
     pdl_wait();
     pdl_launch_dependents();
-    __shared__ uint32_t h[32];
-    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __shared__ uint32_t h[TILE_BUCKETS];
+    if (threadIdx.x < TILE_BUCKETS) h[threadIdx.x] = 0;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_tiles) atomicAdd(&h[tile_bucket(range[t])], 1u);
+    if (t < n_tiles) atomicAdd(&h[tile_bucket(bp, range, t)], 1u);
     __syncthreads();
-    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x < TILE_BUCKETS && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
 }
 
 __global__ void k_tile_offsets(uint32_t* __restrict__ cnt_off) {
     pdl_wait();
     pdl_launch_dependents();
-    // cnt_off[0..31] counts -> cnt_off[32..63] start of each bucket, heaviest bucket first
+    // cnt_off[0..95] counts -> cnt_off[96..191] start of each bucket, from the heaviest bucket of the
+    // first group down
     if (threadIdx.x == 0) {
         uint32_t run = 0;
-        for (int b = 31; b >= 0; --b) {
-            cnt_off[32 + b] = run;
+        for (int b = TILE_BUCKETS - 1; b >= 0; --b) {
+            cnt_off[TILE_BUCKETS + b] = run;
             run += cnt_off[b];
         }
     }
 }
 
-__global__ void k_tile_scatter(const uint2* __restrict__ range, int n_tiles, uint32_t* __restrict__ off,
-                               uint32_t* __restrict__ order) {
+__global__ void k_tile_scatter(const __grid_constant__ BatchParams bp, const uint2* __restrict__ range, int n_tiles,
+                               uint32_t* __restrict__ off, uint32_t* __restrict__ order) {
     pdl_wait();
     pdl_launch_dependents();
     // block-local ranks first, then one global reservation per (block, bucket)
-    __shared__ uint32_t h[32], base[32];
-    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __shared__ uint32_t h[TILE_BUCKETS], base[TILE_BUCKETS];
+    if (threadIdx.x < TILE_BUCKETS) h[threadIdx.x] = 0;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = t < n_tiles ? tile_bucket(range[t]) : -1;
+    const int b = t < n_tiles ? tile_bucket(bp, range, t) : -1;
     const uint32_t rank = b >= 0 ? atomicAdd(&h[b], 1u) : 0u;
     __syncthreads();
-    if (threadIdx.x < 32 && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&off[threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x < TILE_BUCKETS && h[threadIdx.x])
+        base[threadIdx.x] = atomicAdd(&off[threadIdx.x], h[threadIdx.x]);
     __syncthreads();
     if (b >= 0) order[base[b] + rank] = (uint32_t)t;
 }
@@ -468,16 +496,17 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
-cudaError_t launch_tile_order(const uint2* tile_range, int n_tiles, uint32_t* scratch64, uint32_t* order,
-                              cudaStream_t s) {
+cudaError_t launch_tile_order(const BatchParams& bp, const uint2* tile_range, int n_tiles, uint32_t* scratch192,
+                              uint32_t* order, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(scratch64, 0, 64 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(scratch192, 0, 2 * TILE_BUCKETS * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    launch_pdl(k_tile_count, dim3(nblk(n_tiles, 256)), dim3(256), s, tile_range, n_tiles, scratch64);
+    launch_pdl(k_tile_count, dim3(nblk(n_tiles, 256)), dim3(256), s, bp, tile_range, n_tiles, scratch192);
     count_launches(1);
-    launch_pdl(k_tile_offsets, dim3(1), dim3(32), s, scratch64);
+    launch_pdl(k_tile_offsets, dim3(1), dim3(32), s, scratch192);
     count_launches(1);
-    launch_pdl(k_tile_scatter, dim3(nblk(n_tiles, 256)), dim3(256), s, tile_range, n_tiles, scratch64 + 32, order);
+    launch_pdl(k_tile_scatter, dim3(nblk(n_tiles, 256)), dim3(256), s, bp, tile_range, n_tiles,
+               scratch192 + TILE_BUCKETS, order);
     count_launches(1);
     return cudaGetLastError();
 }

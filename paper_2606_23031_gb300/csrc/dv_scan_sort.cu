@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "dv_internal.cuh"
 
 namespace dv {
@@ -267,7 +269,7 @@ __device__ uint32_t g_spin_error = 0u;
 constexpr int OS_THREADS = 256;
 constexpr int OS_MAX_PASSES = 8;
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_VAL = (1u << 30) - 1u;
-constexpr int OS_SPIN_LIMIT = 1 << 22;
+constexpr int OS_SPIN_LIMIT = 1 << 22;  // reads of a predecessor's status word before a pass gives up (~seconds)
 constexpr int OS_LOOK = 8;  // predecessors read per look-back step
 
 template <typename K>
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
                                                          const uint32_t* __restrict__ goff,
                                                          uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
                                                          uint32_t* __restrict__ err, K* __restrict__ okeys,
-                                                         uint32_t* __restrict__ ovals) {
+                                                         uint32_t* __restrict__ ovals, int spin_limit) {
     pdl_wait();
     pdl_launch_dependents();
     __shared__ uint32_t s_tile;
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
                 }
                 const uint32_t* sp = status + (size_t)(t - i) * RS_RADIX + tid;
                 int spins = 0;
-                while ((v[i] & ~OS_VAL) == 0 && ++spins < OS_SPIN_LIMIT) v[i] = os_load(sp);
+                while ((v[i] & ~OS_VAL) == 0 && ++spins < spin_limit) v[i] = os_load(sp);
                 if ((v[i] & ~OS_VAL) == 0) {
                     atomicOr(err, 1u);
                     atomicOr(&g_spin_error, 1u);
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
 
 template <typename K, int ROUNDS>
 cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits,
-                          Arena& ar, cudaStream_t s) {
+                          uint32_t* call_err, int n_sm, Arena& ar, cudaStream_t s) {
     const int passes = (n_bits + 7) / 8;
     const int64_t tile = (int64_t)OS_THREADS * ROUNDS;
     const int64_t n_tiles = (n + tile - 1) / tile;
@@ -432,7 +434,8 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
     cudaError_t e = cudaMemsetAsync(w, 0, words * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     int64_t hist_blocks = (n + OS_THREADS * 4 - 1) / (OS_THREADS * 4);  // ~4 keys per thread, at most 8 CTAs per SM
-    if (hist_blocks > 152 * 8) hist_blocks = 152 * 8;
+    if (hist_blocks > (int64_t)n_sm * 8) hist_blocks = (int64_t)n_sm * 8;
+    uint32_t* perr = call_err ? call_err : err;
     launch_pdl(k_os_hist<K>, dim3((unsigned)(hist_blocks < 1 ? 1 : hist_blocks)), dim3(OS_THREADS), s, keys, n, passes, n_bits, ghist);
     count_launches(1);
     launch_pdl(k_os_bins, dim3(passes), dim3(RS_RADIX), s, ghist);
@@ -444,7 +447,7 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int bits = n_bits - shift < 8 ? n_bits - shift : 8;
-        launch_pdl(k_os_pass<K, ROUNDS>, dim3((unsigned)n_tiles), dim3(OS_THREADS), s, src_k, src_v, n, shift, (1u << bits) - 1u, ghist + p * RS_RADIX, status + (size_t)p * n_tiles * RS_RADIX, counters + p, err, dst_k, dst_v);
+        launch_pdl(k_os_pass<K, ROUNDS>, dim3((unsigned)n_tiles), dim3(OS_THREADS), s, src_k, src_v, n, shift, (1u << bits) - 1u, ghist + p * RS_RADIX, status + (size_t)p * n_tiles * RS_RADIX, counters + p, perr, dst_k, dst_v, OS_SPIN_LIMIT);
         count_launches(1);
         K* tk = src_k;
         src_k = dst_k;
@@ -462,13 +465,16 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
 // SM: fewer, larger tiles shorten the look-back chains, which dominate small passes (a 112k-key
 // depth sort: 2 rounds 65 us, 4 rounds 56 us, 8 rounds 61 us for its 5 passes).
 template <typename K>
-cudaError_t onesweep(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits, Arena& ar,
-                     cudaStream_t s) {
-    const int64_t per_round = (int64_t)OS_THREADS * 152;
-    if (n <= per_round) return onesweep_impl<K, 1>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
-    if (n <= 2 * per_round) return onesweep_impl<K, 2>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
-    if (n <= 4 * per_round) return onesweep_impl<K, 4>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
-    return onesweep_impl<K, 8>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+cudaError_t onesweep(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits,
+                     uint32_t* call_err, Arena& ar, cudaStream_t s) {
+    const int n_sm = sm_count();
+    const int64_t per_round = (int64_t)OS_THREADS * n_sm;
+    if (n <= per_round) return onesweep_impl<K, 1>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    if (n <= 2 * per_round)
+        return onesweep_impl<K, 2>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    if (n <= 4 * per_round)
+        return onesweep_impl<K, 4>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    return onesweep_impl<K, 8>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
 }
 
 }  // namespace
@@ -476,6 +482,56 @@ cudaError_t onesweep(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt,
 uint32_t* spin_error_word() {
     void* p = nullptr;
     return cudaGetSymbolAddress(&p, g_spin_error) == cudaSuccess ? static_cast<uint32_t*>(p) : nullptr;
+}
+
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 152;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
+// One tile of a one-sweep pass whose predecessor never publishes: the tile takes index 1 from a
+// counter preset to 1, and tile 0's status words stay zero, so every look-back spin of the tile
+// runs out of `spin_limit` reads.  The kernel then sets the call's flag and the device's
+// wait-error word and finishes its (clamped) scatter, like a pass in production.  All buffers
+// are sized for two tiles of one round; nothing waits without a bound.
+cudaError_t debug_sort_timeout(int spin_limit, uint32_t* call_flag, uint32_t* device_flag, cudaStream_t s) {
+    const int64_t n = 2 * OS_THREADS;
+    uint32_t* w = nullptr;
+    const size_t words = (size_t)n * 4 + RS_RADIX + 2 * RS_RADIX + 2;
+    cudaError_t e = cudaMallocAsync(&w, words * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    uint32_t* keys = w;                        // [n]
+    uint32_t* vals = keys + n;                 // [n]
+    uint32_t* okeys = vals + n;                // [n]
+    uint32_t* ovals = okeys + n;               // [n]
+    uint32_t* goff = ovals + n;                // [256] zero: every digit starts at 0
+    uint32_t* status = goff + RS_RADIX;        // [2][256] zero: tile 0 never publishes
+    uint32_t* counter = status + 2 * RS_RADIX; // [1] = 1: the launched tile is tile 1
+    uint32_t* err = counter + 1;               // [1]
+    e = cudaMemsetAsync(w, 0, words * sizeof(uint32_t), s);
+    const uint32_t one = 1u;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counter, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_os_pass<uint32_t, 1><<<1, OS_THREADS, 0, s>>>(keys, vals, n, 0, 0xffu, goff, status, counter, err, okeys,
+                                                         ovals, spin_limit);
+        e = cudaGetLastError();
+    }
+    uint32_t h = 0, d = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&d, g_spin_error, sizeof(d), 0, cudaMemcpyDeviceToHost, s);
+    const uint32_t zero = 0u;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_spin_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+    cudaFreeAsync(w, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *call_flag = h;
+    *device_flag = d;
+    return e;
 }
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* total_dev, Arena& ar,
@@ -490,18 +546,18 @@ cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32
 
 // one-sweep passes while the counts fit the 30-bit status words, reduce-then-scan passes beyond
 cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s) {
+                           int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err) {
     if (n <= 1 || n_bits <= 0) return cudaSuccess;
     if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
-        return onesweep<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+        return onesweep<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, ar, s);
     return radix_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 
 cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s) {
+                           int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err) {
     if (n <= 1 || n_bits <= 0) return cudaSuccess;
     if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
-        return onesweep<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
+        return onesweep<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, ar, s);
     return radix_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 

@@ -136,3 +136,56 @@ def test_visibility_pruning(dv):
     keep = oi.visible_from(keys, center, root, cams, -1.0)
     assert 0 < keep.sum() < len(keys)
     np.testing.assert_array_equal(gpu, keys[keep])
+
+
+@pytest.mark.parametrize("dims,level", [((4.5, 1.9, 1.6), 4), ((0.7, 3.1, 1.2), 5), ((2.0, 2.0, 2.0), 0)])
+def test_asset_init_bit_exact(dv, dims, level):
+    keys, dens, root = dv.dv_asset_init(dims, level)
+    ok, od, oroot, _ = oi.asset_init(np.float32(dims).astype(np.float64), level)  # the ABI carries float32 dims
+    np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint64), ok)
+    np.testing.assert_array_equal(dens.cpu().numpy(), np.float32(od))
+    assert root == oroot
+
+
+def test_asset_init_capacity_and_arguments(dv):
+    import ctypes as C
+    import torch
+    lib = dv.load()
+    ctx = dv.default_context()
+    keys = torch.empty(64, dtype=torch.int64, device="cuda")
+    dens = torch.empty((64, 8), dtype=torch.float32, device="cuda")
+    dims = (C.c_float * 3)(4.5, 1.9, 1.6)
+    root, n = C.c_double(), C.c_int64()
+    launches = dv.dv_launch_count()
+    st = lib.dv_asset_init(ctx.handle, dims, 3, -10.0, 64, C.c_void_p(keys.data_ptr()), C.c_void_p(dens.data_ptr()),
+                           C.byref(root), C.byref(n), None)
+    assert st == dv.DV_ERR_CAPACITY and n.value == 0 and dv.dv_launch_count() == launches
+    bad = (C.c_float * 3)(4.5, 0.0, 1.6)
+    st = lib.dv_asset_init(ctx.handle, bad, 2, -10.0, 64, C.c_void_p(keys.data_ptr()), C.c_void_p(dens.data_ptr()),
+                           C.byref(root), C.byref(n), None)
+    assert st == dv.DV_ERR_INVALID_ARG
+    st = lib.dv_asset_init(ctx.handle, dims, 2, -10.0, 64, C.c_void_p(keys.data_ptr()), C.c_void_p(dens.data_ptr()),
+                           C.byref(root), C.byref(n), None)
+    assert st == dv.DV_OK and n.value == 64
+
+
+def test_asset_init_renders_like_the_oracle(dv):
+    """A GPU-initialised asset placed in a scene renders (GPU) as the oracle renders the oracle's grid."""
+    import oracle
+    from helpers import check_forward, device_scene, gpu_render, orbit, pose64, split_images
+    dims = (4.5, 1.9, 1.6)
+    keys, dens, root = dv.dv_asset_init(dims, 4, v_init=-2.0)   # denser than -10 so the render is visible
+    rng = np.random.default_rng(5)
+    k_np = keys.cpu().numpy().view(np.uint64)
+    sh = np.float32(rng.normal(0.0, 0.1, size=(len(k_np), 16, 3)))
+    act = synth.Octree(k_np, dens.cpu().numpy(), sh, 3, (0.0, 0.0, 0.0), root, role=synth.ACTOR,
+                       clip_half=tuple(0.6 * d for d in dims))
+    bg = synth.grid_octree(3, center=(0.0, 0.0, -4.0), root_size=4.0, rng=rng)
+    scene = synth.Scene([bg, act], [synth.Pose(), synth.Pose(synth.rot_z(0.4), (0.5, 0.2, 0.3))])
+    cam = orbit(48, 40, 50.0, 30.0, dist=9.0)
+    ds = device_scene(scene)
+    rgb, depth, alpha, _ = gpu_render(ds, scene.poses, [cam])
+    o_rgb, o_d, o_a, _ = oracle.render(scene.octrees, scene.poses, cam, oracle.Opts(1, 1e-4))
+    check_forward(split_images(rgb.cpu().numpy(), [cam], 3)[0], split_images(depth.cpu().numpy(), [cam])[0],
+                  split_images(alpha.cpu().numpy(), [cam])[0], o_rgb, o_d, o_a, "asset init render")
+    assert o_a.max() > 0.05

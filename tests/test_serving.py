@@ -103,3 +103,49 @@ def test_poisoned_request_is_rejected_at_admission(dv):
     srv.close()
     assert all(x >= 0 for x in lat)
     assert st["requests"] == 5
+
+
+def test_byte_budget_serialises_large_requests_and_batches_small_ones(dv):
+    """Admission by device memory: with a byte budget below two large requests' charges, two large
+    requests never render at once; small requests still share a batch under the same budget."""
+    sc = small_comp_scene(seed=32, n_actors=2)
+    ds = device_scene(sc)
+    big = synth.orbit_camera(640, 480, 55.0, 2.8, 40.0, 20.0, near=0.1, far=50.0)
+    small = synth.orbit_camera(32, 24, 55.0, 2.8, 40.0, 20.0, near=0.1, far=50.0)
+    opts = dv.make_opts(1, 1e-4)
+    # learn one large request's charge (the first batch also calibrates the memory model)
+    probe = dv.Server(ds, max_views=8, n_workers=2, max_batch_pixels=10 ** 8, max_inflight_pixels=10 ** 9, opts=opts)
+    t = probe.submit(big, sc.poses, _outputs(big))
+    probe.wait(t, 60000.0)
+    t = probe.submit(big, sc.poses, _outputs(big))
+    probe.wait(t, 60000.0)
+    b_big = probe.memory()["last_request_bytes"]
+    t = probe.submit(small, sc.poses, _outputs(small))
+    probe.wait(t, 60000.0)
+    b_small = probe.memory()["last_request_bytes"]
+    probe.close()
+    assert b_big > 4 * b_small > 0
+    budget = int(1.5 * b_big)
+    srv = dv.Server(ds, max_views=8, n_workers=2, max_batch_pixels=10 ** 8, max_inflight_pixels=10 ** 9, opts=opts,
+                    max_inflight_bytes=budget)
+    # calibrate the fresh server's model, then queue everything while admission is held
+    t = srv.submit(big, sc.poses, _outputs(big))
+    srv.wait(t, 60000.0)
+    srv.memory(reset_peak=True)           # the calibration request ran alone, charged by the starting model
+    srv.pause(True)
+    tickets = [srv.submit(big, sc.poses, _outputs(big)) for _ in range(3)]
+    srv.pause(False)
+    for t in tickets:
+        srv.wait(t, 60000.0)
+    mem = srv.memory()
+    assert mem["peak_inflight_bytes"] <= budget               # two large requests were never in flight together
+    b0 = srv.stats()["batches"]
+    srv.pause(True)
+    tickets = [srv.submit(small, sc.poses, _outputs(small)) for _ in range(6)]
+    srv.pause(False)
+    for t in tickets:
+        srv.wait(t, 60000.0)
+    st = srv.stats()
+    srv.close()
+    assert st["max_batch"] >= 2                               # the small requests shared batches
+    assert st["batches"] - b0 < 6
