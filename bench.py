@@ -42,13 +42,20 @@ METRIC = "Mpix/s fwd & fwd+bwd; served p50/p99 latency vs plain path, 1 GB300"
 WORKLOAD = ("compositional fwd+bwd: LiDAR-shaped background 500k leaves (levels 6-12, 200 m root) + 3 actors x "
             "20k leaves on straight lanes, SH degree 3, one 1920x1080 camera, K=1, eps_stop=1e-4")
 
-# FP32 operations per algorithmic unit, counted from the kernel source (FMA = 2)
-F_TEST = 23          # voxel slab test (per pixel x list entry examined)
-F_BOX = 50           # actor clip-box test (per pixel x box query)
-F_SAMPLE = 39        # one midpoint sample: position, trilinear (7 lerps), activation
-F_SEG = 23           # per segment: clipping, alpha, composite update, stop test
-F_SAMPLE_BWD = 75    # sample + trilinear weights and d tau / d dens
-F_SEG_BWD = 128      # segment + gradient of tau and colour, share of the warp reduction
+# Algorithmic FP32 operations per unit of the method (FMA = 2, exponential = 1), not counted from the
+# kernels: a ray-box slab test 20 (per pixel x listed voxel, and per pixel x actor clip box); per
+# composited segment K samples of 31 (position, trilinear interpolation of 8 corners, activation)
+# plus 16 (alpha, transmittance, the colour and depth accumulation).  The backward replays the
+# forward's arithmetic (it needs every segment's transmittance and prefix sums) and adds, per sample,
+# 35 (the 8 trilinear weights, the activation's derivative, d tau / d corner) and per segment 43
+# (dL/d tau from the upstream gradients and the suffix sums, the chain to the 8 corners and the 3
+# colour channels, and the 11 additions into the per-voxel gradient sums).
+F_TEST = 20
+F_BOX = 20
+F_SAMPLE = 31
+F_SEG = 16
+F_SAMPLE_BWD = F_SAMPLE + 35
+F_SEG_BWD = F_SEG + 43
 
 
 def log(*a):
@@ -70,6 +77,13 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate and path")
     p.add_argument("--serve-rates", default="200,500,1000,2000")
+    p.add_argument("--profile-pass", action="store_true",
+                   help="no timing: one warm-up and one profiled pass of every row on the 1080p frame, for a "
+                        "counter capture (prints the library's launch counts of both passes)")
+    p.add_argument("--traffic-from", default=None,
+                   help="build profiles/traffic.json and a table from an ncu --csv capture of --profile-pass")
+    p.add_argument("--large", default="cfg3,cfg5",
+                   help="larger scenes timed after the headline (comma list of cfg3, cfg5; empty: none)")
     return p.parse_args()
 
 
@@ -173,31 +187,53 @@ def stage_models(stats, work, n_vox_total, n_pix, K, sh_bytes_per_vox, key_bits)
         "ranges": ("hbm", P * 4 + T * 8),
         "composite_fwd": ("alu", tests * F_TEST + boxes * F_BOX + segs * (K * F_SAMPLE + F_SEG)),
         "composite_bwd": ("alu", tests * F_TEST + boxes * F_BOX + segs * (K * F_SAMPLE_BWD + F_SEG_BWD)),
+        # the same kernels' algorithmic DRAM bytes: per pair the voxel payload (densities 32, colour 12,
+        # key 8) read once per tile, per pixel 20 B of images and 8 B of saved state; the backward also
+        # reads the 20 B of upstream gradients per pixel and adds into 44 B of gradient per visible voxel
+        "composite_fwd_bytes": ("hbm", P * 52 + n_pix * 28),
+        "composite_bwd_bytes": ("hbm", P * 52 + n_pix * 48 + nv * 88),
         "sh_bwd": ("hbm", nv * (48 + 16 + sh_bytes_per_vox + 64 + 2 * sh_bytes_per_vox + 4)),
     }
 
 
-# the sources that decide the compositing kernels' DRAM traffic: the kernels themselves, the
-# record layout and the kernel that writes the records
-TRAFFIC_SOURCES = ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")
+# Stages (the library's profiler names) and the other rows, with the kernels that make them up and the
+# sources that decide their DRAM traffic; a stage's traffic figure is kept only while those sources are
+# unchanged.
+STAGE_KERNELS = {
+    "project": (("k_project", "k_publish"), ("dv_project.cu", "dv_internal.cuh")),
+    "scan": (("k_scan_reduce", "k_scan_top", "k_scan_down"), ("dv_scan_sort.cu", "dv_internal.cuh")),
+    "compact": (("k_compact",), ("dv_project.cu", "dv_internal.cuh")),
+    "sort_vox": (("k_os_hist<unsigned long>", "k_os_bins@u64", "k_os_pass<unsigned long"),
+                 ("dv_scan_sort.cu", "dv_internal.cuh")),
+    "records": (("k_records", "k_vis_start"), ("dv_project.cu", "dv_internal.cuh")),
+    "emit": (("k_emit",), ("dv_project.cu", "dv_internal.cuh")),
+    "sort_pairs": (("k_os_hist<unsigned int>", "k_os_bins@u32", "k_os_pass<unsigned int"),
+                   ("dv_scan_sort.cu", "dv_internal.cuh")),
+    "ranges": (("k_pair_mask", "k_tile_count", "k_tile_offsets", "k_tile_scatter"),
+               ("dv_project.cu", "dv_internal.cuh")),
+    "composite_fwd": (("k_composite<0",), ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")),
+    "composite_bwd": (("k_composite<1",), ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")),
+    "sh_bwd": (("k_sh_bwd",), ("dv_composite.cu", "dv_internal.cuh")),
+}
 
 
-def kernel_source_hash():
+def sources_hash(files):
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2606_23031_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel):
+def load_traffic(stage):
+    """DRAM bytes per launch of a stage from the committed ncu capture, or None once its sources changed."""
     try:
         t = json.load(open(TRAFFIC))
+        e = t["stages"][stage]
     except Exception:
         return None
-    if t.get("source_hash") != kernel_source_hash():
+    if e.get("source_hash") != sources_hash(STAGE_KERNELS[stage][1]):
         return None
-    v = t.get("per_launch_bytes", {}).get(kernel)
-    return v
+    return e.get("bytes_per_launch")
 
 
 def peaks():
@@ -349,6 +385,84 @@ def serving_bench(args, dv, opts):
             "rates": rows}
 
 # ---------------------------------------------------------------------------
+# the larger scenes: 8M-leaf background + 20 actors and 32M + 64 actors, six surround cameras in one call
+# ---------------------------------------------------------------------------
+
+LARGE = {
+    "cfg3": ("full frame: LiDAR-shaped background 8M leaves (levels 6-14, 200 x 200 x 30 m) + 20 actors of 20k-60k "
+             "leaves, 6 surround cameras 1920x1080 in one call, K=1, eps_stop=1e-4"),
+    "cfg5": ("stress: LiDAR-shaped background 32M leaves (levels 6-16, 500 x 500 x 40 m) + 64 actors of 40k leaves, "
+             "6 surround cameras 3840x2160 in one call, K=1, eps_stop=1e-4"),
+}
+
+
+def large_scene_bench(args, dv, dev, which, alu_peak, pk, flush):
+    """Forward and forward+backward Mpix/s of one render call over all six cameras of a large scene, with
+    the compositing kernels' roofline (CUDA events around each stage, separate runs)."""
+    import torch
+    import synth
+    t0 = time.perf_counter()
+    sc, cams = synth.config3(args.seed) if which == "cfg3" else synth.config5(args.seed)
+    t_gen = time.perf_counter() - t0
+    ds = [dv.DeviceOctree.from_host(o, dev) for o in sc.octrees]
+    opts = dv.make_opts(1, 1e-4)
+    ctx = dv.default_context(dev.index)
+    stream = torch.cuda.current_stream()
+    n_pix = sum(c.W * c.H for c in cams)
+    g = torch.Generator(device=dev).manual_seed(args.seed + 23)
+    g_rgb = torch.randn((n_pix, 3), generator=g, device=dev)
+    g_d = 0.01 * torch.randn((n_pix,), generator=g, device=dev)
+    g_a = torch.randn((n_pix,), generator=g, device=dev)
+    d_dens = [torch.zeros_like(o.dens) for o in ds]
+    d_sh = [torch.zeros_like(o.sh) for o in ds]
+
+    def step(bwd):
+        out = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=bwd)
+        if bwd:
+            dv.dv_render_backward(out[-1], g_rgb, g_d, g_a, d_dens, d_sh)
+            out[-1].free()
+
+    step(True)
+    torch.cuda.synchronize()
+    _, _, _, st = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
+    stats, work = st.stats(-1), st.work(-1)
+    st.free()
+    n = 3 if which == "cfg3" else 2
+    res = {"workload": LARGE[which], "pixels_per_step": n_pix, "visible_voxels": stats["n_visible"],
+           "pairs": stats["n_pairs"], "work": work, "generate_s": t_gen, "steps": n}
+    for bwd, key in ((False, "fwd"), (True, "fwd_bwd")):
+        ms = 0.0
+        for _ in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(bwd)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        res[key] = {"value": n_pix / (ms / n * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms / n}
+    ctx.profile(True, stages=["composite_fwd", "composite_bwd"])
+    ctx.profile_read()
+    for _ in range(n):
+        flush.zero_()
+        step(True)
+    torch.cuda.synchronize()
+    pr = ctx.profile_read()
+    ctx.profile(False)
+    K = 1
+    tests, boxes, segs = work["tests"], work["box_tests"], work["segments"]
+    for kname, per_seg in (("composite_fwd", K * F_SAMPLE + F_SEG), ("composite_bwd", K * F_SAMPLE_BWD + F_SEG_BWD)):
+        ms_k = pr[kname][0] / max(pr[kname][1], 1)
+        flops = tests * F_TEST + boxes * F_BOX + segs * per_seg
+        res[kname] = {"ms_per_run": ms_k, "algorithmic_flops": flops,
+                      "achieved_tflops": flops / (ms_k * 1e-3) / 1e12,
+                      "frac": flops / (ms_k * 1e-3) / 1e12 / alu_peak, "bound": "alu"}
+    del ds, d_dens, d_sh
+    torch.cuda.empty_cache()
+    return res
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -403,7 +517,22 @@ def run_ours(args):
 
     # ---- per-stage split, outside the timed region: every stage bracketed by events ----
     pk = peaks()
-    alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s, FP32 FMA issue at max clock
+    # the FP32 FMA peak, measured here on this device (dv_measure_fp32_fma: dependent-FMA chains on every SM),
+    # with the SM clock sampled while it runs
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_p = ClockSampler(local)
+    clk_p.start()
+    time.sleep(0.3)
+    f_peak, ms_peak = 0.0, 0.0
+    for _ in range(3):
+        f, m_ = dv.dv_measure_fp32_fma(local, 8192, 20)
+        f_peak, ms_peak = f_peak + f, ms_peak + m_
+    clk_peak = clk_p.stop()
+    alu_peak = f_peak / (ms_peak * 1e-3) / 1e12   # TFLOP/s
+    alu_peak_src = (f"measured: dv_measure_fp32_fma on {n_sm} SMs ({f_peak:.3g} FP32 ops in {ms_peak:.1f} ms, "
+                    f"8 dependent-FMA chains per thread, full occupancy), SM clock median "
+                    f"{(clk_peak or {}).get('sm_mhz')} MHz; nominal {n_sm} SMs x 128 lanes x 2 x "
+                    f"{pk['sm_max_mhz']:.0f} MHz = {n_sm * 256 * pk['sm_max_mhz'] * 1e-6:.1f} TFLOP/s")
     sh_bytes = sum(o.n * (o.sh_degree + 1) ** 2 * 12 for o in sc.octrees) / max(sum(o.n for o in sc.octrees), 1)
     max_level = max(int((np.asarray(o.key, np.uint64) >> np.uint64(57)).max()) for o in sc.octrees if o.n)
     key_bits = 3 * max_level + max(1, math.ceil(math.log2(len(sc.octrees))))
@@ -678,6 +807,14 @@ def run_ours(args):
                 ach = amount / (avg * 1e-3) / 1e12
                 ent.update({"bound": "alu", "algorithmic_flops": amount, "achieved_tflops": ach,
                             "frac": ach / alu_peak})
+                if name + "_bytes" in models:
+                    # the compositing kernels also move DRAM bytes: their fraction of the copy bandwidth
+                    b = models[name + "_bytes"][1]
+                    ent.update({"algorithmic_bytes": b, "achieved_gbs": b / (avg * 1e-3) / 1e9,
+                                "hbm_frac": b / (avg * 1e-3) / 1e9 / pk["hbm_gbs"]})
+        tr = load_traffic(name)
+        if tr is not None:
+            ent["traffic"] = tr
         kernels[name] = ent
     d = kernels[dom]
     if d["bound"] == "hbm":
@@ -686,12 +823,18 @@ def run_ours(args):
                 "peak_source": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback"}
     else:
         roof = {"bound": "alu", "achieved": d["achieved_tflops"], "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": d["frac"], "traffic": load_traffic(dom), "kernel": dom,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
+                "frac": d["frac"], "traffic": load_traffic(dom), "kernel": dom, "peak_source": alu_peak_src,
+                "hbm_frac": d.get("hbm_frac"), "hbm_peak_gbs": pk["hbm_gbs"]}
 
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_bench(args, dv, opts)
+
+    large = {}
+    if not args.core_only:
+        for which in [x for x in args.large.split(",") if x]:
+            large[which] = large_scene_bench(args, dv, dev, which, alu_peak, pk, flush)
+            log(which, json.dumps(large[which]))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -717,7 +860,7 @@ def run_ours(args):
                     "value": whole_job_mpix_s(world, n_pix, ms_nrm), "unit": "Mpix/s", "ms_per_step": ms_nrm,
                     "what": "fwd+bwd also rendering the normal state N and back-propagating a gradient on it"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
-                "serving": serving,
+                "serving": serving, "large": large or None,
                 "gpu_launches_per_step": launches / max(args.steps, 1), "wall_s_timed": wall,
                 "work": work, "kernels": kernels,
                 "kernels_source": (f"{dom}: CUDA events around it in every timed step; the other stages: "
@@ -729,8 +872,153 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# counter capture: one profiled pass of every row, and the table built from it
+# ---------------------------------------------------------------------------
+
+def run_profile_pass(args):
+    """No timing.  One warm-up pass and one profiled pass over every row on the 1080p frame (fwd+bwd,
+    fwd+bwd with normals, the sky composite and its backward, the weights export with a 64-channel feature
+    render and fusion, the initialisation calls, an asset grid), so that a counter capture of the library's
+    kernels can skip the first pass by count.  Prints the library's launches of each pass."""
+    import numpy as np
+    import torch
+    import paper_2606_23031_gb300 as dv
+    import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    dv.load()
+    sc, cams, _ = workload(args.seed)
+    cam = cams[0]
+    ds = [dv.DeviceOctree.from_host(o, dev) for o in sc.octrees]
+    opts = dv.make_opts(1, 1e-4)
+    ctx = dv.default_context(0)
+    g_rgb, g_d, g_a = upstream(cam, args.seed, dev)
+    n_pix = cam.W * cam.H
+    g_n = torch.randn((n_pix, 3), generator=torch.Generator(dev).manual_seed(args.seed + 7), device=dev)
+    d_dens = [torch.zeros_like(o.dens) for o in ds]
+    d_sh = [torch.zeros_like(o.sh) for o in ds]
+    env = torch.rand((1024, 2048, 3), generator=torch.Generator(dev).manual_seed(args.seed + 9), device=dev)
+    nv = sum(o.n for o in sc.octrees)
+    fe = torch.randn((nv, 64), generator=torch.Generator(dev).manual_seed(args.seed + 11), device=dev)
+    f2 = torch.randn((n_pix, 64), generator=torch.Generator(dev).manual_seed(args.seed + 12), device=dev)
+    acc = torch.zeros((nv, 64), device=dev)
+    rng_i = np.random.default_rng(args.seed + 13)
+    lay = synth.city_layout(rng_i, 100.0, 30.0, 20)
+    cloud = torch.as_tensor(np.float32(synth.lidar_points(rng_i, lay, 1_000_000, 400_000)), device=dev)
+    bg = sc.octrees[0]
+    kt = torch.as_tensor(np.asarray(bg.key, np.uint64).view(np.int64), device=dev)
+    L = int((np.asarray(bg.key, np.uint64) >> np.uint64(57)).max())
+    s_min = float(bg.root_size) / 2 ** L
+    sky_out = torch.empty((n_pix, 3), device=dev)
+    d_env = torch.zeros_like(env)
+    d_alpha = torch.zeros((n_pix,), device=dev)
+
+    def one_pass():
+        rgb, depth, alpha, st = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True)
+        dv.dv_render_backward(st, g_rgb, g_d, g_a, d_dens, d_sh)
+        out = dv.dv_render(ds, sc.poses, cams, opts, ctx=ctx, save_state=True, normals=True)
+        dv.dv_render_backward(out[-1], g_rgb, g_d, g_a, d_dens, d_sh, d_normal=g_n)
+        dv.dv_sky_composite(cams, env, rgb, alpha, ctx=ctx, out=sky_out)
+        dv.dv_sky_backward(cams, env, alpha, g_rgb, d_env, d_alpha, ctx=ctx)
+        w = dv.dv_state_weights(st)
+        dv.dv_features_render(w, fe, ctx=ctx)
+        dv.dv_features_fuse(w, f2, acc, ctx=ctx)
+        grid_c, index_c = dv.dv_shared_corners(kt, L, ctx=ctx)
+        dv.dv_soft_prior(grid_c, bg.center, bg.root_size, L, cloud, s_min, ctx=ctx)
+        dv.dv_subdivide_round(kt, L, bg.center, bg.root_size, cloud, s_min, ctx=ctx)
+        dv.dv_visibility_prune(kt, L, bg.center, bg.root_size, cams, 0.0, ctx=ctx)
+        dv.dv_asset_init((4.5, 1.9, 1.6), 6, ctx=ctx)
+        torch.cuda.synchronize()
+        st.free()
+        out[-1].free()
+
+    dv.dv_launch_count(True)
+    one_pass()
+    warm = dv.dv_launch_count(True)
+    one_pass()
+    prof = dv.dv_launch_count(True)
+    print(f"LAUNCHES {warm} {prof}", flush=True)
+    return 0
+
+
+def build_traffic(csv_path):
+    """profiles/traffic.json and a markdown table (stdout) from an ncu --csv capture of one profiled pass
+    (metrics dram__bytes_read.sum, dram__bytes_write.sum, gpu__time_duration.sum)."""
+    import csv
+    rows = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        k = r["ID"]
+        e = rows.setdefault(k, {"id": int(k), "name": r["Kernel Name"], "m": {}})
+        v = r["Metric Value"].replace(",", "")
+        unit = r.get("Metric Unit", "")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "nsecond": 1e-3, "us": 1.0,
+                 "usecond": 1.0, "ms": 1e3, "msecond": 1e3}.get(unit, 1.0)
+        try:
+            e["m"][r["Metric Name"]] = float(v) * scale
+        except ValueError:
+            pass
+    launches = sorted(rows.values(), key=lambda e: e["id"])
+    # stage of every launch; k_os_bins belongs to the sort whose histogram came just before it
+    stage_of = []
+    last_sort = None
+    for e in launches:
+        st = None
+        for sname, (kernels, _) in STAGE_KERNELS.items():
+            for kn in kernels:
+                if "@" in kn:
+                    continue
+                if kn in e["name"]:
+                    st = sname
+        if "k_os_bins" in e["name"]:
+            st = last_sort
+        if "k_os_hist" in e["name"]:
+            last_sort = st
+        stage_of.append(st)
+    # the profiled pass renders the frame twice (plain, then with normals): the stages of the plain
+    # frame are its first occurrence of each stage until the first composite_bwd and sh_bwd
+    stages = {}
+    seen_sh = False
+    for e, st in zip(launches, stage_of):
+        if st is None or seen_sh:
+            continue
+        rec = stages.setdefault(st, {"bytes": 0.0, "us": 0.0, "kernels": []})
+        rec["bytes"] += e["m"].get("dram__bytes_read.sum", 0.0) + e["m"].get("dram__bytes_write.sum", 0.0)
+        rec["us"] += e["m"].get("gpu__time_duration.sum", 0.0)
+        rec["kernels"].append(e["name"].split("(")[0])
+        if st == "sh_bwd":
+            seen_sh = True
+    per_kernel = {}
+    for e in launches:
+        nm = e["name"].split("(")[0]
+        d = per_kernel.setdefault(nm, {"launches": 0, "bytes": 0.0, "us": 0.0})
+        d["launches"] += 1
+        d["bytes"] += e["m"].get("dram__bytes_read.sum", 0.0) + e["m"].get("dram__bytes_write.sum", 0.0)
+        d["us"] += e["m"].get("gpu__time_duration.sum", 0.0)
+    out = {"source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                     "--clock-control none -k regex:k_ -s <warm-up launches> -c <pass launches> --csv "
+                     "python bench.py --profile-pass (one pass of every row on the 1920x1080 frame)",
+           "stages": {st: {"bytes_per_launch": int(r["bytes"]), "us_ncu": r["us"],
+                           "source_hash": sources_hash(STAGE_KERNELS[st][1]), "kernels": r["kernels"]}
+                      for st, r in stages.items()},
+           "kernels": per_kernel}
+    with open(TRAFFIC, "w") as f:
+        json.dump(out, f, indent=1)
+    print("| kernel | launches | DRAM bytes (read + write) | ncu time (us, serialised) |")
+    print("|---|---|---|---|")
+    for nm, d in sorted(per_kernel.items(), key=lambda kv: -kv[1]["us"]):
+        print(f"| `{nm}` | {d['launches']} | {d['bytes'] / 1e6:.2f} MB | {d['us']:.1f} |")
+    return 0
+
+
 def main():
     args = parse()
+    if args.traffic_from:
+        return build_traffic(args.traffic_from)
+    if args.profile_pass:
+        return run_profile_pass(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -371,14 +371,15 @@ def lidar_background(n_target: int, seed: int, root_size=200.0, center=(0.0, 0.0
     def pack(ijk):
         return (ijk[:, 2] << 42) | (ijk[:, 1] << 21) | ijk[:, 0]
 
-    # occupied cells per level, derived from the finest level by integer halving
+    # occupied cells per level, derived from the finest level by integer halving of the packed keys
+    # (each 21-bit field shifted right by one: the bit that crosses into the next field is cleared)
     sf = root_size / (1 << level_max)
     pc = np.floor((pts - rmin) / sf).astype(np.int64)
     pc = pc[(pc >= 0).all(1) & (pc < (1 << level_max)).all(1)]
-    occ_cells = {level_max: np.unique(pc, axis=0)}
+    occ_keys = {level_max: _unique_sorted(pack(pc))}
+    halve = ~np.int64((1 << 20) | (1 << 41))
     for lv in range(level_max - 1, level_min - 1, -1):
-        occ_cells[lv] = np.unique(occ_cells[lv + 1] >> 1, axis=0)
-    occ_keys = {lv: _unique_sorted(pack(c)) for lv, c in occ_cells.items()}
+        occ_keys[lv] = _unique_sorted((occ_keys[lv + 1] >> 1) & halve)
 
     s0 = root_size / (1 << level_min)
     n0 = 1 << level_min
