@@ -179,12 +179,11 @@ def stage_models(stats, work, n_vox_total, n_pix, K, sh_bytes_per_vox, key_bits)
     tb = max(1, math.ceil(math.log2(max(T, 2)) / 8))
     tests, boxes, segs = work["tests"], work["box_tests"], work["segments"]
     return {
-        "project": ("hbm", V * 32),
-        "records": ("hbm", nv * (4 + 8 + 32 + sh_bytes_per_vox + 4 + 8 + 64 + 4 + 8)),
-        "emit": ("hbm", nv * 16 + P * 8),
-        "sort_vox": ("hbm", vb * nv * 32),
-        "sort_pairs": ("hbm", tb * P * 20),
-        "ranges": ("hbm", P * 4 + T * 8),
+        "project": ("hbm", V * 32 + nv * 24),
+        "records": ("hbm", nv * (4 + 8 + 4 + 8 + 32 + sh_bytes_per_vox + 64 + 8) + P * 8),
+        "sort_vox": ("hbm", vb * nv * 24),
+        "sort_pairs": ("hbm", tb * P * 16),
+        "ranges": ("hbm", P * (4 + 4 + 8 + 1) + T * 12),
         "composite_fwd": ("alu", tests * F_TEST + boxes * F_BOX + segs * (K * F_SAMPLE + F_SEG)),
         "composite_bwd": ("alu", tests * F_TEST + boxes * F_BOX + segs * (K * F_SAMPLE_BWD + F_SEG_BWD)),
         # the same kernels' algorithmic DRAM bytes: per pair the voxel payload (densities 32, colour 12,
@@ -200,17 +199,11 @@ def stage_models(stats, work, n_vox_total, n_pix, K, sh_bytes_per_vox, key_bits)
 # sources that decide their DRAM traffic; a stage's traffic figure is kept only while those sources are
 # unchanged.
 STAGE_KERNELS = {
-    "project": (("k_project", "k_publish"), ("dv_project.cu", "dv_internal.cuh")),
-    "scan": (("k_scan_reduce", "k_scan_top", "k_scan_down"), ("dv_scan_sort.cu", "dv_internal.cuh")),
-    "compact": (("k_compact",), ("dv_project.cu", "dv_internal.cuh")),
-    "sort_vox": (("k_os_hist<unsigned long>", "k_os_bins@u64", "k_os_pass<unsigned long"),
-                 ("dv_scan_sort.cu", "dv_internal.cuh")),
-    "records": (("k_records", "k_vis_start"), ("dv_project.cu", "dv_internal.cuh")),
-    "emit": (("k_emit",), ("dv_project.cu", "dv_internal.cuh")),
-    "sort_pairs": (("k_os_hist<unsigned int>", "k_os_bins@u32", "k_os_pass<unsigned int"),
-                   ("dv_scan_sort.cu", "dv_internal.cuh")),
-    "ranges": (("k_pair_mask", "k_tile_count", "k_tile_offsets", "k_tile_scatter"),
-               ("dv_project.cu", "dv_internal.cuh")),
+    "project": (("k_project",), ("dv_project.cu", "dv_internal.cuh")),
+    "sort_vox": (("k_os_pass<unsigned long",), ("dv_scan_sort.cu", "dv_internal.cuh")),
+    "records": (("k_records_emit",), ("dv_project.cu", "dv_internal.cuh")),
+    "sort_pairs": (("k_os_pass<unsigned int",), ("dv_scan_sort.cu", "dv_internal.cuh")),
+    "ranges": (("k_pair_mask", "k_tile_order"), ("dv_project.cu", "dv_internal.cuh")),
     "composite_fwd": (("k_composite<0",), ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")),
     "composite_bwd": (("k_composite<1",), ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")),
     "sh_bwd": (("k_sh_bwd",), ("dv_composite.cu", "dv_internal.cuh")),
@@ -961,21 +954,13 @@ def build_traffic(csv_path):
         except ValueError:
             pass
     launches = sorted(rows.values(), key=lambda e: e["id"])
-    # stage of every launch; k_os_bins belongs to the sort whose histogram came just before it
+    # stage of every launch
     stage_of = []
-    last_sort = None
     for e in launches:
         st = None
         for sname, (kernels, _) in STAGE_KERNELS.items():
-            for kn in kernels:
-                if "@" in kn:
-                    continue
-                if kn in e["name"]:
-                    st = sname
-        if "k_os_bins" in e["name"]:
-            st = last_sort
-        if "k_os_hist" in e["name"]:
-            last_sort = st
+            if any(kn in e["name"] for kn in kernels):
+                st = sname
         stage_of.append(st)
     # the profiled pass renders the frame twice (plain, then with normals): the stages of the plain
     # frame are its first occurrence of each stage until the first composite_bwd and sh_bwd

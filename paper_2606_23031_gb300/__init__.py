@@ -31,8 +31,7 @@ DV_OK, DV_ERR_INVALID_ARG, DV_ERR_INVALID_POSE, DV_ERR_CAPACITY, DV_ERR_CUDA, DV
 DV_ROLE_BG, DV_ROLE_ACTOR = 0, 1
 DV_ACT_EXPLIN, DV_ACT_IDENTITY = 0, 1
 DV_MAX_OCTREES = 128
-KERNELS = ("project", "scan", "compact", "sort_vox", "records", "emit", "sort_pairs", "ranges", "composite_fwd",
-           "composite_bwd", "sh_bwd")
+KERNELS = ("project", "sort_vox", "records", "sort_pairs", "ranges", "composite_fwd", "composite_bwd", "sh_bwd")
 
 
 def _nvcc():
@@ -360,9 +359,15 @@ class DeviceOctree:
         return DeviceOctree(key, dens, sh, oc.sh_degree, oc.center, oc.root_size, oc.role, oc.clip_half, ml)
 
     def struct(self, dens=None, sh=None) -> dv_octree:
-        o = dv_octree()
         d = self.dens if dens is None else dens
         s = self.sh if sh is None else sh
+        # the struct of the octree's own tensors is kept (with the tensors, so their ids stay theirs)
+        own = dens is None and sh is None
+        if own:
+            c = getattr(self, "_struct", None)
+            if c is not None and c[0] is self.key and c[1] is d and c[2] is s:
+                return c[3]
+        o = dv_octree()
         for t in (self.key, d, s):
             if t.numel() and (not t.is_cuda or not t.is_contiguous()):
                 raise ValueError("octree tensors must be contiguous CUDA tensors")
@@ -377,19 +382,17 @@ class DeviceOctree:
         o.key = self.key.data_ptr() if self.n else None
         o.dens = d.data_ptr() if self.n else None
         o.sh = s.data_ptr() if self.n else None
+        if own:
+            self._struct = (self.key, d, s, o)
         return o
 
 
 def make_pose(p) -> dv_pose:
     import numpy as np
-    P = dv_pose()
-    R = np.asarray(p.R, np.float32).reshape(9)
-    t = np.asarray(p.t, np.float32).reshape(3)
-    for i in range(9):
-        P.R[i] = float(R[i])
-    for i in range(3):
-        P.t[i] = float(t[i])
-    return P
+    buf = np.empty(12, np.float32)
+    buf[:9] = np.asarray(p.R, np.float32).reshape(9)
+    buf[9:] = np.asarray(p.t, np.float32).reshape(3)
+    return dv_pose.from_buffer_copy(buf)
 
 
 def make_camera(cam) -> dv_camera:
@@ -409,8 +412,12 @@ def make_opts(K=1, eps_stop=1e-4, activation=DV_ACT_EXPLIN) -> dv_opts:
 
 def _stream_ptr(stream=None):
     import torch
-    s = torch.cuda.current_stream() if stream is None else stream
-    return C.c_void_p(s.cuda_stream)
+    if stream is None:
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)  # the current stream's handle, cheaply
+        if raw is not None:
+            return C.c_void_p(raw(torch.cuda.current_device()))
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
 
 
 # ---------------------------------------------------------------------------
@@ -470,10 +477,12 @@ def dv_render(octrees, poses, cams, opts=None, *, ctx: Context | None = None, sa
     P = sum(int(c.W) * int(c.H) for c in cams)
     dev = torch.device("cuda", ctx.device)
     if out is None:
-        rgb = torch.empty((P, 3), device=dev, dtype=torch.float32)
-        depth = torch.empty((P,), device=dev, dtype=torch.float32)
-        alpha = torch.empty((P,), device=dev, dtype=torch.float32)
-        normal = torch.empty((P, 3), device=dev, dtype=torch.float32) if normals else None
+        # one allocation, viewed as the output images
+        buf = torch.empty((P * (8 if normals else 5),), device=dev, dtype=torch.float32)
+        rgb = buf[:3 * P].view(P, 3)
+        depth = buf[3 * P:4 * P]
+        alpha = buf[4 * P:5 * P]
+        normal = buf[5 * P:].view(P, 3) if normals else None
     else:
         rgb, depth, alpha = out[:3]
         normal = out[3] if normals else None

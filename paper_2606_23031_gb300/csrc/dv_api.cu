@@ -19,11 +19,10 @@
 
 namespace {
 
-const char* const kKernelNames[] = {"project", "scan",        "compact",       "sort_vox",      "records", "emit",
-                                    "sort_pairs", "ranges", "composite_fwd", "composite_bwd", "sh_bwd"};
+const char* const kKernelNames[] = {"project", "sort_vox", "records", "sort_pairs", "ranges", "composite_fwd",
+                                    "composite_bwd", "sh_bwd"};
 constexpr int kNK = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
-enum { KP_PROJECT, KP_SCAN, KP_COMPACT, KP_SORT_VOX, KP_RECORDS, KP_EMIT, KP_SORT_PAIRS, KP_RANGES, KP_FWD, KP_BWD,
-       KP_SHBWD };
+enum { KP_PROJECT, KP_SORT_VOX, KP_RECORDS, KP_SORT_PAIRS, KP_RANGES, KP_FWD, KP_BWD, KP_SHBWD };
 
 struct ProfRec {
     int k;
@@ -104,10 +103,12 @@ struct dv_ctx {
     dv::Fork fork;          // extra streams and events of the three-launch compositing passes
     int64_t budget = 0;     // bytes one call may take from the pool (0: no limit), set by dv_reserve
     int64_t last_need = 0;  // bytes the last render call needed (or the part known when it failed)
-    uint64_t* h_scalars = nullptr;  // pinned, mapped: [0] n_vis, [1] n_pairs, [2] flags
+    uint64_t* h_scalars = nullptr;  // pinned, mapped: [0] n_vis, [1] n_pairs, [2] flags, [3] call number
     uint64_t* h_scalars_dev = nullptr;  // the same host words as the device sees them
-    uint64_t* d_scalars = nullptr;  // device counters
-    cudaEvent_t ev_sizes = nullptr;  // the scalars have reached the host
+    uint64_t* d_scalars = nullptr;  // device counters [4] (the projection's), then the depth keys' digit counts [8][256] u32
+    uint64_t size_seq = 0;           // render calls so far: the projection writes it into h_scalars[3] last
+    char* h_stage = nullptr;         // pinned staging buffer of the per-call view and octree constants
+    size_t stage_cap = 0;
     uint32_t* d_spin_err = nullptr;  // the device's wait-error word
     bool profiling = false;
     uint32_t prof_mask = ~0u;  // stages bracketed by events while profiling (bit k: stage k)
@@ -473,31 +474,153 @@ T* pool_alloc(dv_ctx* ctx, cudaStream_t s, size_t count, std::vector<void*>& own
 
 int64_t rounded(int64_t bytes) { return ((std::max<int64_t>(bytes, 16) + 511) / 512) * 512; }
 
-// one-sweep radix sort scratch of n keys on n_bits (at most one tile per 256 keys)
-int64_t sort_need(int64_t n, int n_bits) {
-    const int64_t passes = (n_bits + 7) / 8;
-    const int64_t tiles = (n + 255) / 256;
-    return rounded(4 * (passes * (256 + 1 + tiles * 256) + 1));
+// Buffers carved out of one pool allocation, each starting on a 512-byte boundary.  A part
+// registered with a null destination only counts toward the size.
+struct Layout {
+    struct Part {
+        void** p;
+        int64_t off;
+    };
+    std::vector<Part> parts;
+    int64_t bytes = 0;
+    template <typename T>
+    void add(T** p, int64_t count) {
+        if (p) parts.push_back({reinterpret_cast<void**>(p), bytes});
+        bytes += rounded(count * (int64_t)sizeof(T));
+    }
+    void place(void* base) {
+        for (const Part& q : parts) *q.p = static_cast<char*>(base) + q.off;
+    }
+};
+
+// The four blocks of one render call.  Kept in the saved state: (1) what is known before any work
+// is enqueued, (3) what the projection's sizes fix.  Scratch released at the end of the call: (2)
+// the projection's per-(view, voxel) arrays and the depth sort's input, (4) the sorts' other
+// buffers, the pairs before their sort, and the zero-initialised counters and look-back words.
+struct StateBuffers0 {
+    ViewParams* views = nullptr;
+    OctParams* octs = nullptr;
+    uint32_t* n_seg = nullptr;
+    float* t_final = nullptr;
+    uint2* range = nullptr;
+    uint32_t* vis_start = nullptr;
+    uint32_t* tile_order = nullptr;
+    unsigned long long* work = nullptr;  // [0..3] work counters, [4] the call's sort flag
+};
+
+Layout state0_layout(int64_t n_view, int64_t n_oct, int64_t tiles, int64_t pix, StateBuffers0* b) {
+    Layout L;
+    L.add(b ? &b->views : nullptr, n_view);
+    L.add(b ? &b->octs : nullptr, n_view * n_oct);
+    L.add(b ? &b->n_seg : nullptr, pix);
+    L.add(b ? &b->t_final : nullptr, pix);
+    L.add(b ? &b->range : nullptr, tiles);
+    L.add(b ? &b->vis_start : nullptr, n_view * n_oct + 1);
+    L.add(b ? &b->tile_order : nullptr, tiles);
+    L.add(b ? &b->work : nullptr, 5);
+    return L;
+}
+
+struct PreBuffers {
+    uint32_t* cnt = nullptr;   // [NT] tiles of a visible (view, voxel)
+    uint64_t* rect = nullptr;  // [NT] its pixel rectangle
+    uint64_t* key = nullptr;   // [NT] depth keys of the visible ones, appended
+    uint32_t* g = nullptr;     // [NT] their (view, voxel) indices
+};
+
+Layout pre_layout(int64_t NT, PreBuffers* b) {
+    Layout L;
+    L.add(b ? &b->cnt : nullptr, NT);
+    L.add(b ? &b->rect : nullptr, NT);
+    L.add(b ? &b->key : nullptr, NT);
+    L.add(b ? &b->g : nullptr, NT);
+    return L;
+}
+
+struct StateBuffers1 {
+    uint32_t* sorted_g = nullptr;
+    VoxRec* rec = nullptr;
+    float4* nrm = nullptr;
+    uint32_t* pval = nullptr;
+    uint8_t* pmask = nullptr;
+};
+
+Layout state1_layout(int64_t n_vis, int64_t P, bool normals, StateBuffers1* b) {
+    Layout L;
+    L.add(b ? &b->sorted_g : nullptr, n_vis);
+    L.add(b ? &b->rec : nullptr, n_vis);
+    if (normals) L.add(b ? &b->nrm : nullptr, n_vis);
+    L.add(b ? &b->pval : nullptr, P);
+    L.add(b ? &b->pmask : nullptr, P);
+    return L;
+}
+
+struct PostBuffers {
+    uint64_t* key_tmp = nullptr;      // [n_vis] depth sort ping-pong
+    uint32_t* g_tmp = nullptr;        // [n_vis]
+    uint64_t* rect_sorted = nullptr;  // [n_vis]
+    uint32_t* pk0 = nullptr;          // [P] pair keys (tiles) and their ping-pong
+    uint32_t* pk1 = nullptr;
+    uint32_t* pv0 = nullptr;          // [P] pair values (records) and their ping-pong
+    uint32_t* pv1 = nullptr;
+    uint8_t* bucket = nullptr;        // [tiles]
+    unsigned long long* zero = nullptr;  // zeroed: look-back words of the records, then the u32 words below
+    int64_t zero_bytes = 0;
+    // inside `zero`
+    unsigned long long* lb_status = nullptr;
+    uint32_t* vsort_words = nullptr;
+    uint32_t* psort_words = nullptr;
+    uint32_t* pair_hist = nullptr;
+    uint32_t* ticket = nullptr;
+    uint32_t* tile_scratch = nullptr;  // [192] bucket counts and cursors of the tile order
+    uint32_t* tile_cnt = nullptr;
+};
+
+Layout post_layout(int64_t n_vis, int64_t P, int64_t tiles, int key_bits, int tile_bits, PostBuffers* b) {
+    Layout L;
+    L.add(b ? &b->key_tmp : nullptr, n_vis);
+    L.add(b ? &b->g_tmp : nullptr, n_vis);
+    L.add(b ? &b->rect_sorted : nullptr, n_vis);
+    L.add(b ? &b->pk0 : nullptr, P);
+    L.add(b ? &b->pk1 : nullptr, P);
+    L.add(b ? &b->pv0 : nullptr, P);
+    L.add(b ? &b->pv1 : nullptr, P);
+    L.add(b ? &b->bucket : nullptr, tiles);
+    const int64_t n_lb = dv::records_emit_blocks(n_vis);
+    const int64_t vw = dv::sort_counted_words(n_vis, key_bits), pw = dv::sort_counted_words(P, tile_bits);
+    const int64_t hw = (int64_t)dv::key_passes(tile_bits) * 256;
+    const int64_t words32 = vw + pw + hw + 1 + 192 + tiles;
+    const int64_t zb = 8 * n_lb + 4 * words32;
+    L.add(b ? &b->zero : nullptr, (zb + 7) / 8);
+    if (b) b->zero_bytes = zb;
+    return L;
+}
+
+// pointers inside the zeroed part, once it is placed
+void post_place_zero(int64_t n_vis, int64_t P, int key_bits, int tile_bits, PostBuffers& b) {
+    b.lb_status = b.zero;
+    uint32_t* w = reinterpret_cast<uint32_t*>(b.zero + dv::records_emit_blocks(n_vis));
+    b.vsort_words = w;
+    w += dv::sort_counted_words(n_vis, key_bits);
+    b.psort_words = w;
+    w += dv::sort_counted_words(P, tile_bits);
+    b.pair_hist = w;
+    w += dv::key_passes(tile_bits) * 256;
+    b.ticket = w;
+    b.tile_scratch = w + 1;
+    b.tile_cnt = w + 1 + 192;
 }
 
 // the part known before any work is enqueued: per-view constants, per-pixel and per-tile state,
-// the projection's per-(view, voxel) arrays and their scan
+// the projection's per-(view, voxel) arrays
 int64_t need_before(int64_t n_view, int64_t n_oct, int64_t NT, int64_t tiles, int64_t pix) {
-    int64_t b = rounded((int64_t)sizeof(ViewParams) * n_view) + rounded((int64_t)sizeof(OctParams) * n_view * n_oct);
-    b += 2 * rounded(4 * pix) + rounded(8 * tiles) + rounded(4 * (n_view * n_oct + 1)) + rounded(4 * tiles);
-    b += rounded(32) + rounded(8);                                          // work counters, sort flag
-    b += 2 * rounded(4 * NT) + 2 * rounded(8 * NT) + rounded(4 * NT);       // cnt, vis, rect, skey, pos
-    b += rounded(4 * ((NT + 2047) / 2048));                                 // scan block sums
-    return b;
+    return state0_layout(n_view, n_oct, tiles, pix, nullptr).bytes + pre_layout(NT, nullptr).bytes;
 }
 
 // the part that follows from the sizes the projection reports: visible voxels and pairs
-int64_t need_after(int64_t n_vis, int64_t P, int key_bits, int tile_bits, bool normals) {
-    int64_t b = 2 * rounded(8 * n_vis) + 2 * rounded(4 * n_vis) + sort_need(n_vis, key_bits);  // depth sort
-    b += rounded(64 * n_vis) + (normals ? rounded(16 * n_vis) : 0);                         // records
-    b += rounded(4 * n_vis) + 2 * rounded(8 * n_vis) + rounded(8 * ((n_vis + 2047) / 2048));  // cnt, rect, offsets
-    b += 4 * rounded(4 * P) + sort_need(P, tile_bits) + rounded(P) + rounded(768);          // pairs, mask, order
-    return b;
+int64_t need_after(int64_t n_vis, int64_t P, int64_t tiles, int key_bits, int tile_bits, bool normals) {
+    return state1_layout(n_vis, P, normals, nullptr).bytes +
+           post_layout(n_vis, P, tiles, key_bits, tile_bits, nullptr).bytes;
 }
 
 }  // namespace
@@ -506,12 +629,40 @@ namespace dv {
 int64_t render_need_before(int64_t n_view, int64_t n_oct, int64_t NT, int64_t tiles, int64_t pix) {
     return need_before(n_view, n_oct, NT, tiles, pix);
 }
-int64_t render_need_after(int64_t n_vis, int64_t P, int key_bits, int tile_bits, bool normals) {
-    return need_after(n_vis, P, key_bits, tile_bits, normals);
+int64_t render_need_after(int64_t n_vis, int64_t P, int64_t tiles, int key_bits, int tile_bits, bool normals) {
+    return need_after(n_vis, P, tiles, key_bits, tile_bits, normals);
 }
 }  // namespace dv
 
 namespace {
+
+// Room for `bytes` in the context's pinned staging buffer (no copy out of it is pending: every call
+// that filled it has seen its sizes or waited for its stream).
+cudaError_t stage_reserve(dv_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->stage_cap) return cudaSuccess;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->stage_cap = 0;
+    const size_t cap = std::max<size_t>(bytes, 64 << 10);
+    const cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_stage), cap, cudaHostAllocDefault);
+    if (e == cudaSuccess) ctx->stage_cap = cap;
+    return e;
+}
+
+// Waits until the projection has written this call's sizes: its last block stores the call number
+// into h_scalars[3] after the sizes, so polling that word ends as soon as they are there; querying
+// the stream now and then reports a kernel that failed.
+cudaError_t wait_sizes(dv_ctx* ctx, uint64_t seq, cudaStream_t s) {
+    for (uint32_t i = 1;; ++i) {
+        if (__atomic_load_n(ctx->h_scalars + 3, __ATOMIC_ACQUIRE) == seq) return cudaSuccess;
+        if ((i & 255u) == 0) {
+            const cudaError_t q = cudaStreamQuery(s);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return q;
+            return __atomic_load_n(ctx->h_scalars + 3, __ATOMIC_ACQUIRE) == seq ? cudaSuccess : cudaErrorUnknown;
+        }
+    }
+}
 
 // The forward of one render call over all its views.  State buffers go to `st`
 // (freed by the caller when no state is wanted).
@@ -586,7 +737,11 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         bp.n_tiles_small = (int32_t)n_small;
     }
     B.n_pix = pix;
-    const int64_t need0 = need_before(n_view, n_oct, bp.n_vox * n_view, tiles, pix);
+    const int64_t NT = bp.n_vox * n_view;
+    if (NT >= ((int64_t)1 << 32)) return fail(ctx, DV_ERR_CAPACITY, "views x voxels exceeds 2^32");
+    const int key_bits = bp.view_shift + bits_for(n_view);
+    const int tile_bits = bits_for(tiles);
+    const int64_t need0 = need_before(n_view, n_oct, NT, tiles, pix);
     ctx->last_need = need0;
     if (ctx->budget > 0 && need0 > ctx->budget)
         return fail(ctx, DV_ERR_CAPACITY, "the call needs at least " + std::to_string(need0) +
@@ -594,26 +749,24 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
                                               std::to_string(ctx->budget) + " (dv_reserve)");
     cudaError_t e = cudaSuccess;
     std::vector<void*>& own = st->owned;
-    B.d_views = pool_alloc<ViewParams>(ctx, s, (size_t)n_view, own, e);
-    B.d_octs = pool_alloc<OctParams>(ctx, s, h_octs.size(), own, e);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B.d_views, B.h_views.data(), sizeof(ViewParams) * n_view, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B.d_octs, h_octs.data(), sizeof(OctParams) * h_octs.size(), cudaMemcpyHostToDevice, s);
+    StateBuffers0 sb0;
+    {
+        Layout L = state0_layout(n_view, n_oct, tiles, pix, &sb0);
+        char* blk = pool_alloc<char>(ctx, s, (size_t)L.bytes, own, e);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate state");
+        L.place(blk);
+    }
+    B.d_views = sb0.views;
+    B.d_octs = sb0.octs;
+    B.n_seg = sb0.n_seg;
+    B.t_final = sb0.t_final;
+    B.range = sb0.range;
+    B.vis_start = sb0.vis_start;
+    B.tile_order = sb0.tile_order;
+    B.work = sb0.work;
+    B.d_sort_err = reinterpret_cast<uint64_t*>(sb0.work + 4);
     bp.views = B.d_views;
     bp.octs = B.d_octs;
-    const int64_t NT = bp.n_vox * n_view;
-    if (NT >= ((int64_t)1 << 32)) return fail(ctx, DV_ERR_CAPACITY, "views x voxels exceeds 2^32");
-    B.n_seg = pool_alloc<uint32_t>(ctx, s, (size_t)pix, own, e);
-    B.t_final = pool_alloc<float>(ctx, s, (size_t)pix, own, e);
-    B.range = pool_alloc<uint2>(ctx, s, (size_t)tiles, own, e);
-    B.vis_start = pool_alloc<uint32_t>(ctx, s, (size_t)n_view * n_oct + 1, own, e);
-    B.tile_order = pool_alloc<uint32_t>(ctx, s, (size_t)tiles, own, e);
-    B.work = pool_alloc<unsigned long long>(ctx, s, 4, own, e);
-    B.d_sort_err = pool_alloc<uint64_t>(ctx, s, 1, own, e);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B.work, 0, 4 * sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B.d_sort_err, 0, sizeof(uint64_t), s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "allocate state");
     if (!ctx->slots.take(&B.h_status, &B.h_status_dev, &B.status_id))
         return fail(ctx, DV_ERR_NOMEM, "mapped host memory for the call's status word");
     *(volatile uint64_t*)B.h_status = kStatusPending;
@@ -622,34 +775,48 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     Arena ar;
     ar.pool = ctx->pool;
     ar.stream = s;
-    uint32_t* cnt = ar.alloc<uint32_t>((size_t)NT);
-    uint64_t* rect = ar.alloc<uint64_t>((size_t)NT);
-    uint64_t* skey = ar.alloc<uint64_t>((size_t)NT);
-    uint32_t* vis = ar.alloc<uint32_t>((size_t)NT);
-    uint32_t* pos = ar.alloc<uint32_t>((size_t)NT);
-    if (ar.err != cudaSuccess) {
-        ar.release();
-        return cuda_fail(ctx, ar.err, "allocate scratch");
+    PreBuffers pre;
+    {
+        Layout L = pre_layout(NT, &pre);
+        char* blk = ar.alloc<char>((size_t)L.bytes);
+        if (ar.err != cudaSuccess) {
+            ar.release();
+            return cuda_fail(ctx, ar.err, "allocate scratch");
+        }
+        L.place(blk);
     }
-    uint32_t* d_flags = (uint32_t*)(ctx->d_scalars + 2);
-    e = cudaMemsetAsync(ctx->d_scalars, 0, 3 * sizeof(uint64_t), s);
+    // The view and octree constants in one asynchronous copy from the pinned staging buffer (the
+    // two parts sit at the same offsets there as in the state block).  The buffer is free again once
+    // this call has seen its sizes (the projection follows the copy on the stream); a call that
+    // fails before that waits for its stream, so the next call never overwrites a pending copy.
+    const size_t octs_off = (size_t)(reinterpret_cast<char*>(B.d_octs) - reinterpret_cast<char*>(B.d_views));
+    const size_t stage_bytes = octs_off + sizeof(OctParams) * h_octs.size();
+    e = stage_reserve(ctx, stage_bytes);
+    if (e != cudaSuccess) {
+        ar.release();
+        return cuda_fail(ctx, e, "staging buffer");
+    }
+    memcpy(ctx->h_stage, B.h_views.data(), sizeof(ViewParams) * n_view);
+    memcpy(ctx->h_stage + octs_off, h_octs.data(), sizeof(OctParams) * h_octs.size());
+    e = cudaMemcpyAsync(B.d_views, ctx->h_stage, stage_bytes, cudaMemcpyHostToDevice, s);
+    // the projection's counters, then the digit counts of the depth keys
+    uint32_t* key_hist = reinterpret_cast<uint32_t*>(ctx->d_scalars + 4);
+    const uint64_t seq = ++ctx->size_seq;
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctx->d_scalars, 0, 4 * sizeof(uint64_t) + (size_t)key_passes(key_bits) * 256 * 4, s);
     {
         Prof p(ctx, KP_PROJECT, s);
         if (e == cudaSuccess)
-            e = launch_project(bp, cnt, rect, skey, vis, d_flags, (unsigned long long*)ctx->d_scalars, s);
+            e = launch_project(bp, pre.cnt, pre.rect, pre.key, pre.g, key_hist, key_bits,
+                               (unsigned long long*)ctx->d_scalars, ctx->h_scalars_dev, seq, ctx->d_spin_err,
+                               B.work, s);
     }
-    // the sizes of everything below come back to the host while the GPU runs the
-    // visibility scan, which needs none of them
-    // a kernel stores the counters into mapped host memory: no copy engine is involved, so a large
-    // device-to-host transfer queued by the caller on another stream cannot delay this read-back
-    if (e == cudaSuccess) e = launch_publish(ctx->d_scalars, ctx->h_scalars_dev, 3, ctx->d_spin_err, 2, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_sizes, s);
-    {
-        Prof p(ctx, KP_SCAN, s);
-        if (e == cudaSuccess) e = scan_u32_to_u32(vis, pos, NT, nullptr, ar, s);
-    }
-    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_sizes);
+    // the projection's last block writes the sizes into mapped host memory: no copy engine is
+    // involved, so a large device-to-host transfer queued by the caller on another stream cannot
+    // delay this read-back
+    if (e == cudaSuccess) e = wait_sizes(ctx, seq, s);
     if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
         ar.release();
         return cuda_fail(ctx, e, "project");
     }
@@ -671,8 +838,7 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
         return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 (tile, voxel) pairs in one call");
     }
     {
-        const int64_t need = need0 + need_after(n_vis, P, bp.view_shift + bits_for(n_view), bits_for(tiles),
-                                                bp.normals != 0);
+        const int64_t need = need0 + need_after(n_vis, P, tiles, key_bits, tile_bits, bp.normals != 0);
         ctx->last_need = need;
         if (ctx->budget > 0 && need > ctx->budget) {
             ar.release();
@@ -685,82 +851,70 @@ dv_status render_batch(dv_ctx* ctx, const dv_octree* oct, int n_oct, const dv_po
     }
     B.n_vis = n_vis;
     B.n_pairs = P;
-    // depth-order sort of the visible (view, voxel)s
-    uint64_t* k0 = ar.alloc<uint64_t>((size_t)n_vis);
-    uint64_t* k1 = ar.alloc<uint64_t>((size_t)n_vis);
-    uint32_t* g1 = ar.alloc<uint32_t>((size_t)n_vis);
-    B.sorted_g = pool_alloc<uint32_t>(ctx, s, (size_t)n_vis, own, e);
-    bp.sorted_g = B.sorted_g;
-    uint32_t* g0 = B.sorted_g;
+    bp.n_vis = n_vis;
+    bp.n_pairs = P;
+    StateBuffers1 sb1;
+    {
+        Layout L = state1_layout(n_vis, P, bp.normals != 0, &sb1);
+        char* blk = pool_alloc<char>(ctx, s, (size_t)L.bytes, own, e);
+        if (e == cudaSuccess) L.place(blk);
+    }
+    PostBuffers post;
+    {
+        Layout L = post_layout(n_vis, P, tiles, key_bits, tile_bits, &post);
+        char* blk = ar.alloc<char>((size_t)L.bytes);
+        if (ar.err == cudaSuccess) {
+            L.place(blk);
+            post_place_zero(n_vis, P, key_bits, tile_bits, post);
+        }
+    }
     if (ar.err != cudaSuccess || e != cudaSuccess) {
         ar.release();
         return cuda_fail(ctx, ar.err != cudaSuccess ? ar.err : e, "allocate sort");
     }
-    {
-        Prof p(ctx, KP_COMPACT, s);
-        e = launch_compact(vis, pos, skey, NT, k0, g0, s);
-    }
-    uint64_t* kk = k0;
-    uint32_t* gg = g0;
+    B.sorted_g = sb1.sorted_g;
+    B.rec = sb1.rec;
+    B.nrm = sb1.nrm;
+    B.pval = sb1.pval;
+    B.pmask = sb1.pmask;
+    bp.sorted_g = B.sorted_g;
+    bp.nrm = B.nrm;
+    e = cudaMemsetAsync(post.zero, 0, (size_t)post.zero_bytes, s);
+    // depth-order sort of the visible (view, voxel)s: the values land in sorted_g
+    uint64_t* sorted_key = nullptr;
     {
         Prof p(ctx, KP_SORT_VOX, s);
         if (e == cudaSuccess)
-            e = radix_sort_u64(kk, gg, k1, g1, n_vis, bp.view_shift + bits_for(n_view), ar, s, sort_err);
+            e = sort_counted_u64(pre.key, pre.g, post.key_tmp, post.g_tmp, sorted_key, B.sorted_g, n_vis, key_bits,
+                                 key_hist, post.vsort_words, sort_err, ar, s);
     }
-    if (e == cudaSuccess && gg != B.sorted_g)
-        e = cudaMemcpyAsync(B.sorted_g, gg, sizeof(uint32_t) * (size_t)n_vis, cudaMemcpyDeviceToDevice, s);
-    B.rec = pool_alloc<VoxRec>(ctx, s, (size_t)n_vis, own, e);
-    if (bp.normals) B.nrm = pool_alloc<float4>(ctx, s, (size_t)n_vis, own, e);
-    bp.nrm = B.nrm;
-    uint32_t* cnt_sorted = ar.alloc<uint32_t>((size_t)n_vis);
-    uint64_t* rect_sorted = ar.alloc<uint64_t>((size_t)n_vis);
-    uint64_t* off_pairs = ar.alloc<uint64_t>((size_t)n_vis);
-    if (ar.err != cudaSuccess || e != cudaSuccess) {
-        ar.release();
-        return cuda_fail(ctx, ar.err != cudaSuccess ? ar.err : e, "sort voxels");
-    }
+    // records, then the (tile, record) pairs in depth order with their tile counts and digits
     {
         Prof p(ctx, KP_RECORDS, s);
-        e = launch_records(bp, B.sorted_g, n_vis, cnt, rect, B.rec, B.nrm, cnt_sorted, rect_sorted, s);
-        if (e == cudaSuccess) e = launch_vis_start(bp, kk, n_vis, B.vis_start, s);
+        if (e == cudaSuccess)
+            e = launch_records_emit(bp, B.sorted_g, sorted_key, n_vis, P, pre.cnt, pre.rect, B.rec, B.nrm,
+                                    post.rect_sorted, B.vis_start, post.pk0, post.pv0, post.pair_hist, tile_bits,
+                                    post.tile_cnt, post.lb_status, post.ticket, sort_err, ctx->d_spin_err, s);
     }
-    {
-        Prof p(ctx, KP_SCAN, s);
-        if (e == cudaSuccess) e = scan_u32_to_u64(cnt_sorted, off_pairs, n_vis, nullptr, ar, s);
-    }
-    // pairs
-    uint32_t* pk0 = ar.alloc<uint32_t>((size_t)P);
-    uint32_t* pk1 = ar.alloc<uint32_t>((size_t)P);
-    uint32_t* pv0 = pool_alloc<uint32_t>(ctx, s, (size_t)P, own, e);
-    uint32_t* pv1 = ar.alloc<uint32_t>((size_t)P);
-    if (ar.err != cudaSuccess || e != cudaSuccess) {
-        ar.release();
-        return cuda_fail(ctx, ar.err != cudaSuccess ? ar.err : e, "allocate pairs");
-    }
-    {
-        Prof p(ctx, KP_EMIT, s);
-        e = launch_emit(bp, off_pairs, rect_sorted, B.sorted_g, n_vis, P, pk0, pv0, s);
-    }
-    uint32_t* pk = pk0;
-    uint32_t* pv = pv0;
+    // stable sort of the pairs by tile: every tile's list stays front to back; the values land in pval
+    uint32_t* sorted_tile = nullptr;
     {
         Prof p(ctx, KP_SORT_PAIRS, s);
-        if (e == cudaSuccess) e = radix_sort_u32(pk, pv, pk1, pv1, P, bits_for(tiles), ar, s, sort_err);
+        if (e == cudaSuccess)
+            e = sort_counted_u32(post.pk0, post.pv0, post.pk1, post.pv1, sorted_tile, B.pval, P, tile_bits,
+                                 post.pair_hist, post.psort_words, sort_err, ar, s);
     }
-    // the call's own sort flag goes to its status slot (read by dv_state_check, the backward and the
-    // serving loop), so a timeout is reported to the call that had it
-    if (e == cudaSuccess) e = launch_publish(B.d_sort_err, B.h_status_dev, 1, nullptr, -1, s);
-    if (e == cudaSuccess) B.published = true;
-    if (e == cudaSuccess && pv != pv0)
-        e = cudaMemcpyAsync(pv0, pv, sizeof(uint32_t) * (size_t)P, cudaMemcpyDeviceToDevice, s);
-    B.pval = pv0;
-    B.pmask = pool_alloc<uint8_t>(ctx, s, (size_t)P, own, e);
     {
         Prof p(ctx, KP_RANGES, s);
+        // the call's own sort flag goes to its status slot (read by dv_state_check, the backward and
+        // the serving loop), so a timeout is reported to the call that had it
         if (e == cudaSuccess)
-            e = launch_pair_mask_ranges(bp, pk, B.pval, rect_sorted, P, B.pmask, B.range, (int)tiles, s);
-        uint32_t* tscr = ar.alloc<uint32_t>(192);
-        if (e == cudaSuccess) e = tscr ? launch_tile_order(bp, B.range, (int)tiles, tscr, B.tile_order, s) : ar.err;
+            e = launch_pair_mask(bp, sorted_tile, B.pval, post.rect_sorted, P, n_vis, B.pmask, B.range,
+                                 B.d_sort_err, B.h_status_dev, s);
+        if (e == cudaSuccess) B.published = true;
+        if (e == cudaSuccess)
+            e = launch_tile_order(bp, post.tile_cnt, (int)tiles, B.range, post.bucket, post.tile_scratch,
+                                  B.tile_order, s);
     }
     {
         Prof p(ctx, KP_FWD, s);
@@ -853,19 +1007,19 @@ dv_status dv_create(dv_ctx** out, int32_t device) {
         cudaMemPoolDestroy(ctx->pool);
         return DV_ERR_NOMEM;
     }
-    if (cudaMalloc(&ctx->d_scalars, 4 * sizeof(uint64_t)) != cudaSuccess) {
+    memset(ctx->h_scalars, 0, 4 * sizeof(uint64_t));
+    if (cudaMalloc(&ctx->d_scalars, 4 * sizeof(uint64_t) + 8 * 256 * sizeof(uint32_t)) != cudaSuccess) {
         cudaFreeHost(ctx->h_scalars);
         cudaMemPoolDestroy(ctx->pool);
         return DV_ERR_NOMEM;
     }
     ctx->d_spin_err = dv::spin_error_word();
-    if (!ctx->d_spin_err || cudaEventCreateWithFlags(&ctx->ev_sizes, cudaEventDisableTiming) != cudaSuccess ||
+    if (!ctx->d_spin_err ||
         cudaStreamCreateWithPriority(&ctx->fork.side, cudaStreamNonBlocking, side_priority()) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->fork.side2, cudaStreamNonBlocking, side_priority()) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->fork.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->fork.ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->fork.ev_join2, cudaEventDisableTiming) != cudaSuccess) {
-        if (ctx->ev_sizes) cudaEventDestroy(ctx->ev_sizes);
         if (ctx->fork.ev_fork) cudaEventDestroy(ctx->fork.ev_fork);
         if (ctx->fork.ev_join) cudaEventDestroy(ctx->fork.ev_join);
         if (ctx->fork.side) cudaStreamDestroy(ctx->fork.side);
@@ -896,7 +1050,6 @@ void dv_destroy(dv_ctx* ctx) {
         cudaEventDestroy(r.b);
     }
     for (auto e : ctx->spare) cudaEventDestroy(e);
-    cudaEventDestroy(ctx->ev_sizes);
     if (ctx->fork.ev_fork) cudaEventDestroy(ctx->fork.ev_fork);
     if (ctx->fork.ev_join) cudaEventDestroy(ctx->fork.ev_join);
     if (ctx->fork.ev_join2) cudaEventDestroy(ctx->fork.ev_join2);
@@ -904,6 +1057,7 @@ void dv_destroy(dv_ctx* ctx) {
     if (ctx->fork.side2) cudaStreamDestroy(ctx->fork.side2);
     cudaFree(ctx->d_scalars);
     cudaFreeHost(ctx->h_scalars);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
 }

@@ -403,6 +403,12 @@ __device__ __forceinline__ void warp_reduce_add(const float* acc, float* gp) {
     if (nreal > 0 && v[0] != 0.0f) atomicAdd(gp + idx, v[0]);
 }
 
+// Record of pair q.  Every pair's record is below n_vis unless a sort's bounded wait ran out (the
+// call is then reported as timed out); the clamp keeps the reads and gradient atomics in range.
+__device__ __forceinline__ uint32_t rec_index(const BatchParams& bp, const uint32_t* __restrict__ pval, uint32_t q) {
+    return min(__ldg(pval + q), (uint32_t)(bp.n_vis - 1));
+}
+
 // Per-lane walk of one actor's sub-list (divergent; only for actors beyond the
 // NTA lockstep slots).
 template <bool GRAD, int KS, bool NRM, bool WEX>
@@ -418,7 +424,7 @@ __device__ __noinline__ void walk_actor_lane(Pix<NRM>& ps, const Bwd<NRM>& bw, c
     for (uint32_t q = q0; q < q1 && !ps.done; ++q) {
         if (!(__ldg(pmask + q) & wbit)) continue;
         ps.tests += 1;
-        const uint32_t r = __ldg(pval + q);
+        const uint32_t r = rec_index(bp, pval, q);
         const float4* R = rec[r].v;
         const float4 g = __ldg(R);
         float t0, t1;
@@ -525,7 +531,11 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     const float t_near = fp.near_, t_far = fp.far_;
     const int tile = gtile - bp.tile_base[view];
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const uint2 rg = __ldg(tile_range + gtile);
+    // the tile's slice of the pair list, kept inside [0, n_pairs] whatever the range words hold (they
+    // are only inconsistent after a sort wait that timed out, which the call then reports)
+    uint2 rg = __ldg(tile_range + gtile);
+    rg.y = (uint32_t)min((int64_t)rg.y, bp.n_pairs);
+    rg.x = min(rg.x, rg.y);
     // per-pixel set-up first: its loads overlap the tile set-up below
     const int lane = tid & 31, warp = tid >> 5;
     const uint32_t wbit = 1u << ((half * 2 + (warp >> 1)) * 2 + (warp & 1));  // this warp's 8x4 block
@@ -596,7 +606,10 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     }
     // tile set-up, all loads independent of one another: the view's octree boundaries in
     // the record order, and which actor boxes cover this tile
-    for (int i = tid; i <= n_oct; i += CT_THREADS) s_vs[i] = __ldg(vis_start + view * n_oct + i);
+    for (int i = tid; i <= n_oct; i += CT_THREADS) {
+        s_vs[i] = __ldg(vis_start + view * n_oct + i);
+        s_sub[i] = rg.x;  // every sub-list start stays inside the tile's slice
+    }
     if (ACT) {
         for (int o = tid; o < n_oct; o += CT_THREADS) {
             const OctParams& P = vo[o];
@@ -624,15 +637,13 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
         for (uint32_t base = rg.x; base < rg.y; base += CT_THREADS) {
             const uint32_t q = base + tid;
             if (q < rg.y) {
-                const int o = oct_of(__ldg(pval + q));
-                const int op = q > rg.x ? oct_of(__ldg(pval + q - 1)) : -1;
+                const int o = oct_of(rec_index(bp, pval, q));
+                const int op = q > rg.x ? oct_of(rec_index(bp, pval, q - 1)) : -1;
                 for (int x = op + 1; x <= o; ++x) s_sub[x] = q;
                 if (q + 1 == rg.y)
                     for (int x = o + 1; x <= n_oct; ++x) s_sub[x] = rg.y;
             }
         }
-        if (rg.x == rg.y)
-            for (int i = tid; i <= n_oct; i += CT_THREADS) s_sub[i] = rg.x;
     }
     if (ACT && tid < 32) {
         // actor list of the tile in octree order (warp 0, ballot compaction)
@@ -679,12 +690,12 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     // left to do in this list.  The batch loop, its barriers and its early exit are
     // CTA-uniform.
     auto stream = [&](uint32_t q0, uint32_t q1, auto&& chunk) {
-        const uint32_t n_batch = (q1 - q0 + CT_THREADS - 1) / CT_THREADS;
+        const uint32_t n_batch = q1 > q0 ? (q1 - q0 + CT_THREADS - 1) / CT_THREADS : 0u;
         uint32_t r_ahead = 0, m_ahead = 0;
         if (n_batch > 0) {
             const uint32_t qa = q0 + tid;
             if (qa < q1) {
-                const uint32_t r = __ldg(pval + qa);
+                const uint32_t r = rec_index(bp, pval, qa);
                 const float4* R = rec[r].v;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) cp_async16(&s_rec[0][tid][k], R + k);
@@ -695,7 +706,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
             cp_async_commit();
             const uint32_t qb = q0 + CT_THREADS + tid;
             if (qb < q1) {
-                r_ahead = __ldg(pval + qb);
+                r_ahead = rec_index(bp, pval, qb);
                 m_ahead = __ldg(pmask + qb);
             }
         }
@@ -715,7 +726,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                 cp_async_commit();
                 const uint32_t qb = q0 + (bi + 2) * CT_THREADS + tid;
                 if (qb < q1) {
-                    r_ahead = __ldg(pval + qb);
+                    r_ahead = rec_index(bp, pval, qb);
                     m_ahead = __ldg(pmask + qb);
                 }
             }

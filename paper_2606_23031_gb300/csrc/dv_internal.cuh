@@ -59,6 +59,8 @@ struct BatchParams {
     int32_t n_tiles_small;  // tiles that 1 to 4 actor clip boxes cover (next in the tile order)
     int32_t normals;     // the call renders the normal state N (records carry voxel normals)
     int64_t n_vox;       // voxels of one view (all octrees)
+    int64_t n_vis;       // visible (view, voxel)s = records of the call (set once the projection reports it)
+    int64_t n_pairs;     // (tile, record) pairs of the call (likewise)
     int64_t vox_offset[DV_MAX_OCTREES + 1];
     int32_t tile_base[DV_MAX_VIEWS + 1];
     const ViewParams* views;  // device [n_view]
@@ -159,10 +161,35 @@ int sm_count();
 // returns the tile's call flag and the device's wait-error word (which it then clears).  Synchronous.
 cudaError_t debug_sort_timeout(int spin_limit, uint32_t* call_flag, uint32_t* device_flag, cudaStream_t s);
 
+// Sort of n (key, value) pairs on bits [0, n_bits) whose digit counts the kernel that wrote the keys
+// has already taken: hist[p][256] counts digit (key >> 8p) & 255 of every key, for every 8-bit pass p.
+// `words` (sort_counted_words(n, n_bits) 32-bit words, zeroed by the caller) hold the passes' tile
+// counters and look-back status.  keys/vals and keys_tmp/vals_tmp are the ping-pong buffers (the
+// input is overwritten); the last pass writes vals_out and keys_out, or, with keys_out null, the
+// ping-pong buffer it does not read, returned in keys_out.  call_err (device word, not null) is set
+// to 1 if a bounded look-back wait runs out (the result is then not sorted).  Counts of 2^30 keys
+// or more take reduce-then-scan passes (which count their own digits) and copy to the outputs.
+int64_t sort_counted_words(int64_t n, int n_bits);
+cudaError_t sort_counted_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t* vals_tmp,
+                             uint64_t*& keys_out, uint32_t* vals_out, int64_t n, int n_bits, const uint32_t* hist,
+                             uint32_t* words, uint32_t* call_err, Arena& ar, cudaStream_t s);
+cudaError_t sort_counted_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                             uint32_t*& keys_out, uint32_t* vals_out, int64_t n, int n_bits, const uint32_t* hist,
+                             uint32_t* words, uint32_t* call_err, Arena& ar, cudaStream_t s);
+// 8-bit passes of an n_bits key
+int key_passes(int n_bits);
+
 // kernel launchers (one thread per (view, voxel) unless stated)
-cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
-                           uint32_t* flags, unsigned long long* totals, cudaStream_t s);
-// n (<= 32) counters from device memory into mapped host memory, by a kernel (no copy engine)
+// Projection: for each visible (view, voxel) g, cnt[g] (tiles) and rect[g] (pixel rectangle); the
+// visible ones appended to (out_key, out_g) (depth key, g) in no particular order, the digits of
+// their keys counted in key_hist [key_passes(key_bits)][256] (zeroed by the caller).  scal[4]
+// (zeroed by the caller): visible count, pair count, flags (DV_FLAG_*), finished blocks; the last
+// block copies the first three into host_out (mapped host memory), with the device's wait-error word
+// (taken and cleared) folded into the flags, then writes `seq` into host_out[3] once the three are
+// there.  It also clears work[5] (the call's work counters and sort flag).
+cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* out_key, uint32_t* out_g,
+                           uint32_t* key_hist, int key_bits, unsigned long long* scal, uint64_t* host_out, uint64_t seq,
+                           uint32_t* spin_err, unsigned long long* work, cudaStream_t s);
 // copies n words into mapped host memory; with spin_err, takes (and clears) the device's wait-error
 // word and sets DV_FLAG_SPIN_TIMEOUT in word flag_idx
 cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, uint32_t* spin_err, int flag_idx,
@@ -170,26 +197,29 @@ cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n
 // device address of this device's wait-error word (bounded waits that run out set it; shared by every
 // context on the device); nullptr on failure
 uint32_t* spin_error_word();
-cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
-                           uint64_t* out_key, uint32_t* out_val, cudaStream_t s);
-cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
-                           const uint64_t* rect, VoxRec* rec, float4* nrm, uint32_t* cnt_sorted,
-                           uint64_t* rect_sorted, cudaStream_t s);
-// start of every (view, octree) group in depth-key order: vis_start[n_view * n_oct + 1]
-cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, int64_t n_vis, uint32_t* vis_start,
-                             cudaStream_t s);
-cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64_t* rect_sorted,
-                        const uint32_t* sorted_g, int64_t n_vis, int64_t n_pairs, uint32_t* pair_key,
-                        uint32_t* pair_val, cudaStream_t s);
-// per tile-sorted pair: its 8x4-block mask; per tile: its [first, end) range of the pair list
-cudaError_t launch_pair_mask_ranges(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
-                                    const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, uint2* tile_range,
-                                    int n_tiles, cudaStream_t s);
-// tiles ordered by decreasing pair-list length (log2 buckets) within three groups, in this order: the
-// tiles that 5 or more actor clip boxes cover (bp.n_tiles_large), those that 1 to 4 cover
-// (bp.n_tiles_small), the others; scratch: 192 words
-cudaError_t launch_tile_order(const BatchParams& bp, const uint2* tile_range, int n_tiles, uint32_t* scratch192,
-                              uint32_t* order, cudaStream_t s);
+// One thread per visible voxel in depth order: records (and normals), rect_sorted, vis_start
+// [n_view * n_oct + 1] (start of every (view, octree) group), and the (tile, record) pairs in
+// depth order at offsets of a single-pass scan of the tile counts; counts the pairs of every tile in
+// tile_cnt and the tile-sort digits in pair_hist [key_passes(tile_bits)][256].  tile_cnt, pair_hist,
+// lb_status [records_emit_blocks(n_vis)] and ticket are zeroed by the caller.
+cudaError_t launch_records_emit(const BatchParams& bp, const uint32_t* sorted_g, const uint64_t* sorted_key,
+                                int64_t n_vis, int64_t n_pairs, const uint32_t* cnt, const uint64_t* rect,
+                                VoxRec* rec, float4* nrm, uint64_t* rect_sorted, uint32_t* vis_start,
+                                uint32_t* pair_key, uint32_t* pair_val, uint32_t* pair_hist, int tile_bits,
+                                uint32_t* tile_cnt, unsigned long long* lb_status, uint32_t* ticket,
+                                uint32_t* call_err, uint32_t* dev_err, cudaStream_t s);
+int64_t records_emit_blocks(int64_t n_vis);
+// per tile-sorted pair: its 8x4-block mask; per tile with pairs: its [first, end) range of the
+// tile-sorted pair list; also copies *sort_err into the call's mapped status word
+cudaError_t launch_pair_mask(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
+                             const uint64_t* rect_sorted, int64_t n_pairs, int64_t n_vis, uint8_t* mask,
+                             uint2* tile_range, const uint64_t* sort_err, uint64_t* status_host, cudaStream_t s);
+// the empty range for every tile without pairs, and the tiles ordered by decreasing list length (log2
+// buckets of tile_cnt) within three groups, in this order: the tiles that 5 or more actor clip boxes
+// cover (bp.n_tiles_large), those that 1 to 4 cover (bp.n_tiles_small), the others.  bucket: one byte
+// of scratch per tile; scratch192: zeroed words.
+cudaError_t launch_tile_order(const BatchParams& bp, const uint32_t* tile_cnt, int n_tiles, uint2* range,
+                              uint8_t* bucket, uint32_t* scratch192, uint32_t* order, cudaStream_t s);
 // Two more streams of the context with their events: a compositing pass runs its three launches (the
 // tiles that many actor boxes cover, those that a few cover, the others) side by side on these and
 // the call's stream.
@@ -273,7 +303,7 @@ dv_status validate_request(const dv_camera& cam, const dv_pose* poses, int n_oct
 // enqueued (n_view views of n_oct octrees, NT = views x voxels, tiles and pixels over the views) and
 // the part that follows from the projection's sizes (visible voxels, pairs)
 int64_t render_need_before(int64_t n_view, int64_t n_oct, int64_t NT, int64_t tiles, int64_t pix);
-int64_t render_need_after(int64_t n_vis, int64_t P, int key_bits, int tile_bits, bool normals);
+int64_t render_need_after(int64_t n_vis, int64_t P, int64_t tiles, int key_bits, int tile_bits, bool normals);
 
 // render of views whose outputs live in separate device buffers (serving loop); the saved state
 // (non-null) lets the caller check the call's sorts once its stream has finished

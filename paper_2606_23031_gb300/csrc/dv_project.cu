@@ -1,4 +1,4 @@
-// Per-voxel projection, visibility compaction, render records and tile binning.
+// Per-voxel projection, render records and tile binning.
 //
 // All kernels run over every view of a render call at once (a view is one camera
 // of one request, with its own actor poses); tiles are numbered globally.
@@ -7,12 +7,18 @@
 //          the 8 corners placed in the camera frame by the composed pose
 //          (local -> world -> camera, Sec. 3.2), near/far culling, a conservative
 //          screen rectangle of the box (clipped against the near plane) turned
-//          into a tile rectangle, and the depth-order key.
+//          into a tile rectangle, and the depth-order key.  The visible ones are
+//          appended (one reservation per block) to the depth sort's input, whose
+//          digit counts the same kernel takes; the last block to finish writes the
+//          call's sizes into mapped host memory.
 // records  (one thread per visible voxel, in depth-key order): 64-byte record
 //          with the local box, the 8 raw densities and the view-dependent SH
-//          colour for this camera.
-// emit     one (tile, record) pair per tile of the rectangle.
-// ranges   [start, end) of every tile in the tile-sorted pair list.
+//          colour for this camera; the block then writes the (tile, record) pairs
+//          of its voxels, one per tile of each rectangle, at the offsets a
+//          single-pass scan (look-back over earlier blocks) gives, counting the
+//          pairs of every tile and the digits of the tile sort on the way.
+// mask     which 8x4-pixel blocks of its tile each sorted pair touches, and the tile ranges.
+// order    the tiles by list length (from the per-tile counts) within their actor-coverage group.
 //
 // Depth-order key.  Leaves of one octree are cells of a binary space partition
 // (each node split by the three planes through its centre).  For rays that all
@@ -25,6 +31,8 @@
 // are exact integer comparisons of 2*(o - root_min)/root*2^L against the
 // node-centre lattice coordinates.  The view and octree indices sit above the
 // path bits, so one sort groups each (view, octree) and orders it front to back.
+// Keys are unique (distinct leaves have distinct paths), so the order in which
+// the projection appends them does not change the sorted result.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,11 +87,10 @@ __device__ __forceinline__ void proj_point(const ViewParams& fp, float x, float 
     v1 = fmaxf(v1, v);
 }
 
-// Projection of (view, voxel) g; sets cnt[g], vis[g] (and rect[g], skey[g] when visible)
-// and returns the tile count (0: not visible).
-__device__ __forceinline__ uint32_t project_voxel(const BatchParams& bp, int64_t g, uint32_t* __restrict__ cnt,
-                                                  uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
-                                                  uint32_t* __restrict__ vis, uint32_t* __restrict__ flags) {
+// Projection of (view, voxel) g: returns its tile count (0: not visible) and, when visible, its
+// pixel rectangle and depth-order key.
+__device__ __forceinline__ uint32_t project_voxel(const BatchParams& bp, int64_t g, uint64_t& rect,
+                                                  uint64_t& skey, uint32_t* __restrict__ flags) {
     const int view = (int)(g / bp.n_vox);
     const int64_t gv = g - (int64_t)view * bp.n_vox;
     const int o = find_octree(bp, gv);
@@ -91,11 +98,10 @@ __device__ __forceinline__ uint32_t project_voxel(const BatchParams& bp, int64_t
     const OctParams& P = bp.octs[view * bp.n_oct + o];
     const int64_t v = gv - bp.vox_offset[o];
     const uint64_t key = P.key[v];
-    cnt[g] = 0;
-    vis[g] = 0;
     const Leaf L = decode_leaf(P, key);
     if (L.level > P.max_level || L.i >> L.level || L.j >> L.level || L.k >> L.level) {
         atomicOr(flags, DV_FLAG_BAD_LEVEL);
+        __threadfence();  // visible to the block that reports the flags
         return 0;
     }
     // corners in the camera frame: p = M (mn + s*offset) + m
@@ -152,10 +158,8 @@ __device__ __forceinline__ uint32_t project_voxel(const BatchParams& bp, int64_t
     if (!(pu0 <= pu1 && pv0 <= pv1)) return 0;
     const uint32_t tx0 = pu0 >> 4, tx1 = pu1 >> 4, ty0 = pv0 >> 4, ty1 = pv1 >> 4;
     const uint32_t n_tiles = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-    cnt[g] = n_tiles;
-    vis[g] = 1;
     // pixel rectangle (tiles are its pixels >> 4)
-    rect[g] = (uint64_t)pu0 | ((uint64_t)pu1 << 16) | ((uint64_t)pv0 << 32) | ((uint64_t)pv1 << 48);
+    rect = (uint64_t)pu0 | ((uint64_t)pu1 << 16) | ((uint64_t)pv0 << 32) | ((uint64_t)pv1 << 48);
     // depth-order key (see the file comment)
     uint64_t bsp = 0;
     const int Lk = bp.Lkey;
@@ -171,54 +175,95 @@ __device__ __forceinline__ uint32_t project_voxel(const BatchParams& bp, int64_t
         bsp = (bsp << 3) | (fi << 2) | (fj << 1) | fk;
     }
     bsp <<= 3 * (Lk - L.level);
-    skey[g] = ((uint64_t)view << bp.view_shift) | ((uint64_t)o << bp.oct_shift) | bsp;
+    skey = ((uint64_t)view << bp.view_shift) | ((uint64_t)o << bp.oct_shift) | bsp;
     return n_tiles;
 }
 
-// One thread per (view, voxel); the block's visible voxels and (tile, voxel) pairs are
-// added to totals[0] and totals[1], so the host learns both sizes from this kernel alone.
+constexpr int MAX_KEY_PASSES = 8;  // 8-bit digits of a 64-bit key
+
+// One thread per (view, voxel).  A block reserves one run of the sort input for its visible voxels
+// (scal[0] counts them, scal[1] their pairs), adds the digits of their keys to key_hist
+// [key_passes][256], and the block that finishes last copies scal[0..2] into host_out[0..2] (the
+// device's wait-error word folded into the flags) and then `seq` into host_out[3], so the host learns
+// the sizes from this kernel alone, as soon as they are final.  scal[3] counts finished blocks.
+// Block 0 also clears the call's five work words.
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParams bp, uint32_t* __restrict__ cnt,
-                                                 uint64_t* __restrict__ rect, uint64_t* __restrict__ skey,
-                                                 uint32_t* __restrict__ vis, uint32_t* __restrict__ flags,
-                                                 unsigned long long* __restrict__ totals) {
+                                                 uint64_t* __restrict__ rect, uint64_t* __restrict__ out_key,
+                                                 uint32_t* __restrict__ out_g, uint32_t* __restrict__ key_hist,
+                                                 int key_passes, unsigned long long* __restrict__ scal,
+                                                 volatile uint64_t* host_out, uint64_t seq,
+                                                 uint32_t* __restrict__ spin_err, unsigned long long* __restrict__ work) {
     pdl_wait();
     pdl_launch_dependents();
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // view * n_vox + voxel
+    if (blockIdx.x == 0 && threadIdx.x < 5) work[threadIdx.x] = 0ull;
+    __shared__ uint32_t h[MAX_KEY_PASSES][256];
+    __shared__ uint32_t s_wv[8];
+    __shared__ unsigned long long s_wp[8];
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_nv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + tid;  // view * n_vox + voxel
+    uint64_t rc = 0, key = 0;
     uint32_t c = 0;
-    if (g < bp.n_vox * bp.n_view) c = project_voxel(bp, g, cnt, rect, skey, vis, flags);
-    unsigned long long nv = c ? 1ull : 0ull, np = c;
+    if (g < bp.n_vox * bp.n_view) c = project_voxel(bp, g, rc, key, reinterpret_cast<uint32_t*>(scal + 2));
+    const unsigned bal = __ballot_sync(0xffffffffu, c != 0);
+    unsigned long long np = c;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        nv += __shfl_down_sync(0xffffffffu, nv, off);
-        np += __shfl_down_sync(0xffffffffu, np, off);
-    }
-    __shared__ unsigned long long s_nv[8], s_np[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) np += __shfl_down_sync(0xffffffffu, np, off);
     if (lane == 0) {
-        s_nv[warp] = nv;
-        s_np[warp] = np;
+        s_wv[warp] = __popc(bal);
+        s_wp[warp] = np;
+    }
+    for (int i = tid; i < key_passes * 256; i += 256) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t nv = 0;
+        unsigned long long pp = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t x = s_wv[w];
+            s_wv[w] = nv;  // exclusive offsets of the warps
+            nv += x;
+            pp += s_wp[w];
+        }
+        s_nv = nv;
+        s_base = nv ? atomicAdd(scal + 0, (unsigned long long)nv) : 0ull;
+        if (pp) atomicAdd(scal + 1, pp);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            nv += s_nv[w];
-            np += s_np[w];
+    if (s_nv) {
+        if (c) {
+            const unsigned long long q = s_base + s_wv[warp] + __popc(bal & ((1u << lane) - 1u));
+            out_key[q] = key;
+            out_g[q] = (uint32_t)g;
+            cnt[g] = c;
+            rect[g] = rc;
+            for (int p = 0; p < key_passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 255u], 1u);
         }
-        if (nv) atomicAdd(totals + 0, nv);
-        if (np) atomicAdd(totals + 1, np);
+        __syncthreads();
+        for (int i = tid; i < key_passes * 256; i += 256) {
+            const uint32_t x = (&h[0][0])[i];
+            if (x) atomicAdd(key_hist + i, x);
+        }
     }
-}
-
-__global__ void k_compact(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ pos,
-                          const uint64_t* __restrict__ skey, int64_t n, uint64_t* __restrict__ out_key,
-                          uint32_t* __restrict__ out_val) {
-    pdl_wait();
-    pdl_launch_dependents();
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || !vis[g]) return;
-    const uint32_t p = pos[g];
-    out_key[p] = skey[g];
-    out_val[p] = (uint32_t)g;
+    // the last block to finish sees every block's counts (each block's totals come from its thread 0,
+    // a flag from the thread that set it, after its own fence)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(scal + 3, 1ull);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            const uint64_t nv = atomicAdd(scal + 0, 0ull), pp = atomicAdd(scal + 1, 0ull);
+            uint64_t fl = atomicOr(reinterpret_cast<unsigned long long*>(scal + 2), 0ull);
+            if (spin_err && atomicExch(spin_err, 0u)) fl |= DV_FLAG_SPIN_TIMEOUT;
+            host_out[0] = nv;
+            host_out[1] = pp;
+            host_out[2] = fl;
+            __threadfence_system();
+            host_out[3] = seq;
+            __threadfence_system();
+        }
+    }
 }
 
 // Real SH basis (degree <= 3) times coefficients, for a unit direction.
@@ -248,89 +293,6 @@ __device__ __forceinline__ void sh_eval_basis(int deg, float x, float y, float z
     b[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
 }
 
-__global__ void __launch_bounds__(256) k_records(const __grid_constant__ BatchParams bp,
-                                                 const uint32_t* __restrict__ sorted_g, int64_t n_vis,
-                                                 const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ rect,
-                                                 VoxRec* __restrict__ rec, float4* __restrict__ nrm,
-                                                 uint32_t* __restrict__ cnt_sorted,
-                                                 uint64_t* __restrict__ rect_sorted) {
-    pdl_wait();
-    pdl_launch_dependents();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_vis) return;
-    const uint32_t g = sorted_g[r];
-    const int view = (int)(g / bp.n_vox);
-    const int64_t gv = (int64_t)g - (int64_t)view * bp.n_vox;
-    const int o = find_octree(bp, gv);
-    const OctParams& P = bp.octs[view * bp.n_oct + o];
-    const int64_t v = gv - bp.vox_offset[o];
-    const Leaf L = decode_leaf(P, P.key[v]);
-    const float4* d4 = reinterpret_cast<const float4*>(P.dens + v * 8);
-    const float4 da = __ldg(d4), db = __ldg(d4 + 1);
-    // min corner relative to the camera centre (octree frame), then the view direction:
-    // camera centre -> voxel centre
-    const float rx = L.mn[0] - P.o_loc[0], ry = L.mn[1] - P.o_loc[1], rz = L.mn[2] - P.o_loc[2];
-    float gx = fmaf(0.5f, L.s, rx);
-    float gy = fmaf(0.5f, L.s, ry);
-    float gz = fmaf(0.5f, L.s, rz);
-    const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
-    const float ig = gl > 0.0f ? 1.0f / gl : 0.0f;
-    gx *= ig;
-    gy *= ig;
-    gz *= ig;
-    float b[16];
-    sh_eval_basis(P.sh_degree, gx, gy, gz, b);
-    const int nsh = (P.sh_degree + 1) * (P.sh_degree + 1);
-    const float* shv = P.sh + v * nsh * 3;
-    float cc[3] = {0.5f, 0.5f, 0.5f};
-    if ((nsh * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(shv) & 15) == 0) {
-        // 16-byte loads of the coefficient rows, flattened: element e = 3 q + channel
-#pragma unroll
-        for (int e0 = 0; e0 < 48; e0 += 4) {
-            if (e0 >= nsh * 3) break;
-            const float4 x4 = __ldg(reinterpret_cast<const float4*>(shv + e0));
-            const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) cc[(e0 + i) % 3] = fmaf(b[(e0 + i) / 3], xs[i], cc[(e0 + i) % 3]);
-        }
-    } else {
-        for (int q = 0; q < nsh; ++q) {
-            cc[0] = fmaf(b[q], __ldg(shv + q * 3 + 0), cc[0]);
-            cc[1] = fmaf(b[q], __ldg(shv + q * 3 + 1), cc[1]);
-            cc[2] = fmaf(b[q], __ldg(shv + q * 3 + 2), cc[2]);
-        }
-    }
-    const float c0 = cc[0], c1 = cc[1], c2 = cc[2];
-    VoxRec R;
-    R.v[0] = make_float4(rx, ry, rz, L.s);
-    // the trilinear field as a polynomial in the voxel coordinates (x, y, z) in [0, 1]^3:
-    // rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz, from corner c = x + 2y + 4z
-    const float p1 = da.y - da.x, p2 = da.z - da.x, p3 = db.x - da.x;
-    const float p4 = (da.w - da.z) - p1, p5 = (db.y - db.x) - p1, p6 = (db.z - db.x) - p2;
-    const float p7 = ((db.w - db.z) - (db.y - db.x)) - ((da.w - da.z) - p1);
-    R.v[1] = make_float4(da.x, p1, p2, p4);
-    R.v[2] = make_float4(p3, p5, p6, p7);
-    R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);
-    rec[r] = R;
-    if (nrm) {
-        // voxel normal: minus the direction of the trilinear density gradient at the voxel centre
-        // (per axis: the four corners on its high side minus the four on its low side), rotated
-        // into the world frame by the octree's pose
-        const float gxl = (da.y + da.w + db.y + db.w) - (da.x + da.z + db.x + db.z);
-        const float gyl = (da.z + da.w + db.z + db.w) - (da.x + da.y + db.x + db.y);
-        const float gzl = (db.x + db.y + db.z + db.w) - (da.x + da.y + da.z + da.w);
-        const float g2 = fmaf(gxl, gxl, fmaf(gyl, gyl, gzl * gzl));
-        const float s = g2 > 0.0f ? -rsqrtf(g2) : 0.0f;
-        const float nl[3] = {gxl * s, gyl * s, gzl * s};
-        float nw[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) nw[k] = fmaf(P.Rw[k * 3 + 0], nl[0], fmaf(P.Rw[k * 3 + 1], nl[1], P.Rw[k * 3 + 2] * nl[2]));
-        nrm[r] = make_float4(nw[0], nw[1], nw[2], 0.0f);
-    }
-    cnt_sorted[r] = cnt[g];
-    rect_sorted[r] = rect[g];
-}
-
 // (view, octree) group of a depth key: view * n_oct + octree
 __device__ __forceinline__ int key_group(const BatchParams& bp, uint64_t k) {
     const int view = (int)(k >> bp.view_shift);
@@ -338,45 +300,215 @@ __device__ __forceinline__ int key_group(const BatchParams& bp, uint64_t k) {
     return view * bp.n_oct + o;
 }
 
-__global__ void k_vis_start(const __grid_constant__ BatchParams bp, const uint64_t* __restrict__ key, int64_t n_vis,
-                            uint32_t* __restrict__ vis_start) {
-    pdl_wait();
-    pdl_launch_dependents();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_vis) return;
-    const int grp = key_group(bp, key[r]);
-    const int prev = r > 0 ? key_group(bp, key[r - 1]) : -1;
-    for (int q = prev + 1; q <= grp; ++q) vis_start[q] = (uint32_t)r;
-    if (r == n_vis - 1)
-        for (int q = grp + 1; q <= bp.n_view * bp.n_oct; ++q) vis_start[q] = (uint32_t)n_vis;
+constexpr int MAX_PAIR_PASSES = 4;  // 8-bit digits of a 32-bit tile index
+constexpr unsigned long long LB_INC = 1ull << 63, LB_AGG = 1ull << 62, LB_VAL = LB_AGG - 1ull;
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
 }
 
-// one thread per (tile, voxel) pair: the pair's voxel is the last record whose first
-// pair offset is <= the pair index (binary search), its tile the matching cell of
-// the voxel's tile rectangle (row-major), so every thread writes exactly one pair
-__global__ void k_emit(const __grid_constant__ BatchParams bp, const uint64_t* __restrict__ off,
-                       const uint64_t* __restrict__ rect_sorted, const uint32_t* __restrict__ sorted_g,
-                       int64_t n_vis, int64_t n_pairs, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+// One thread per visible voxel in depth-key order, blocks taken in order from a counter.
+//  1. the voxel's render record (and normal), its rectangle in depth order, and the start of its
+//     (view, octree) group in vis_start;
+//  2. the block's pair offsets: a block scan of the tile counts, then the block's first pair from
+//     a look-back over the earlier blocks' published counts (the block reads 256 predecessors at a
+//     time; an inclusive one ends the walk; every spin is bounded);
+//  3. the block's pairs, spread over all its threads (a pair finds its voxel by binary search in
+//     the block's offsets), with the tile-sort digits and the per-tile pair counts.
+__global__ void __launch_bounds__(256) k_records_emit(
+    const __grid_constant__ BatchParams bp, const uint32_t* __restrict__ sorted_g,
+    const uint64_t* __restrict__ sorted_key, int64_t n_vis, int64_t n_pairs, const uint32_t* __restrict__ cnt,
+    const uint64_t* __restrict__ rect, VoxRec* __restrict__ rec, float4* __restrict__ nrm,
+    uint64_t* __restrict__ rect_sorted, uint32_t* __restrict__ vis_start, uint32_t* __restrict__ pkey,
+    uint32_t* __restrict__ pval, uint32_t* __restrict__ pair_hist, int pair_passes, uint32_t* __restrict__ tile_cnt,
+    unsigned long long* __restrict__ lb_status, uint32_t* __restrict__ ticket, uint32_t* __restrict__ call_err,
+    uint32_t* __restrict__ dev_err, int spin_limit) {
     pdl_wait();
     pdl_launch_dependents();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pairs) return;
-    int64_t lo = 0, hi = n_vis - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (__ldg(off + mid) <= (uint64_t)p)
-            lo = mid;
-        else
-            hi = mid - 1;
+    __shared__ uint32_t s_blk;
+    __shared__ uint32_t s_off[256];
+    __shared__ uint64_t s_rc[256];
+    __shared__ int32_t s_tb[256], s_tx[256];
+    __shared__ uint32_t s_ws[8];
+    __shared__ uint32_t s_inc[8];
+    __shared__ unsigned long long s_part[8];
+    __shared__ unsigned long long s_excl;
+    __shared__ uint32_t h[MAX_PAIR_PASSES][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_blk = atomicAdd(ticket, 1u);
+    for (int i = tid; i < pair_passes * 256; i += 256) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    const uint32_t blk = s_blk;
+    const int64_t r = (int64_t)blk * 256 + tid;
+    uint32_t c = 0;
+    if (r < n_vis) {
+        const uint32_t g = sorted_g[r];
+        const int view = (int)(g / bp.n_vox);
+        const int64_t gv = (int64_t)g - (int64_t)view * bp.n_vox;
+        const int o = find_octree(bp, gv);
+        const OctParams& P = bp.octs[view * bp.n_oct + o];
+        const int64_t v = gv - bp.vox_offset[o];
+        const Leaf L = decode_leaf(P, P.key[v]);
+        const float4* d4 = reinterpret_cast<const float4*>(P.dens + v * 8);
+        const float4 da = __ldg(d4), db = __ldg(d4 + 1);
+        // min corner relative to the camera centre (octree frame), then the view direction:
+        // camera centre -> voxel centre
+        const float rx = L.mn[0] - P.o_loc[0], ry = L.mn[1] - P.o_loc[1], rz = L.mn[2] - P.o_loc[2];
+        float gx = fmaf(0.5f, L.s, rx);
+        float gy = fmaf(0.5f, L.s, ry);
+        float gz = fmaf(0.5f, L.s, rz);
+        const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+        const float ig = gl > 0.0f ? 1.0f / gl : 0.0f;
+        gx *= ig;
+        gy *= ig;
+        gz *= ig;
+        float b[16];
+        sh_eval_basis(P.sh_degree, gx, gy, gz, b);
+        const int nsh = (P.sh_degree + 1) * (P.sh_degree + 1);
+        const float* shv = P.sh + v * nsh * 3;
+        float cc[3] = {0.5f, 0.5f, 0.5f};
+        if ((nsh * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(shv) & 15) == 0) {
+            // 16-byte loads of the coefficient rows, flattened: element e = 3 q + channel
+#pragma unroll
+            for (int e0 = 0; e0 < 48; e0 += 4) {
+                if (e0 >= nsh * 3) break;
+                const float4 x4 = __ldg(reinterpret_cast<const float4*>(shv + e0));
+                const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) cc[(e0 + i) % 3] = fmaf(b[(e0 + i) / 3], xs[i], cc[(e0 + i) % 3]);
+            }
+        } else {
+            for (int q = 0; q < nsh; ++q) {
+                cc[0] = fmaf(b[q], __ldg(shv + q * 3 + 0), cc[0]);
+                cc[1] = fmaf(b[q], __ldg(shv + q * 3 + 1), cc[1]);
+                cc[2] = fmaf(b[q], __ldg(shv + q * 3 + 2), cc[2]);
+            }
+        }
+        const float c0 = cc[0], c1 = cc[1], c2 = cc[2];
+        VoxRec R;
+        R.v[0] = make_float4(rx, ry, rz, L.s);
+        // the trilinear field as a polynomial in the voxel coordinates (x, y, z) in [0, 1]^3:
+        // rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz, from corner c = x + 2y + 4z
+        const float p1 = da.y - da.x, p2 = da.z - da.x, p3 = db.x - da.x;
+        const float p4 = (da.w - da.z) - p1, p5 = (db.y - db.x) - p1, p6 = (db.z - db.x) - p2;
+        const float p7 = ((db.w - db.z) - (db.y - db.x)) - ((da.w - da.z) - p1);
+        R.v[1] = make_float4(da.x, p1, p2, p4);
+        R.v[2] = make_float4(p3, p5, p6, p7);
+        R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);
+        rec[r] = R;
+        if (nrm) {
+            // voxel normal: minus the direction of the trilinear density gradient at the voxel centre
+            // (per axis: the four corners on its high side minus the four on its low side), rotated
+            // into the world frame by the octree's pose
+            const float gxl = (da.y + da.w + db.y + db.w) - (da.x + da.z + db.x + db.z);
+            const float gyl = (da.z + da.w + db.z + db.w) - (da.x + da.y + db.x + db.y);
+            const float gzl = (db.x + db.y + db.z + db.w) - (da.x + da.y + da.z + da.w);
+            const float g2 = fmaf(gxl, gxl, fmaf(gyl, gyl, gzl * gzl));
+            const float s = g2 > 0.0f ? -rsqrtf(g2) : 0.0f;
+            const float nl[3] = {gxl * s, gyl * s, gzl * s};
+            float nw[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) nw[k] = fmaf(P.Rw[k * 3 + 0], nl[0], fmaf(P.Rw[k * 3 + 1], nl[1], P.Rw[k * 3 + 2] * nl[2]));
+            nrm[r] = make_float4(nw[0], nw[1], nw[2], 0.0f);
+        }
+        c = cnt[g];
+        const uint64_t rc = rect[g];
+        rect_sorted[r] = rc;
+        s_rc[tid] = rc;
+        s_tb[tid] = bp.tile_base[view];
+        s_tx[tid] = bp.views[view].tiles_x;
+        // start of every (view, octree) group in depth order
+        const int grp = key_group(bp, sorted_key[r]);
+        const int prev = r > 0 ? key_group(bp, sorted_key[r - 1]) : -1;
+        for (int q = prev + 1; q <= grp; ++q) vis_start[q] = (uint32_t)r;
+        if (r == n_vis - 1)
+            for (int q = grp + 1; q <= bp.n_view * bp.n_oct; ++q) vis_start[q] = (uint32_t)n_vis;
     }
-    const uint64_t rc = __ldg(rect_sorted + lo);
-    const uint32_t tx0 = (rc & 0xffff) >> 4, tx1 = ((rc >> 16) & 0xffff) >> 4, ty0 = ((rc >> 32) & 0xffff) >> 4;
-    const uint32_t w = tx1 - tx0 + 1;
-    const uint32_t k = (uint32_t)((uint64_t)p - __ldg(off + lo));
-    const int view = (int)(__ldg(sorted_g + lo) / (uint64_t)bp.n_vox);
-    const uint32_t tiles_x = (uint32_t)bp.views[view].tiles_x;
-    pkey[p] = (uint32_t)bp.tile_base[view] + (ty0 + k / w) * tiles_x + tx0 + k % w;
-    pval[p] = (uint32_t)lo;
+    // block exclusive scan of the tile counts
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_ws[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t x = s_ws[w];
+        wbase += w < warp ? x : 0u;
+        total += x;
+    }
+    s_off[tid] = wbase + incl - c;
+    // the block's first pair: publish the block's count, then look back over the earlier blocks,
+    // 256 at a time (thread j reads block blk - 1 - j); the nearest inclusive count ends the walk
+    unsigned long long* mine = lb_status + blk;
+    if (tid == 0) *(volatile unsigned long long*)mine = (blk == 0 ? LB_INC : LB_AGG) | total;
+    unsigned long long excl = 0;
+    if (blk > 0) {
+        for (int64_t t = (int64_t)blk - 1; t >= 0; t -= 256) {
+            const int64_t i = t - tid;
+            unsigned long long v = i >= 0 ? lb_load(lb_status + i) : LB_INC;
+            int spins = 0;
+            while (!(v & (LB_INC | LB_AGG)) && ++spins < spin_limit) v = lb_load(lb_status + i);
+            const bool lost = !(v & (LB_INC | LB_AGG));
+            const unsigned inc = __ballot_sync(0xffffffffu, (v & LB_INC) != 0);
+            if (lane == 0) s_inc[warp] = inc ? warp * 32 + __ffs(inc) - 1 : 256;
+            if (__syncthreads_or(lost)) {
+                if (tid == 0) {
+                    atomicOr(call_err, 1u);
+                    atomicOr(dev_err, 1u);
+                }
+                break;
+            }
+            int stop = 256;  // nearest inclusive predecessor in this window
+#pragma unroll
+            for (int w = 0; w < 8; ++w) stop = min(stop, (int)s_inc[w]);
+            unsigned long long x = tid <= stop ? (v & LB_VAL) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) s_part[warp] = x;
+            __syncthreads();
+#pragma unroll
+            for (int w = 0; w < 8; ++w) excl += s_part[w];
+            __syncthreads();  // s_inc and s_part are rewritten by the next window
+            if (stop < 256) break;
+        }
+        if (tid == 0) *(volatile unsigned long long*)mine = LB_INC | (excl + total);
+    }
+    if (tid == 0) s_excl = excl;
+    __syncthreads();
+    const unsigned long long first = s_excl;
+    const int64_t left = n_vis - (int64_t)blk * 256;
+    const int nb = left < 256 ? (int)left : 256;
+    for (uint32_t i = tid; i < total; i += 256) {
+        int lo = 0, hi = nb - 1;  // last voxel of the block whose first pair is <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const uint64_t rc = s_rc[lo];
+        const uint32_t tx0 = (rc & 0xffff) >> 4, tx1 = ((rc >> 16) & 0xffff) >> 4, ty0 = ((rc >> 32) & 0xffff) >> 4;
+        const uint32_t w = tx1 - tx0 + 1;
+        const uint32_t k = i - s_off[lo];
+        const uint32_t tile = (uint32_t)s_tb[lo] + (ty0 + k / w) * (uint32_t)s_tx[lo] + tx0 + k % w;
+        const unsigned long long p = first + i;
+        if (p < (unsigned long long)n_pairs) {  // only a timed-out look-back can leave the range
+            pkey[p] = tile;
+            pval[p] = blk * 256u + (uint32_t)lo;
+        }
+        atomicAdd(tile_cnt + tile, 1u);
+        for (int q = 0; q < pair_passes; ++q) atomicAdd(&h[q][(tile >> (8 * q)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = tid; i < pair_passes * 256; i += 256) {
+        const uint32_t x = (&h[0][0])[i];
+        if (x) atomicAdd(pair_hist + i, x);
+    }
 }
 
 // For every sorted pair: which of the tile's eight 8x4-pixel blocks (bit sy*2+sx for
@@ -395,21 +527,31 @@ __device__ __forceinline__ int view_of_tile(const BatchParams& bp, int t) {
 }
 
 // one thread per tile-sorted pair: the 8x4-pixel blocks of its tile the voxel's pixel rectangle
-// touches (bit sy * 2 + sx), and the tile's list range from the key boundaries
+// touches (bit sy * 2 + sx), and the [first, end) range of every tile that has pairs, from the key
+// boundaries.  Thread 0 also copies the call's sort flag into its mapped host status word (the sorts
+// have all completed when this kernel runs).
 __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32_t* __restrict__ pkey,
                             const uint32_t* __restrict__ pval, const uint64_t* __restrict__ rect_sorted,
-                            int64_t n_pairs, uint8_t* __restrict__ mask, uint2* __restrict__ range) {
+                            int64_t n_pairs, int64_t n_vis, uint8_t* __restrict__ mask, uint2* __restrict__ range,
+                            const uint64_t* __restrict__ sort_err, volatile uint64_t* status_out) {
     pdl_wait();
     pdl_launch_dependents();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0 && status_out) {
+        *status_out = *(const volatile uint64_t*)sort_err;
+        __threadfence_system();
+    }
     if (p >= n_pairs) return;
     const uint32_t key = pkey[p];
-    if (p == 0 || pkey[p - 1] != key) range[key].x = (uint32_t)p;
-    if (p == n_pairs - 1 || pkey[p + 1] != key) range[key].y = (uint32_t)(p + 1);
+    if (key < (uint32_t)bp.n_tiles) {  // always, unless a sort wait timed out
+        if (p == 0 || pkey[p - 1] != key) range[key].x = (uint32_t)p;
+        if (p == n_pairs - 1 || pkey[p + 1] != key) range[key].y = (uint32_t)(p + 1);
+    }
     const int view = view_of_tile(bp, (int)key);
-    const uint32_t t = pkey[p] - (uint32_t)bp.tile_base[view];
+    const uint32_t t = key - (uint32_t)bp.tile_base[view];
     const uint32_t tiles_x = (uint32_t)bp.views[view].tiles_x;
-    const uint64_t rc = __ldg(rect_sorted + pval[p]);
+    const uint32_t v = min(pval[p], (uint32_t)(n_vis - 1));  // in range unless a sort wait timed out
+    const uint64_t rc = __ldg(rect_sorted + v);
     const int x0 = (int)(t % (uint32_t)tiles_x) * DV_TILE, y0 = (int)(t / (uint32_t)tiles_x) * DV_TILE;
     const int u0 = (int)(rc & 0xffff) - x0, u1 = (int)((rc >> 16) & 0xffff) - x0;
     const int v0 = (int)((rc >> 32) & 0xffff) - y0, v1 = (int)(rc >> 48) - y0;
@@ -430,9 +572,8 @@ __global__ void k_pair_mask(const __grid_constant__ BatchParams bp, const uint32
 // not matter (tiles are independent).
 constexpr int TILE_BUCKETS = 96;
 
-__device__ __forceinline__ int tile_bucket(const BatchParams& bp, const uint2* __restrict__ range, int t) {
-    const uint2 r = range[t];
-    const int b = 31 - __clz((int)(r.y - r.x) + 1);
+__device__ __forceinline__ int tile_bucket(const BatchParams& bp, uint32_t n_pairs, int t) {
+    const int b = 31 - __clz((int)n_pairs + 1);
     const int view = view_of_tile(bp, t);
     const int tl = t - bp.tile_base[view];
     const int tiles_x = bp.views[view].tiles_x;
@@ -447,68 +588,54 @@ __device__ __forceinline__ int tile_bucket(const BatchParams& bp, const uint2* _
     return b + (boxes >= 5 ? 64 : boxes > 0 ? 32 : 0);
 }
 
-__global__ void k_tile_count(const __grid_constant__ BatchParams bp, const uint2* __restrict__ range, int n_tiles,
-                             uint32_t* __restrict__ cnt) {
+// one thread per tile: its bucket (kept in bucket[t]) into the global bucket counts hist[96]; a tile
+// without pairs gets the empty range (the pair-mask kernel wrote the others)
+__global__ void __launch_bounds__(256) k_tile_count(const __grid_constant__ BatchParams bp,
+                                                    const uint32_t* __restrict__ tile_cnt, int n_tiles,
+                                                    uint8_t* __restrict__ bucket, uint2* __restrict__ range,
+                                                    uint32_t* __restrict__ hist) {
     pdl_wait();
     pdl_launch_dependents();
     __shared__ uint32_t h[TILE_BUCKETS];
     if (threadIdx.x < TILE_BUCKETS) h[threadIdx.x] = 0;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_tiles) atomicAdd(&h[tile_bucket(bp, range, t)], 1u);
+    if (t < n_tiles) {
+        const uint32_t c = tile_cnt[t];
+        if (c == 0) range[t] = make_uint2(0u, 0u);
+        const int b = tile_bucket(bp, c, t);
+        bucket[t] = (uint8_t)b;
+        atomicAdd(&h[b], 1u);
+    }
     __syncthreads();
-    if (threadIdx.x < TILE_BUCKETS && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x < TILE_BUCKETS && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
 }
 
-__global__ void k_tile_offsets(uint32_t* __restrict__ cnt_off) {
+// one thread per tile: each block turns the 96 bucket counts into bucket starts, heaviest bucket of
+// the first group first, then reserves one run per (block, bucket) from the cursors
+__global__ void __launch_bounds__(256) k_tile_scatter(const uint8_t* __restrict__ bucket, int n_tiles,
+                                                      const uint32_t* __restrict__ hist,
+                                                      uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
     pdl_wait();
     pdl_launch_dependents();
-    // cnt_off[0..95] counts -> cnt_off[96..191] start of each bucket, from the heaviest bucket of the
-    // first group down
-    if (threadIdx.x == 0) {
+    __shared__ uint32_t start[TILE_BUCKETS], h[TILE_BUCKETS], base[TILE_BUCKETS];
+    const int tid = threadIdx.x;
+    if (tid < TILE_BUCKETS) h[tid] = 0;
+    if (tid == 0) {
         uint32_t run = 0;
         for (int b = TILE_BUCKETS - 1; b >= 0; --b) {
-            cnt_off[TILE_BUCKETS + b] = run;
-            run += cnt_off[b];
+            start[b] = run;
+            run += hist[b];
         }
     }
-}
-
-__global__ void k_tile_scatter(const __grid_constant__ BatchParams bp, const uint2* __restrict__ range, int n_tiles,
-                               uint32_t* __restrict__ off, uint32_t* __restrict__ order) {
-    pdl_wait();
-    pdl_launch_dependents();
-    // block-local ranks first, then one global reservation per (block, bucket)
-    __shared__ uint32_t h[TILE_BUCKETS], base[TILE_BUCKETS];
-    if (threadIdx.x < TILE_BUCKETS) h[threadIdx.x] = 0;
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = t < n_tiles ? tile_bucket(bp, range, t) : -1;
+    const int t = blockIdx.x * blockDim.x + tid;
+    const int b = t < n_tiles ? bucket[t] : -1;
     const uint32_t rank = b >= 0 ? atomicAdd(&h[b], 1u) : 0u;
     __syncthreads();
-    if (threadIdx.x < TILE_BUCKETS && h[threadIdx.x])
-        base[threadIdx.x] = atomicAdd(&off[threadIdx.x], h[threadIdx.x]);
+    if (tid < TILE_BUCKETS && h[tid]) base[tid] = start[tid] + atomicAdd(&cursor[tid], h[tid]);
     __syncthreads();
     if (b >= 0) order[base[b] + rank] = (uint32_t)t;
-}
-
-inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-}  // namespace
-
-cudaError_t launch_tile_order(const BatchParams& bp, const uint2* tile_range, int n_tiles, uint32_t* scratch192,
-                              uint32_t* order, cudaStream_t s) {
-    if (n_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(scratch192, 0, 2 * TILE_BUCKETS * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    launch_pdl(k_tile_count, dim3(nblk(n_tiles, 256)), dim3(256), s, bp, tile_range, n_tiles, scratch192);
-    count_launches(1);
-    launch_pdl(k_tile_offsets, dim3(1), dim3(32), s, scratch192);
-    count_launches(1);
-    launch_pdl(k_tile_scatter, dim3(nblk(n_tiles, 256)), dim3(256), s, bp, tile_range, n_tiles,
-               scratch192 + TILE_BUCKETS, order);
-    count_launches(1);
-    return cudaGetLastError();
 }
 
 // copies n counters into mapped host memory (system-scope stores, visible to the host once the
@@ -526,6 +653,12 @@ __global__ void k_publish(const uint64_t* __restrict__ src, volatile uint64_t* d
     __threadfence_system();
 }
 
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+int key_passes(int n_bits) { return (n_bits + 7) / 8; }
+
 cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n, uint32_t* spin_err, int flag_idx,
                            cudaStream_t s) {
     launch_pdl(k_publish, dim3(1), dim3(32), s, src, host_mapped_dst, n, spin_err, flag_idx);
@@ -533,55 +666,55 @@ cudaError_t launch_publish(const uint64_t* src, uint64_t* host_mapped_dst, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* skey, uint32_t* vis,
-                           uint32_t* flags, unsigned long long* totals, cudaStream_t s) {
+cudaError_t launch_project(const BatchParams& bp, uint32_t* cnt, uint64_t* rect, uint64_t* out_key, uint32_t* out_g,
+                           uint32_t* key_hist, int key_bits, unsigned long long* scal, uint64_t* host_out, uint64_t seq,
+                           uint32_t* spin_err, unsigned long long* work, cudaStream_t s) {
     const int64_t n = bp.n_vox * bp.n_view;
-    if (n <= 0) return cudaSuccess;
-    launch_pdl(k_project, dim3(nblk(n, 256)), dim3(256), s, bp, cnt, rect, skey, vis, flags, totals);
+    const int passes = key_passes(key_bits);
+    if (passes > MAX_KEY_PASSES) return cudaErrorInvalidValue;
+    // with no voxel at all, one empty block still clears the work words and reports the (zero) sizes
+    launch_pdl(k_project, dim3(n > 0 ? nblk(n, 256) : 1u), dim3(256), s, bp, cnt, rect, out_key, out_g, key_hist,
+               passes, scal, (volatile uint64_t*)host_out, seq, spin_err, work);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const uint32_t* vis, const uint32_t* pos, const uint64_t* skey, int64_t n,
-                           uint64_t* out_key, uint32_t* out_val, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    launch_pdl(k_compact, dim3(nblk(n, 256)), dim3(256), s, vis, pos, skey, n, out_key, out_val);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_records(const BatchParams& bp, const uint32_t* sorted_g, int64_t n_vis, const uint32_t* cnt,
-                           const uint64_t* rect, VoxRec* rec, float4* nrm, uint32_t* cnt_sorted,
-                           uint64_t* rect_sorted, cudaStream_t s) {
-    if (n_vis <= 0) return cudaSuccess;
-    launch_pdl(k_records, dim3(nblk(n_vis, 256)), dim3(256), s, bp, sorted_g, n_vis, cnt, rect, rec, nrm, cnt_sorted, rect_sorted);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_vis_start(const BatchParams& bp, const uint64_t* sorted_key, int64_t n_vis, uint32_t* vis_start,
-                             cudaStream_t s) {
+cudaError_t launch_records_emit(const BatchParams& bp, const uint32_t* sorted_g, const uint64_t* sorted_key,
+                                int64_t n_vis, int64_t n_pairs, const uint32_t* cnt, const uint64_t* rect,
+                                VoxRec* rec, float4* nrm, uint64_t* rect_sorted, uint32_t* vis_start,
+                                uint32_t* pair_key, uint32_t* pair_val, uint32_t* pair_hist, int tile_bits,
+                                uint32_t* tile_cnt, unsigned long long* lb_status, uint32_t* ticket,
+                                uint32_t* call_err, uint32_t* dev_err, cudaStream_t s) {
     if (n_vis <= 0) return cudaMemsetAsync(vis_start, 0, sizeof(uint32_t) * (bp.n_view * bp.n_oct + 1), s);
-    launch_pdl(k_vis_start, dim3(nblk(n_vis, 256)), dim3(256), s, bp, sorted_key, n_vis, vis_start);
+    const int passes = key_passes(tile_bits);
+    if (passes > MAX_PAIR_PASSES || !call_err || !dev_err) return cudaErrorInvalidValue;
+    launch_pdl(k_records_emit, dim3(nblk(n_vis, 256)), dim3(256), s, bp, sorted_g, sorted_key, n_vis, n_pairs, cnt,
+               rect, rec, nrm, rect_sorted, vis_start, pair_key, pair_val, pair_hist, passes, tile_cnt, lb_status,
+               ticket, call_err, dev_err, (int)(1 << 22));
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const BatchParams& bp, const uint64_t* off, const uint64_t* rect_sorted,
-                        const uint32_t* sorted_g, int64_t n_vis, int64_t n_pairs, uint32_t* pair_key,
-                        uint32_t* pair_val, cudaStream_t s) {
-    if (n_vis <= 0 || n_pairs <= 0) return cudaSuccess;
-    launch_pdl(k_emit, dim3(nblk(n_pairs, 256)), dim3(256), s, bp, off, rect_sorted, sorted_g, n_vis, n_pairs, pair_key, pair_val);
+int64_t records_emit_blocks(int64_t n_vis) { return (n_vis + 255) / 256; }
+
+cudaError_t launch_pair_mask(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
+                             const uint64_t* rect_sorted, int64_t n_pairs, int64_t n_vis, uint8_t* mask,
+                             uint2* tile_range, const uint64_t* sort_err, uint64_t* status_host, cudaStream_t s) {
+    if (n_pairs <= 0) return launch_publish(sort_err, status_host, 1, nullptr, -1, s);
+    launch_pdl(k_pair_mask, dim3(nblk(n_pairs, 256)), dim3(256), s, bp, pair_key, pair_val, rect_sorted, n_pairs,
+               n_vis, mask, tile_range, sort_err, (volatile uint64_t*)status_host);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_mask_ranges(const BatchParams& bp, const uint32_t* pair_key, const uint32_t* pair_val,
-                                    const uint64_t* rect_sorted, int64_t n_pairs, uint8_t* mask, uint2* tile_range,
-                                    int n_tiles, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(tile_range, 0, sizeof(uint2) * (size_t)n_tiles, s);
-    if (e != cudaSuccess || n_pairs <= 0) return e;
-    launch_pdl(k_pair_mask, dim3(nblk(n_pairs, 256)), dim3(256), s, bp, pair_key, pair_val, rect_sorted, n_pairs, mask, tile_range);
+cudaError_t launch_tile_order(const BatchParams& bp, const uint32_t* tile_cnt, int n_tiles, uint2* range,
+                              uint8_t* bucket, uint32_t* scratch192, uint32_t* order, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    launch_pdl(k_tile_count, dim3(nblk(n_tiles, 256)), dim3(256), s, bp, tile_cnt, n_tiles, bucket, range,
+               scratch192);
+    count_launches(1);
+    launch_pdl(k_tile_scatter, dim3(nblk(n_tiles, 256)), dim3(256), s, (const uint8_t*)bucket, n_tiles,
+               (const uint32_t*)scratch192, scratch192 + TILE_BUCKETS, order);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -270,7 +270,7 @@ constexpr int OS_THREADS = 256;
 constexpr int OS_MAX_PASSES = 8;
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_VAL = (1u << 30) - 1u;
 constexpr int OS_SPIN_LIMIT = 1 << 22;  // reads of a predecessor's status word before a pass gives up (~seconds)
-constexpr int OS_LOOK = 8;  // predecessors read per look-back step
+constexpr int OS_LOOK = 32;  // predecessors read per look-back step (their loads are in flight together)
 
 template <typename K>
 __global__ void __launch_bounds__(OS_THREADS) k_os_hist(const K* __restrict__ keys, int64_t n, int n_passes,
@@ -293,23 +293,12 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_hist(const K* __restrict__ ke
         if (h[p][threadIdx.x]) atomicAdd(&ghist[p * RS_RADIX + threadIdx.x], h[p][threadIdx.x]);
 }
 
-// exclusive scan of each pass's 256 digit counts (one block per pass)
-__global__ void k_os_bins(uint32_t* __restrict__ ghist) {
-    pdl_wait();
-    pdl_launch_dependents();
-    __shared__ uint32_t tot;
-    uint32_t* h = ghist + blockIdx.x * RS_RADIX;
-    const uint32_t x = h[threadIdx.x];
-    const uint32_t e = block_excl_scan<uint32_t>(x, &tot);
-    h[threadIdx.x] = e;
-}
-
 __device__ __forceinline__ uint32_t os_load(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 
 template <typename K, int ROUNDS>
 __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                          int64_t n, int shift, uint32_t mask,
-                                                         const uint32_t* __restrict__ goff,
+                                                         const uint32_t* __restrict__ hist,
                                                          uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
                                                          uint32_t* __restrict__ err, K* __restrict__ okeys,
                                                          uint32_t* __restrict__ ovals, int spin_limit) {
@@ -319,24 +308,37 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
     __shared__ uint32_t run[RS_RADIX];
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
     __shared__ uint32_t s_base[RS_RADIX];
+    __shared__ uint32_t s_tot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     run[tid] = 0;
     for (int w = 0; w < RS_WARPS; ++w) wcnt[w][tid] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const int64_t base = (int64_t)tile * OS_THREADS * ROUNDS;
-    const unsigned lt = (1u << lane) - 1u;
+    // The tile's keys are loaded for tile blockIdx.x while the counter's answer is on its way (blocks
+    // are almost always handed out in index order); a block that drew another tile loads again.
     K key[ROUNDS];
     uint32_t val[ROUNDS], dig[ROUNDS], rank[ROUNDS];
-    // all of the tile's loads first (no barrier between them), then the ranking rounds
+    auto load_tile = [&](uint32_t tl) {
+        const int64_t b0 = (int64_t)tl * OS_THREADS * ROUNDS;
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            const int64_t i = b0 + (int64_t)r * OS_THREADS + tid;
+            const bool ok = i < n;
+            key[r] = ok ? keys[i] : K(0);
+            val[r] = ok ? vals[i] : 0u;
+        }
+    };
+    load_tile(blockIdx.x);
+    // first slot of every digit: exclusive scan of the pass's digit counts (every tile scans the 256
+    // counts itself, which costs less than a launch)
+    const uint32_t goff = block_excl_scan<uint32_t>(hist[tid], &s_tot);
+    const uint32_t tile = s_tile;
+    if (tile != blockIdx.x) load_tile(tile);  // block-uniform
+    const int64_t base = (int64_t)tile * OS_THREADS * ROUNDS;
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const int64_t i = base + (int64_t)r * OS_THREADS + tid;
-        const bool ok = i < n;
-        key[r] = ok ? keys[i] : K(0);
-        val[r] = ok ? vals[i] : 0u;
-        dig[r] = ok ? ((uint32_t)(key[r] >> shift) & mask) : 0xffffffffu;
+        dig[r] = i < n ? ((uint32_t)(key[r] >> shift) & mask) : 0xffffffffu;
     }
     // stable tile-local ranks, round by round
 #pragma unroll
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
     uint32_t* st = status + (size_t)tile * RS_RADIX + tid;
     if (tile == 0) {
         *(volatile uint32_t*)st = OS_INC | mine;
-        s_base[tid] = goff[tid];
+        s_base[tid] = goff;
     } else {
         *(volatile uint32_t*)st = OS_AGG | mine;
         // look back OS_LOOK predecessors at a time: their status words are loaded together, then
@@ -401,9 +403,9 @@ __global__ void __launch_bounds__(OS_THREADS) k_os_pass(const K* __restrict__ ke
             }
             t -= OS_LOOK;
         }
-        __threadfence();
+        // (no fence: readers take nothing from this tile but the word itself)
         *(volatile uint32_t*)st = OS_INC | ((excl + mine) & OS_VAL);
-        s_base[tid] = goff[tid] + excl;
+        s_base[tid] = goff + excl;
     }
     __syncthreads();
 #pragma unroll
@@ -438,8 +440,6 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
     uint32_t* perr = call_err ? call_err : err;
     launch_pdl(k_os_hist<K>, dim3((unsigned)(hist_blocks < 1 ? 1 : hist_blocks)), dim3(OS_THREADS), s, keys, n, passes, n_bits, ghist);
     count_launches(1);
-    launch_pdl(k_os_bins, dim3(passes), dim3(RS_RADIX), s, ghist);
-    count_launches(1);
     K* src_k = keys;
     uint32_t* src_v = vals;
     K* dst_k = keys_alt;
@@ -464,20 +464,110 @@ cudaError_t onesweep_impl(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals
 // Keys per tile: 256 x ROUNDS, growing with n so that a pass has about one to two tiles per
 // SM: fewer, larger tiles shorten the look-back chains, which dominate small passes (a 112k-key
 // depth sort: 2 rounds 65 us, 4 rounds 56 us, 8 rounds 61 us for its 5 passes).
+int onesweep_rounds(int64_t n, int n_sm) {
+    const int64_t per_round = (int64_t)OS_THREADS * n_sm;
+    return n <= per_round ? 1 : n <= 2 * per_round ? 2 : n <= 4 * per_round ? 4 : 8;
+}
+
 template <typename K>
 cudaError_t onesweep(K*& keys, uint32_t*& vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int n_bits,
                      uint32_t* call_err, Arena& ar, cudaStream_t s) {
     const int n_sm = sm_count();
-    const int64_t per_round = (int64_t)OS_THREADS * n_sm;
-    if (n <= per_round) return onesweep_impl<K, 1>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
-    if (n <= 2 * per_round)
-        return onesweep_impl<K, 2>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
-    if (n <= 4 * per_round)
-        return onesweep_impl<K, 4>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
-    return onesweep_impl<K, 8>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    switch (onesweep_rounds(n, n_sm)) {
+    case 1: return onesweep_impl<K, 1>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    case 2: return onesweep_impl<K, 2>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    case 4: return onesweep_impl<K, 4>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    default: return onesweep_impl<K, 8>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, n_sm, ar, s);
+    }
+}
+
+// The passes of a sort whose digit counts the producer of the keys has already taken.  The input
+// buffers are overwritten (they are one side of the ping-pong); the last pass writes (*keys_out,
+// vals_out), and a null *keys_out takes whichever ping-pong buffer that pass does not read.
+template <typename K, int ROUNDS>
+cudaError_t counted_passes(K* keys, uint32_t* vals, K* keys_tmp, uint32_t* vals_tmp, K** keys_out,
+                           uint32_t* vals_out, int64_t n, int n_bits, const uint32_t* hist, uint32_t* words,
+                           uint32_t* call_err, cudaStream_t s) {
+    const int passes = (n_bits + 7) / 8;
+    const int64_t n_tiles = (n + (int64_t)OS_THREADS * ROUNDS - 1) / ((int64_t)OS_THREADS * ROUNDS);
+    uint32_t* counters = words;         // [passes]
+    uint32_t* status = words + passes;  // [passes][n_tiles][256]
+    K* sk = keys;
+    uint32_t* sv = vals;
+    for (int p = 0; p < passes; ++p) {
+        const bool last = p == passes - 1;
+        K* dk = sk == keys ? keys_tmp : keys;
+        uint32_t* dvv = sv == vals ? vals_tmp : vals;
+        if (last) {
+            if (*keys_out) dk = *keys_out;
+            dvv = vals_out;
+        }
+        const int shift = 8 * p;
+        const int bits = n_bits - shift < 8 ? n_bits - shift : 8;
+        launch_pdl(k_os_pass<K, ROUNDS>, dim3((unsigned)n_tiles), dim3(OS_THREADS), s, (const K*)sk,
+                   (const uint32_t*)sv, n, shift, (1u << bits) - 1u, hist + p * RS_RADIX,
+                   status + (size_t)p * n_tiles * RS_RADIX, counters + p, call_err, dk, dvv, OS_SPIN_LIMIT);
+        count_launches(1);
+        sk = dk;
+        sv = dvv;
+    }
+    *keys_out = sk;
+    return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t sort_counted(K* keys, uint32_t* vals, K* keys_tmp, uint32_t* vals_tmp, K*& keys_out, uint32_t* vals_out,
+                         int64_t n, int n_bits, const uint32_t* hist, uint32_t* words, uint32_t* call_err, Arena& ar,
+                         cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (n_bits <= 0 || n == 1) {
+        if (!keys_out) keys_out = keys_tmp;
+        cudaError_t e = cudaMemcpyAsync(keys_out, keys, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals_out, vals, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        return e;
+    }
+    if (n >= (int64_t)OS_VAL || (n_bits + 7) / 8 > OS_MAX_PASSES) {
+        // counts beyond the 30-bit status words: reduce-then-scan passes, then a copy to the outputs
+        K* kk = keys;
+        uint32_t* vv = vals;
+        cudaError_t e = radix_impl<K>(kk, vv, keys_tmp, vals_tmp, n, n_bits, ar, s);
+        if (e != cudaSuccess) return e;
+        if (!keys_out) keys_out = kk;
+        if (keys_out != kk) e = cudaMemcpyAsync(keys_out, kk, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && vals_out != vv)
+            e = cudaMemcpyAsync(vals_out, vv, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        return e;
+    }
+    switch (onesweep_rounds(n, sm_count())) {
+    case 1: return counted_passes<K, 1>(keys, vals, keys_tmp, vals_tmp, &keys_out, vals_out, n, n_bits, hist, words, call_err, s);
+    case 2: return counted_passes<K, 2>(keys, vals, keys_tmp, vals_tmp, &keys_out, vals_out, n, n_bits, hist, words, call_err, s);
+    case 4: return counted_passes<K, 4>(keys, vals, keys_tmp, vals_tmp, &keys_out, vals_out, n, n_bits, hist, words, call_err, s);
+    default: return counted_passes<K, 8>(keys, vals, keys_tmp, vals_tmp, &keys_out, vals_out, n, n_bits, hist, words, call_err, s);
+    }
 }
 
 }  // namespace
+
+int64_t sort_counted_words(int64_t n, int n_bits) {
+    const int passes = (n_bits + 7) / 8;
+    const int64_t per_tile = (int64_t)OS_THREADS * onesweep_rounds(n, sm_count());
+    const int64_t n_tiles = (n + per_tile - 1) / per_tile;
+    return passes + (int64_t)passes * n_tiles * RS_RADIX;
+}
+
+cudaError_t sort_counted_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp, uint32_t* vals_tmp,
+                             uint64_t*& keys_out, uint32_t* vals_out, int64_t n, int n_bits, const uint32_t* hist,
+                             uint32_t* words, uint32_t* call_err, Arena& ar, cudaStream_t s) {
+    return sort_counted<uint64_t>(keys, vals, keys_tmp, vals_tmp, keys_out, vals_out, n, n_bits, hist, words,
+                                  call_err, ar, s);
+}
+
+cudaError_t sort_counted_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                             uint32_t*& keys_out, uint32_t* vals_out, int64_t n, int n_bits, const uint32_t* hist,
+                             uint32_t* words, uint32_t* call_err, Arena& ar, cudaStream_t s) {
+    return sort_counted<uint32_t>(keys, vals, keys_tmp, vals_tmp, keys_out, vals_out, n, n_bits, hist, words,
+                                  call_err, ar, s);
+}
 
 uint32_t* spin_error_word() {
     void* p = nullptr;

@@ -98,7 +98,7 @@ int64_t request_bytes(const dv_server* S, const Request& r) {
     const int64_t n_vis = (int64_t)std::ceil(S->vis_frac * (double)S->n_vox);
     const int64_t P = (int64_t)std::ceil(S->pairs_per_tile * (double)tiles);
     const int64_t b = dv::render_need_before(1, (int64_t)S->oct.size(), S->n_vox, tiles, r.pixels) +
-                      dv::render_need_after(n_vis, P, S->key_bits, bits_of(std::max<int64_t>(tiles, 2)), false);
+                      dv::render_need_after(n_vis, P, tiles, S->key_bits, bits_of(std::max<int64_t>(tiles, 2)), false);
     return b + b / 4;
 }
 
