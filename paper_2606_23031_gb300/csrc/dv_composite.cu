@@ -64,6 +64,7 @@ constexpr int NTA_LARGE = 8;
 
 struct PixBase {
     float C0, C1, C2, D, T;
+    float R;  // residual form of the backward: sum over the composited segments of w (dL/dC . c + dL/dD mid)
     uint32_t n;
     uint32_t tests, boxes;  // work counters: voxel slab tests, actor box tests
     bool done;
@@ -79,6 +80,7 @@ struct BwdBase {
     // upstream gradient and the forward's results
     float g0, g1, g2, gD, gA;
     float Cf0, Cf1, Cf2, Df, Tend;
+    float base;  // dL/dA T_end - (dL/dC . C_final + dL/dD D_final [+ dL/dN . N_final]), for the residual form
 };
 template <bool NRM>
 struct Bwd : BwdBase {};
@@ -274,14 +276,64 @@ __device__ __forceinline__ void composite_tau(Pix<NRM>& ps, float tau, float4 co
     if (ps.T < eps_stop) ps.done = true;
 }
 
+// d L / d dens[c] of one segment, added into acc[0..7], from gt = d L / d tau
+template <int KS>
+__device__ __forceinline__ void seg_density_grad(float gt, const float* dtd, const float* sxyz, float* acc) {
+    if constexpr (KS == 1) {
+        // gt s w_c(x, y, z): the trilinear weights with gt s folded into the y-z products
+        const float a = gt * sxyz[0];
+        const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
+        const float x0 = 1.0f - x;
+        const float ay0 = a * (1.0f - y), ay1 = a * y;
+        const float c00 = ay0 * (1.0f - z), c10 = ay1 * (1.0f - z), c01 = ay0 * z, c11 = ay1 * z;
+        acc[0] = fmaf(x0, c00, acc[0]);
+        acc[1] = fmaf(x, c00, acc[1]);
+        acc[2] = fmaf(x0, c10, acc[2]);
+        acc[3] = fmaf(x, c10, acc[3]);
+        acc[4] = fmaf(x0, c01, acc[4]);
+        acc[5] = fmaf(x, c01, acc[5]);
+        acc[6] = fmaf(x0, c11, acc[6]);
+        acc[7] = fmaf(x, c11, acc[7]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = fmaf(gt, dtd[c], acc[c]);
+    }
+}
+
 // Composites one segment (with the stop test when STOP); with GRAD also adds
 // this segment's gradient into acc[0..10] (8 densities, 3 colour channels).
-template <bool GRAD, bool STOP, int KS, bool NRM, bool WEX = false>
+// RF (backward only): the residual form.  The gradient of tau_k only needs the upstream-weighted
+// sums, dL/dtau_k = T_{k+1} s_k - (K - R_k) + dL/dA T_end with s_k = dL/dC . c_k + dL/dD mid_k
+// (+ dL/dN . n_k), K the same sum over the final images and R_k = sum_{j <= k} w_j s_j; so the lane
+// carries the one scalar R instead of the prefix colour, depth (and normal).
+template <bool GRAD, bool STOP, int KS, bool NRM, bool WEX = false, bool RF = false>
 __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp, float4 da, float4 db,
                                             float4 col, float4 nv, const float* rel, const float* d, float t0,
                                             float t1, float* acc, uint32_t r = 0, ExportSink* ex = nullptr) {
     float dtd[8], sxyz[4];
     const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd, sxyz);
+    if constexpr (GRAD && RF) {
+        const float e = __expf(-tau);
+        const float w = ps.T * (1.0f - e);
+        const float mid = 0.5f * (t0 + t1);
+        float s = fmaf(bw.g0, col.x, fmaf(bw.g1, col.y, fmaf(bw.g2, col.z, bw.gD * mid)));
+        if constexpr (NRM) {
+            s = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, s)));
+            acc[11] = fmaf(bw.gN0, w, acc[11]);
+            acc[12] = fmaf(bw.gN1, w, acc[12]);
+            acc[13] = fmaf(bw.gN2, w, acc[13]);
+        }
+        ps.R = fmaf(w, s, ps.R);
+        ps.T = ps.T * e;
+        ps.n += 1;
+        const float gt = fmaf(ps.T, s, bw.base + ps.R);
+        seg_density_grad<KS>(gt, dtd, sxyz, acc);
+        acc[8] = fmaf(bw.g0, w, acc[8]);
+        acc[9] = fmaf(bw.g1, w, acc[9]);
+        acc[10] = fmaf(bw.g2, w, acc[10]);
+        if (STOP && ps.T < bp.eps_stop) ps.done = true;
+        return;
+    }
     const float w = composite_step<NRM>(ps, tau, col, nv, t0, t1);
     if constexpr (WEX) {
         if (ex->n < ex->lim) {
@@ -306,25 +358,7 @@ __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, co
             acc[12] = fmaf(bw.gN1, w, acc[12]);
             acc[13] = fmaf(bw.gN2, w, acc[13]);
         }
-        if constexpr (KS == 1) {
-            // d L / d dens[c] = gt s w_c(x, y, z): the trilinear weights with gt s folded into the y-z products
-            const float a = gt * sxyz[0];
-            const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
-            const float x0 = 1.0f - x;
-            const float ay0 = a * (1.0f - y), ay1 = a * y;
-            const float c00 = ay0 * (1.0f - z), c10 = ay1 * (1.0f - z), c01 = ay0 * z, c11 = ay1 * z;
-            acc[0] = fmaf(x0, c00, acc[0]);
-            acc[1] = fmaf(x, c00, acc[1]);
-            acc[2] = fmaf(x0, c10, acc[2]);
-            acc[3] = fmaf(x, c10, acc[3]);
-            acc[4] = fmaf(x0, c01, acc[4]);
-            acc[5] = fmaf(x, c01, acc[5]);
-            acc[6] = fmaf(x0, c11, acc[6]);
-            acc[7] = fmaf(x, c11, acc[7]);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = fmaf(gt, dtd[c], acc[c]);
-        }
+        seg_density_grad<KS>(gt, dtd, sxyz, acc);
         acc[8] = fmaf(bw.g0, w, acc[8]);
         acc[9] = fmaf(bw.g1, w, acc[9]);
         acc[10] = fmaf(bw.g2, w, acc[10]);
@@ -503,6 +537,9 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];  // sub-list of octree o: [s_sub[o], s_sub[o+1])
     __shared__ uint32_t s_vs[DV_MAX_OCTREES + 1];   // first record of octree o in this view
     constexpr bool ACT = NTA > 0;
+    // the backward of tiles that no actor box covers carries the residual form (no actor partials
+    // or replays need the prefix colour and depth there)
+    constexpr bool RFORM = BWD && !ACT;
     __shared__ bool s_flag[ACT ? DV_MAX_OCTREES : 1];  // actor o's box covers this tile
     __shared__ int16_t s_act[ACT ? DV_MAX_OCTREES : 1];
     __shared__ float s_iv[ACT ? NTA : 1][2][ACT ? CT_THREADS : 1];
@@ -563,6 +600,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     ps.C0 = ps.C1 = ps.C2 = ps.D = 0.0f;
     if constexpr (NRM) ps.N0 = ps.N1 = ps.N2 = 0.0f;
     ps.T = 1.0f;
+    ps.R = 0.0f;
     ps.n = 0;
     ps.tests = 0;
     ps.boxes = 0;
@@ -604,6 +642,8 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
             bw.Nf2 = fp.normal[lpix * 3 + 2];
         }
     }
+    bw.base = bw.gA * bw.Tend - fmaf(bw.g0, bw.Cf0, fmaf(bw.g1, bw.Cf1, fmaf(bw.g2, bw.Cf2, bw.gD * bw.Df)));
+    if constexpr (NRM) bw.base -= fmaf(bw.gN0, bw.Nf0, fmaf(bw.gN1, bw.Nf1, bw.gN2 * bw.Nf2));
     // tile set-up, all loads independent of one another: the view's octree boundaries in
     // the record order, and which actor boxes cover this tile
     for (int i = tid; i <= n_oct; i += CT_THREADS) {
@@ -917,7 +957,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                     float cur = fmaxf(t_in, tau_cur);
                     while (nxt.o >= 0 && nxt.a < t_out && !ps.done) {
                         if (nxt.a > cur) {
-                            add_segment<BWD, true, KS, NRM, WEX>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, nxt.a,
+                            add_segment<BWD, true, KS, NRM, WEX, RFORM>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, nxt.a,
                                                                  acc, s_r[slot][j], &ex);
                             contributed = true;
                             if (ps.done) break;
@@ -929,7 +969,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                         ps.boxes += n_ta;
                     }
                     if (!ps.done && t_out > cur) {
-                        add_segment<BWD, true, KS, NRM, WEX>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, t_out, acc,
+                        add_segment<BWD, true, KS, NRM, WEX, RFORM>(ps, bw, bp, da, dd, col, nv, rel, db_, cur, t_out, acc,
                                                              s_r[slot][j], &ex);
                         contributed = true;
                     }
