@@ -312,25 +312,28 @@ __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, co
                                             float t1, float* acc, uint32_t r = 0, ExportSink* ex = nullptr) {
     float dtd[8], sxyz[4];
     const float tau = seg_tau<GRAD, KS>(da, db, col.w, rel, d, t0, t1, bp.K, bp.inv_k, bp.activation, dtd, sxyz);
-    if constexpr (GRAD && RF) {
+    if constexpr (RF) {
+        // (without GRAD: an actor's partial in the backward, R only)
         const float e = __expf(-tau);
         const float w = ps.T * (1.0f - e);
         const float mid = 0.5f * (t0 + t1);
         float s = fmaf(bw.g0, col.x, fmaf(bw.g1, col.y, fmaf(bw.g2, col.z, bw.gD * mid)));
-        if constexpr (NRM) {
-            s = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, s)));
-            acc[11] = fmaf(bw.gN0, w, acc[11]);
-            acc[12] = fmaf(bw.gN1, w, acc[12]);
-            acc[13] = fmaf(bw.gN2, w, acc[13]);
-        }
+        if constexpr (NRM) s = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, s)));
         ps.R = fmaf(w, s, ps.R);
         ps.T = ps.T * e;
         ps.n += 1;
-        const float gt = fmaf(ps.T, s, bw.base + ps.R);
-        seg_density_grad<KS>(gt, dtd, sxyz, acc);
-        acc[8] = fmaf(bw.g0, w, acc[8]);
-        acc[9] = fmaf(bw.g1, w, acc[9]);
-        acc[10] = fmaf(bw.g2, w, acc[10]);
+        if constexpr (GRAD) {
+            const float gt = fmaf(ps.T, s, bw.base + ps.R);
+            seg_density_grad<KS>(gt, dtd, sxyz, acc);
+            acc[8] = fmaf(bw.g0, w, acc[8]);
+            acc[9] = fmaf(bw.g1, w, acc[9]);
+            acc[10] = fmaf(bw.g2, w, acc[10]);
+            if constexpr (NRM) {
+                acc[11] = fmaf(bw.gN0, w, acc[11]);
+                acc[12] = fmaf(bw.gN1, w, acc[12]);
+                acc[13] = fmaf(bw.gN2, w, acc[13]);
+            }
+        }
         if (STOP && ps.T < bp.eps_stop) ps.done = true;
         return;
     }
@@ -471,7 +474,7 @@ __device__ __noinline__ void walk_actor_lane(Pix<NRM>& ps, const Bwd<NRM>& bw, c
 #pragma unroll
         for (int c = 0; c < GradLayout<NRM>::NV; ++c) acc[c] = 0.0f;
         const float4 nv = NRM ? __ldg(bp.nrm + r) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        add_segment<GRAD, true, KS, NRM, WEX>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), nv, rel, d, t0,
+        add_segment<GRAD, true, KS, NRM, WEX, GRAD>(ps, bw, bp, __ldg(R + 1), __ldg(R + 2), __ldg(R + 3), nv, rel, d, t0,
                                               t1, acc, r, ex);
         if (GRAD) atomic_grad<NRM>(grad_rec, r, acc);
     }
@@ -537,9 +540,9 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     __shared__ uint32_t s_sub[DV_MAX_OCTREES + 1];  // sub-list of octree o: [s_sub[o], s_sub[o+1])
     __shared__ uint32_t s_vs[DV_MAX_OCTREES + 1];   // first record of octree o in this view
     constexpr bool ACT = NTA > 0;
-    // the backward of tiles that no actor box covers carries the residual form (no actor partials
-    // or replays need the prefix colour and depth there)
-    constexpr bool RFORM = BWD && !ACT;
+    // the backward carries the residual form: the actor partials, the states recorded at actor
+    // entries and the replays hold (R, T) instead of the prefix colour, depth (and normal)
+    constexpr bool RFORM = BWD;
     __shared__ bool s_flag[ACT ? DV_MAX_OCTREES : 1];  // actor o's box covers this tile
     __shared__ int16_t s_act[ACT ? DV_MAX_OCTREES : 1];
     __shared__ float s_iv[ACT ? NTA : 1][2][ACT ? CT_THREADS : 1];
@@ -822,7 +825,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                         t1 = fminf(t1, b);
                         if (t1 > t0) {
                             const float rel[3] = {g.x, g.y, g.z};
-                            add_segment<G, true, KS, NRM, X>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
+                            add_segment<G, true, KS, NRM, X, RFORM>(pt, bw, bp, s_rec[slot][j][1], s_rec[slot][j][2],
                                                              s_rec[slot][j][3], staged_nv(slot, j), rel, d, t0, t1,
                                                              acc, s_r[slot][j], &ex);
                             hit = true;
@@ -847,6 +850,7 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
         pt.C0 = pt.C1 = pt.C2 = pt.D = 0.0f;
         if constexpr (NRM) pt.N0 = pt.N1 = pt.N2 = 0.0f;
         pt.T = 1.0f;
+        pt.R = 0.0f;
         pt.n = 0;
         pt.tests = 0;
         pt.boxes = 0;
@@ -855,7 +859,11 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
         // actor whatever T it enters with (T <= 1), so its partial may stop there too
         walk_actor(pt, s_act[q], a, b, std::false_type(), std::false_type());
         ps.tests += pt.tests;
-        if (act) {
+        if (act && RFORM) {
+            s_st[q][0][tid] = pt.R;
+            s_st[q][4][tid] = pt.T;
+            s_st[q][5][tid] = __int_as_float((int)pt.n);
+        } else if (act) {
             s_st[q][0][tid] = pt.C0;
             s_st[q][1][tid] = pt.C1;
             s_st[q][2][tid] = pt.C2;
@@ -880,7 +888,23 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     }
     // enters actor interval `it`: apply its partial, or stop inside it, or walk it per lane
     auto enter_actor = [&](const ActInt& it) {
-        if (it.q < NTA) {
+        if (RFORM && it.q < NTA) {
+            // backward: record the entry state (R, T) for the replay, then apply the partial
+            const int q = it.q;
+            const float pR = s_st[q][0][tid], pT = s_st[q][4][tid];
+            const uint32_t pn = (uint32_t)__float_as_int(s_st[q][5][tid]);
+            const bool stop_inside = ps.T * pT < bp.eps_stop;
+            s_st[q][0][tid] = ps.R;
+            s_st[q][4][tid] = ps.T;
+            s_st[q][5][tid] = stop_inside ? 2.0f : 1.0f;
+            if (stop_inside) {
+                ps.done = true;
+            } else {
+                ps.R = fmaf(ps.T, pR, ps.R);
+                ps.T = ps.T * pT;
+                ps.n += pn;
+            }
+        } else if (it.q < NTA) {
             const int q = it.q;
             const float pC0 = s_st[q][0][tid], pC1 = s_st[q][1][tid], pC2 = s_st[q][2][tid];
             const float pD = s_st[q][3][tid], pT = s_st[q][4][tid];
@@ -1047,15 +1071,22 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
         const bool act = REPLAY ? status >= 1 : status == 2;
         if (__syncthreads_or(act) == 0) continue;
         Pix<NRM> pt;
-        pt.C0 = act ? s_st[q][0][tid] : 0.0f;
-        pt.C1 = act ? s_st[q][1][tid] : 0.0f;
-        pt.C2 = act ? s_st[q][2][tid] : 0.0f;
-        pt.D = act ? s_st[q][3][tid] : 0.0f;
         pt.T = act ? s_st[q][4][tid] : 1.0f;
-        if constexpr (NRM) {
-            pt.N0 = act ? s_st[q][6][tid] : 0.0f;
-            pt.N1 = act ? s_st[q][7][tid] : 0.0f;
-            pt.N2 = act ? s_st[q][8][tid] : 0.0f;
+        if (RFORM) {
+            pt.R = act ? s_st[q][0][tid] : 0.0f;
+            pt.C0 = pt.C1 = pt.C2 = pt.D = 0.0f;
+            if constexpr (NRM) pt.N0 = pt.N1 = pt.N2 = 0.0f;
+        } else {
+            pt.R = 0.0f;
+            pt.C0 = act ? s_st[q][0][tid] : 0.0f;
+            pt.C1 = act ? s_st[q][1][tid] : 0.0f;
+            pt.C2 = act ? s_st[q][2][tid] : 0.0f;
+            pt.D = act ? s_st[q][3][tid] : 0.0f;
+            if constexpr (NRM) {
+                pt.N0 = act ? s_st[q][6][tid] : 0.0f;
+                pt.N1 = act ? s_st[q][7][tid] : 0.0f;
+                pt.N2 = act ? s_st[q][8][tid] : 0.0f;
+            }
         }
         pt.n = 0;
         pt.tests = 0;
