@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate and path")
+    p.add_argument("--serve-min-requests", type=int, default=1000,
+                   help="requests per rate at least (the window grows for low rates), so p99 rests on >= 10 tail samples")
     p.add_argument("--serve-rates", default="200,500,1000,2000")
     p.add_argument("--profile-pass", action="store_true",
                    help="no timing: one warm-up and one profiled pass of every row on the 1080p frame, for a "
@@ -366,7 +368,7 @@ def serving_bench(args, dv, opts):
     ds = [dv.DeviceOctree.from_host(o) for o in scene.octrees]
     rows = []
     for rate in [float(x) for x in args.serve_rates.split(",") if x]:
-        n = max(16, int(rate * args.serve_seconds))
+        n = max(args.serve_min_requests, int(rate * args.serve_seconds))
         reqs = synth.request_stream(n, rate, args.seed + int(rate))
         row = {"rate_hz": rate}
         for mode in ("plain", "batched"):
@@ -665,7 +667,13 @@ def run_ours(args):
         feats = {"what": "weights export of the frame, then a 64-channel feature render and 2-D feature fusion",
                  "slots": slots, "export_us": 1e3 * t_ex / reps, "render64_us": 1e3 * t_r / reps,
                  "fuse64_us": 1e3 * t_fu / reps,
-                 "render64_gbs": (slots * (8 + 64 * 4) + n_pix * 64 * 4) / (t_r / reps * 1e-3) / 1e9}
+                 "render64_gbs": (slots * (8 + 64 * 4) + n_pix * 64 * 4) / (t_r / reps * 1e-3) / 1e9,
+                 "fuse64_gbs": (slots * (8 + 64 * 4) + n_pix * 64 * 4) / (t_fu / reps * 1e-3) / 1e9,
+                 "bytes_model": ("per slot its (voxel, weight) and one 64-float feature row (the voxel's for the "
+                                 "render, the pixel's for the fusion), plus one 64-float row per pixel; rows are "
+                                 "counted once per slot (no reuse)")}
+        feats["render64_hbm_frac"] = feats["render64_gbs"] / pk["hbm_gbs"]
+        feats["fuse64_hbm_frac"] = feats["fuse64_gbs"] / pk["hbm_gbs"]
 
     # ---- LiDAR-guided initialisation (Sec. 3.3) of the frame's background: shared corners, Eq. 1
     # prior from a 1.4M-point synthetic sweep, one proximity-subdivision round ----
