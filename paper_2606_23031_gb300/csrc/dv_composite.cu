@@ -169,18 +169,16 @@ __device__ __forceinline__ InvDir inv_dir(const float* d) {
 
 // Ray / voxel slab test.  g = (min corner - ray origin, size): along axis k the ray
 // crosses the min plane at g_k / d_k and the max plane at (g_k + size) / d_k; which of
-// the two it enters by follows from the sign of d_k.
+// the two it enters by follows from the sign of d_k.  The x and y axes go through packed two-lane
+// multiplies and FMAs (the same roundings as scalar ones, half the instructions).
 __device__ __forceinline__ bool slab_cube(const InvDir& v, float4 g, float& t0, float& t1) {
-    const float rel[3] = {g.x, g.y, g.z};
-    float en[3], ex[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float ta = rel[k] * v.inv[k];
-        en[k] = fmaf(g.w, v.in[k], ta);
-        ex[k] = fmaf(g.w, v.ip[k], ta);
-    }
-    t0 = max3f(en[0], en[1], en[2]);
-    t1 = min3f(ex[0], ex[1], ex[2]);
+    const float2 ww = make_float2(g.w, g.w);
+    const float2 ta = __fmul2_rn(make_float2(g.x, g.y), make_float2(v.inv[0], v.inv[1]));
+    const float2 en = __ffma2_rn(ww, make_float2(v.in[0], v.in[1]), ta);
+    const float2 ex = __ffma2_rn(ww, make_float2(v.ip[0], v.ip[1]), ta);
+    const float tz = g.z * v.inv[2];
+    t0 = max3f(en.x, en.y, fmaf(g.w, v.in[2], tz));
+    t1 = min3f(ex.x, ex.y, fmaf(g.w, v.ip[2], tz));
     return t0 < t1;
 }
 
@@ -221,11 +219,14 @@ __device__ __forceinline__ float seg_tau(float4 da, float4 db, float is, const f
         const float x = __saturatef(fmaf(t, d[0], -rel[0]) * is);
         const float y = __saturatef(fmaf(t, d[1], -rel[1]) * is);
         const float z = __saturatef(fmaf(t, d[2], -rel[2]) * is);
-        // the record holds the trilinear field as a polynomial (da = (c0, c1, c2, c4), db = (c3, c5, c6,
-        // c7)): rho = (c0 + c1 x) + y (c2 + c4 x) + z ((c3 + c5 x) + y (c6 + c7 x))
-        const float p0 = fmaf(da.y, x, da.x), p1 = fmaf(da.w, x, da.z);
-        const float p2 = fmaf(db.y, x, db.x), p3 = fmaf(db.w, x, db.z);
-        const float rho = fmaf(fmaf(p3, y, p2), z, fmaf(p1, y, p0));
+        // the record holds the trilinear field as a polynomial (da = (c0, c3, c1, c5), db = (c2, c6, c4,
+        // c7)): rho = (c0 + c1 x) + y (c2 + c4 x) + z ((c3 + c5 x) + y (c6 + c7 x)), the two x-linear
+        // pairs and the two y steps taken as packed two-lane FMAs (same roundings as the scalar form)
+        const float2 xx = make_float2(x, x);
+        const float2 pA = __ffma2_rn(make_float2(da.z, da.w), xx, make_float2(da.x, da.y));
+        const float2 pB = __ffma2_rn(make_float2(db.z, db.w), xx, make_float2(db.x, db.y));
+        const float2 qq = __ffma2_rn(pB, make_float2(y, y), pA);
+        const float rho = fmaf(qq.y, z, qq.x);
         tau += act_fn(rho, act);
         if (GRAD && KS == 1) {
             sxyz[0] = act_grad(rho, act) * h;
@@ -280,20 +281,19 @@ __device__ __forceinline__ void composite_tau(Pix<NRM>& ps, float tau, float4 co
 template <int KS>
 __device__ __forceinline__ void seg_density_grad(float gt, const float* dtd, const float* sxyz, float* acc) {
     if constexpr (KS == 1) {
-        // gt s w_c(x, y, z): the trilinear weights with gt s folded into the y-z products
+        // gt s w_c(x, y, z): the trilinear weights with gt s folded into the y-z products; corners c and
+        // c + 1 (x = 0 and 1) are accumulated as one packed two-lane FMA
         const float a = gt * sxyz[0];
         const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
-        const float x0 = 1.0f - x;
-        const float ay0 = a * (1.0f - y), ay1 = a * y;
-        const float c00 = ay0 * (1.0f - z), c10 = ay1 * (1.0f - z), c01 = ay0 * z, c11 = ay1 * z;
-        acc[0] = fmaf(x0, c00, acc[0]);
-        acc[1] = fmaf(x, c00, acc[1]);
-        acc[2] = fmaf(x0, c10, acc[2]);
-        acc[3] = fmaf(x, c10, acc[3]);
-        acc[4] = fmaf(x0, c01, acc[4]);
-        acc[5] = fmaf(x, c01, acc[5]);
-        acc[6] = fmaf(x0, c11, acc[6]);
-        acc[7] = fmaf(x, c11, acc[7]);
+        const float2 xw = make_float2(1.0f - x, x);
+        const float2 ay = __fmul2_rn(make_float2(a, a), make_float2(1.0f - y, y));
+        const float2 cz0 = __fmul2_rn(ay, make_float2(1.0f - z, 1.0f - z));
+        const float2 cz1 = __fmul2_rn(ay, make_float2(z, z));
+        float2 r;
+        r = __ffma2_rn(xw, make_float2(cz0.x, cz0.x), make_float2(acc[0], acc[1])); acc[0] = r.x; acc[1] = r.y;
+        r = __ffma2_rn(xw, make_float2(cz0.y, cz0.y), make_float2(acc[2], acc[3])); acc[2] = r.x; acc[3] = r.y;
+        r = __ffma2_rn(xw, make_float2(cz1.x, cz1.x), make_float2(acc[4], acc[5])); acc[4] = r.x; acc[5] = r.y;
+        r = __ffma2_rn(xw, make_float2(cz1.y, cz1.y), make_float2(acc[6], acc[7])); acc[6] = r.x; acc[7] = r.y;
     } else {
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = fmaf(gt, dtd[c], acc[c]);

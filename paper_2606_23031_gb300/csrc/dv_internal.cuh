@@ -73,8 +73,9 @@ static_assert(sizeof(BatchParams) < 4096, "BatchParams is meant to stay small");
 
 // 64-byte per-voxel render record, one per visible (view, voxel) in depth-key order.
 //   v[0] = (min - o, size)   min corner relative to the camera centre o, both in the octree's frame
-//   v[1] = (c0, c1, c2, c4)  the trilinear density as a polynomial in the voxel coordinates,
-//   v[2] = (c3, c5, c6, c7)  rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz
+//   v[1] = (c0, c3, c1, c5)  the trilinear density as a polynomial in the voxel coordinates,
+//   v[2] = (c2, c6, c4, c7)  rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz, paired
+//                            so that (c0, c3) + (c1, c5) x and (c2, c6) + (c4, c7) x are packed FMAs
 //   v[3] = (r, g, b, 1/size)
 struct __align__(16) VoxRec {
     float4 v[4];

@@ -388,12 +388,13 @@ __global__ void __launch_bounds__(256) k_records_emit(
         VoxRec R;
         R.v[0] = make_float4(rx, ry, rz, L.s);
         // the trilinear field as a polynomial in the voxel coordinates (x, y, z) in [0, 1]^3:
-        // rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz, from corner c = x + 2y + 4z
+        // rho = c0 + c1 x + c2 y + c3 z + c4 xy + c5 xz + c6 yz + c7 xyz, from corner c = x + 2y + 4z,
+        // stored as (c0, c3, c1, c5), (c2, c6, c4, c7) for the compositing kernels' packed FMAs
         const float p1 = da.y - da.x, p2 = da.z - da.x, p3 = db.x - da.x;
         const float p4 = (da.w - da.z) - p1, p5 = (db.y - db.x) - p1, p6 = (db.z - db.x) - p2;
         const float p7 = ((db.w - db.z) - (db.y - db.x)) - ((da.w - da.z) - p1);
-        R.v[1] = make_float4(da.x, p1, p2, p4);
-        R.v[2] = make_float4(p3, p5, p6, p7);
+        R.v[1] = make_float4(da.x, p3, p1, p5);
+        R.v[2] = make_float4(p2, p6, p4, p7);
         R.v[3] = make_float4(fmaxf(c0, 0.0f), fmaxf(c1, 0.0f), fmaxf(c2, 0.0f), 1.0f / L.s);
         rec[r] = R;
         if (nrm) {
