@@ -303,11 +303,11 @@ dv_status dv_features_render(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets,
  * Feature fusion over a weights export (the transpose of dv_features_render):
  * ADDS weight * feat2d[p][c] into accum[voxel][c] and weight into wsum[voxel]
  * (NULL = skip) for every slot of every pixel; accum / wsum is then the
- * weighted mean of the 2-D features seen by each voxel.  The slots are sorted
- * by voxel in scratch memory (about 20 bytes per slot from the context's pool)
- * and each voxel's run is summed in slot order before one atomic add per run
- * and channel.  Reads the slot count offsets[n_pix] back, so it synchronises
- * the stream.  DV_ERR_CAPACITY beyond 2^32 - 1 slots or pixels.
+ * weighted mean of the 2-D features seen by each voxel.  One kernel: the
+ * slots of every 128 consecutive pixels are grouped by voxel in shared memory
+ * and each voxel's sum over them is added once per channel (atomics, so the
+ * order of the additions varies from run to run).  Allocates nothing and does
+ * not synchronise the stream.
  */
 dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, const uint32_t* voxel,
                            const float* weight, const float* feat2d, int32_t C, float* accum, float* wsum,

@@ -1271,15 +1271,8 @@ dv_status dv_features_fuse(dv_ctx* ctx, int64_t n_pix, const int64_t* offsets, c
     if (n_pix > 0 && (!offsets || !feat2d || !accum)) return fail(ctx, DV_ERR_INVALID_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    dv::Arena ar;
-    ar.pool = ctx->pool;
-    ar.stream = s;
-    bool timeout = false;
-    cudaError_t e = dv::feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, ar, s, &timeout);
-    ar.release();
-    if (e == cudaErrorInvalidValue) return fail(ctx, DV_ERR_CAPACITY, "more than 2^32 - 1 slots or pixels");
+    const cudaError_t e = dv::feat_fuse(n_pix, offsets, voxel, weight, feat2d, C, accum, wsum, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "feature fusion");
-    if (timeout) return fail(ctx, DV_ERR_TIMEOUT, "the fusion's slot sort ran out of its bounded wait; sums invalid");
     return DV_OK;
 }
 

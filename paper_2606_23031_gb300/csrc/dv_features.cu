@@ -10,8 +10,8 @@
 // ..., 64, 128) a lane owns a 16-byte quad of channels and the warp covers 32 / (C / 4) slots at
 // once; other C take one lane per channel, 32 channels per pass over the slots.
 // Fusion: adding every slot into its voxel's row with its own atomics is bound by the L2's
-// atomic rate (one add per slot and channel), so the slots are first sorted by voxel and each
-// run of one voxel is summed in registers and added once.
+// atomic rate (one add per slot and channel), so the slots of a chunk of consecutive pixels are
+// grouped by voxel in shared memory and each voxel's sum over the chunk is added once.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,184 +76,224 @@ __global__ void __launch_bounds__(FT_WARPS * 32) k_feat_render4(int64_t n_pix, c
     if (g == 0) out[(size_t)p * Q + q] = acc;
 }
 
-// ---- fusion by voxel runs ----
-// The slots are sorted by voxel (stable, so a voxel's slots keep their export order); a warp
-// takes FZ_CHUNK consecutive sorted slots, sums w * F2d[p] over each run of one voxel in
-// registers and adds a run's sums into the voxel's row once.  Atomics drop from one per slot
-// and channel to one per run and channel (a run is cut only at chunk ends), and within a run the
-// sum is taken in export order.
+// ---- fusion by pixel chunks ----
+// A block takes FL_PIX consecutive pixels (their slots are one contiguous range) and a slice of up
+// to FL_SW channels.  Neighbouring pixels see mostly the same voxels (a 128-pixel run of an image
+// row: a few thousand slots over about a hundred distinct voxels), so the block sums the chunk's
+// slots per voxel and adds each voxel's sums to the global rows once per chunk.  The 2-D features
+// are read once, in order, and the slots need no global sort.
+//  * The chunk's 2-D feature slice is staged in shared memory.
+//  * The slots, FL_PIECE at a time, get a row from an open-addressing table keyed by the voxel
+//    index (compare-and-swap inserts, FL_ROWS rows); a voxel that finds no row within FL_PROBES
+//    probes goes to the overflow row, whose slots are added to the global sums one by one.
+//  * A counting sort by row groups the piece's slots; warp w then takes rows w, w + 8, ...: its two
+//    16-lane halves walk alternate slots of the row, a lane holding a 4-channel quad of the sums in
+//    registers, and the halves' sums are added by shuffles before one atomic add per quad.
+constexpr int FL_PIX = 128;     // pixels per chunk
+constexpr int FL_SW = 64;       // channels per slice (16 quads)
+constexpr int FL_ROWS = 255;    // voxel rows; row FL_ROWS holds the overflow slots
+constexpr int FL_PIECE = 3072;  // slots grouped at once (three 59 KB blocks fit an SM)
+constexpr int FL_PROBES = 32;
+constexpr int FL_THREADS = 256;
+constexpr int FL_SPT = FL_PIECE / FL_THREADS;  // slots per thread and piece
+constexpr uint32_t FL_EMPTY = 0xffffffffu;
 
-constexpr int FZ_CHUNK = 256;  // sorted slots per warp
+struct FuseSmem {
+    float4 f[FL_PIX][FL_SW / 4];      // 2-D features of the chunk's pixels, this slice
+    int64_t off[FL_PIX + 1];          // slot offsets of the chunk's pixels
+    uint32_t key[FL_ROWS];            // voxel of each row (FL_EMPTY: free)
+    uint32_t cnt[FL_ROWS + 1];        // slots per row, then the fill cursors
+    uint32_t start[FL_ROWS + 2];      // first grouped slot of each row
+    uint32_t wtot[FL_THREADS / 32];   // scan: warp totals
+    float sw[FL_PIECE];               // grouped by row: the slot's weight,
+    uint16_t order[FL_PIECE];         //   its index in the piece,
+    uint8_t spl[FL_PIECE];            //   and its pixel within the chunk
+};
 
-// key = voxel, value = slot, pw[slot] = (pixel, weight bits); the largest voxel index goes to *vmax.
-// A block takes FZ_PREP consecutive pixels, whose slots are one contiguous range, and strides over
-// that range with coalesced loads and stores; a slot's pixel is the last of the block's offsets at
-// or below it (binary search in shared memory).
-constexpr int FZ_PREP = 256;
-__global__ void __launch_bounds__(FZ_PREP) k_fuse_prep(int64_t n_pix, const int64_t* __restrict__ off,
-                                                       const uint32_t* __restrict__ vox, const float* __restrict__ wgt,
-                                                       uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-                                                       uint2* __restrict__ pw, uint32_t* __restrict__ vmax) {
-    __shared__ int64_t s_off[FZ_PREP + 1];
-    const int64_t p0 = (int64_t)blockIdx.x * FZ_PREP;
-    const int np = (int)min((int64_t)FZ_PREP, n_pix - p0);
-    for (int i = threadIdx.x; i <= np; i += FZ_PREP) s_off[i] = off[p0 + i];
-    __syncthreads();
-    uint32_t m = 0;
-    const int64_t e1 = s_off[np];
-    for (int64_t e = s_off[0] + threadIdx.x; e < e1; e += FZ_PREP) {
-        int lo = 0, hi = np - 1;  // the owner i has s_off[i] <= e < s_off[i + 1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= e)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        const uint32_t v = __ldg(vox + e);
-        key[e] = v;
-        val[e] = (uint32_t)e;
-        pw[e] = make_uint2((uint32_t)(p0 + lo), __float_as_uint(__ldg(wgt + e)));
-        m = max(m, v);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(vmax, m);
+__device__ __forceinline__ uint32_t fl_hash(uint32_t v) { return ((v * 2654435761u) >> 16) % FL_ROWS; }
+
+// 16-byte asynchronous global -> shared copy (L2 only) and its fences
+__device__ __forceinline__ void fl_cp_async16(void* smem, const void* gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void fl_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void fl_cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void fl_add4(float4& a, float w, float4 f) {
+    a.x = fmaf(w, f.x, a.x);
+    a.y = fmaf(w, f.y, a.y);
+    a.z = fmaf(w, f.z, a.z);
+    a.w = fmaf(w, f.w, a.w);
 }
 
-// Any C: lane owns channels c0 + lane + 32 j, j < CPL; the warp walks its slots in groups of
-// FZ_LOOK, issuing their loads together before summing them in order.
-constexpr int FZ_LOOK = 4;
-template <int CPL>
-__global__ void __launch_bounds__(256) k_fuse_runs(int64_t n, const uint32_t* __restrict__ skey,
-                                                   const uint32_t* __restrict__ sval, const uint2* __restrict__ pw,
-                                                   const float* __restrict__ f2d, int C, float* __restrict__ acc,
-                                                   float* __restrict__ wsum) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * FZ_CHUNK;
-    if (i0 >= n) return;
-    const int64_t i1 = min(n, i0 + FZ_CHUNK);
-    for (int c0 = 0; c0 < C; c0 += 32 * CPL) {
-        float a[CPL];
-#pragma unroll
-        for (int j = 0; j < CPL; ++j) a[j] = 0.0f;
-        float ws = 0.0f;
-        uint32_t cur = __ldg(skey + i0);
-        auto flush = [&]() {
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int c = c0 + lane + 32 * j;
-                if (c < C && a[j] != 0.0f) atomicAdd(acc + (size_t)cur * C + c, a[j]);
-                a[j] = 0.0f;
-            }
-            if (c0 == 0 && wsum && lane == 0 && ws != 0.0f) atomicAdd(wsum + cur, ws);
-            ws = 0.0f;
-        };
-        for (int64_t i = i0; i < i1; i += FZ_LOOK) {
-            uint32_t v[FZ_LOOK];
-            float w[FZ_LOOK], f[FZ_LOOK][CPL];
-#pragma unroll
-            for (int k = 0; k < FZ_LOOK; ++k) {
-                const bool in = i + k < i1;
-                v[k] = in ? __ldg(skey + i + k) : cur;
-                const uint2 q = in ? __ldg(pw + __ldg(sval + i + k)) : make_uint2(0u, 0u);
-                w[k] = __uint_as_float(q.y);
-                const size_t row = (size_t)q.x * C;
-#pragma unroll
-                for (int j = 0; j < CPL; ++j) {
-                    const int c = c0 + lane + 32 * j;
-                    f[k][j] = (in && c < C) ? __ldg(f2d + row + c) : 0.0f;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < FZ_LOOK; ++k) {
-                if (i + k < i1) {
-                    if (v[k] != cur) {
-                        flush();
-                        cur = v[k];
-                    }
-#pragma unroll
-                    for (int j = 0; j < CPL; ++j) a[j] = fmaf(w[k], f[k][j], a[j]);
-                    ws += w[k];
-                }
-            }
-        }
-        flush();
+// adds quad a (channels c .. c + 3, those below C) into row v of the global sums
+template <bool VEC>
+__device__ __forceinline__ void fl_flush4(float* __restrict__ acc, uint32_t v, int C, int c, float4 a) {
+    if (c >= C || (a.x == 0.0f && a.y == 0.0f && a.z == 0.0f && a.w == 0.0f)) return;
+    float* row = acc + (size_t)v * C + c;
+    if (VEC) {
+        atomicAdd(reinterpret_cast<float4*>(row), a);
+    } else {
+        atomicAdd(row, a.x);
+        if (c + 1 < C) atomicAdd(row + 1, a.y);
+        if (c + 2 < C) atomicAdd(row + 2, a.z);
+        if (c + 3 < C) atomicAdd(row + 3, a.w);
     }
 }
 
-// C = 4 Q with Q | 32: lane (g = lane / Q, q = lane % Q) owns the 16-byte quad q of every
-// S-th slot (S = 32 / Q slots per load instruction).  Per 32 sorted slots the warp loads their
-// (voxel, slot) and (pixel, weight) with one load each, lane k holding slot k, then R * S slots
-// at a time gathers their rows (R loads in flight per lane) and sums them in slot order into
-// the running voxel's quads; at a run's end the S partial quads are added across the groups and
-// the run is added once.
-// (4 rows in flight and 5 resident blocks per SM measured best: 8 rows held 3 blocks, more blocks spilled)
-template <int Q, int R = (Q < 4 ? Q : 4)>
-__global__ void __launch_bounds__(256, 5) k_fuse_runs4(int64_t n, const uint32_t* __restrict__ skey,
-                                                    const uint32_t* __restrict__ sval, const uint2* __restrict__ pw,
-                                                    const float4* __restrict__ f2d, float4* __restrict__ acc,
-                                                    float* __restrict__ wsum) {
-    constexpr int S = 32 / Q;
-    const int lane = threadIdx.x & 31, g = lane / Q, q = lane % Q;
-    const int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * FZ_CHUNK;
-    if (i0 >= n) return;
-    const int64_t i1 = min(n, i0 + FZ_CHUNK);
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    float ws = 0.0f;
-    uint32_t cur = __ldg(skey + i0);
-    auto flush = [&]() {
-#pragma unroll
-        for (int d = Q; d < 32; d <<= 1) {
-            a.x += __shfl_xor_sync(0xffffffffu, a.x, d);
-            a.y += __shfl_xor_sync(0xffffffffu, a.y, d);
-            a.z += __shfl_xor_sync(0xffffffffu, a.z, d);
-            a.w += __shfl_xor_sync(0xffffffffu, a.w, d);
-        }
-        if (g == 0 && (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f)) atomicAdd(acc + (size_t)cur * Q + q, a);
-        if (wsum && lane == 0 && ws != 0.0f) atomicAdd(wsum + cur, ws);
-        a = make_float4(0.f, 0.f, 0.f, 0.f);
-        ws = 0.0f;
-    };
-    for (int64_t i = i0; i < i1; i += 32) {
-        const int cnt = (int)min((int64_t)32, i1 - i);
-        const bool in = lane < cnt;
-        const uint32_t v_l = in ? __ldg(skey + i + lane) : 0u;
-        const uint2 pw_l = in ? __ldg(pw + __ldg(sval + i + lane)) : make_uint2(0u, 0u);
-        const float w_l = __uint_as_float(pw_l.y);
-        for (int k0 = 0; k0 < cnt; k0 += S * R) {
-            float4 f[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int sl = k0 + r * S + g;  // < 32 + S * R <= 64
-                const uint32_t pp = __shfl_sync(0xffffffffu, pw_l.x, sl & 31);
-                f[r] = sl < cnt ? __ldg(f2d + (size_t)pp * Q + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+template <bool VEC>
+__global__ void __launch_bounds__(FL_THREADS, 3) k_fuse_local(int64_t n_pix, const int64_t* __restrict__ off,
+                                                             const uint32_t* __restrict__ vox,
+                                                             const float* __restrict__ wgt,
+                                                             const float* __restrict__ f2d, int C,
+                                                             float* __restrict__ acc, float* __restrict__ wsum) {
+    extern __shared__ __align__(16) unsigned char fl_raw[];
+    FuseSmem& S = *reinterpret_cast<FuseSmem*>(fl_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = lane & 15, g = lane >> 4;  // channel quad, half-warp
+    for (int i = tid; i < FL_ROWS; i += FL_THREADS) S.key[i] = FL_EMPTY;
+    const int64_t n_chunks = (n_pix + FL_PIX - 1) / FL_PIX;
+    const int n_slices = (C + FL_SW - 1) / FL_SW;
+    for (int64_t task = blockIdx.x; task < n_chunks * n_slices; task += gridDim.x) {
+        const int64_t p0 = (task / n_slices) * FL_PIX;
+        const int c0 = (int)(task % n_slices) * FL_SW;
+        const int np = (int)min((int64_t)FL_PIX, n_pix - p0);
+        __syncthreads();  // the previous task is done with the shared arrays
+        // the chunk's 2-D feature slice: 16-byte asynchronous copies (rows 16-byte aligned), which
+        // land while the slots are grouped; otherwise plain loads
+        if (VEC) {
+            for (int i = tid; i < FL_PIX * (FL_SW / 4); i += FL_THREADS) {
+                const int pl = i / (FL_SW / 4), qd = i % (FL_SW / 4), c = c0 + 4 * qd;
+                if (pl < np && c < C)
+                    fl_cp_async16(&S.f[pl][qd], f2d + (size_t)(p0 + pl) * C + c);
+                else
+                    S.f[pl][qd] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            fl_cp_async_commit();
+        } else {
+            for (int i = tid; i < FL_PIX * FL_SW; i += FL_THREADS) {
+                const int pl = i / FL_SW, j = i % FL_SW, c = c0 + j;
+                (&S.f[0][0].x)[i] = pl < np && c < C ? __ldg(f2d + (size_t)(p0 + pl) * C + c) : 0.0f;
+            }
+        }
+        for (int i = tid; i <= np; i += FL_THREADS) S.off[i] = off[p0 + i];
+        __syncthreads();
+        const int64_t e_end = S.off[np];
+        for (int64_t e0 = S.off[0]; e0 < e_end; e0 += FL_PIECE) {
+            const int ns = (int)min((int64_t)FL_PIECE, e_end - e0);
+            for (int i = tid; i <= FL_ROWS; i += FL_THREADS) S.cnt[i] = 0;
+            // this thread's slots tid + j * FL_THREADS: loads first (all in flight together)
+            uint32_t v_[FL_SPT], r_[FL_SPT];
+            float w_[FL_SPT];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int j = 0; j < FL_SPT; ++j) {
+                const int k = tid + j * FL_THREADS;
+                v_[j] = k < ns ? __ldg(vox + e0 + k) : 0u;
+                w_[j] = k < ns ? __ldg(wgt + e0 + k) : 0.0f;
+            }
+            __syncthreads();
+            // each slot's pixel (binary search of the chunk's offsets) and its voxel's row
 #pragma unroll
-                for (int h = 0; h < S; ++h) {
-                    const int sl = k0 + r * S + h;
-                    if (sl < cnt) {  // warp-uniform
-                        const uint32_t vv = __shfl_sync(0xffffffffu, v_l, sl);
-                        const float ww = __shfl_sync(0xffffffffu, w_l, sl);
-                        if (vv != cur) {
-                            flush();
-                            cur = vv;
+            for (int j = 0; j < FL_SPT; ++j) {
+                const int k = tid + j * FL_THREADS;
+                r_[j] = 0u;
+                if (k < ns) {
+                    const int64_t e = e0 + k;
+                    int lo = 0, hi = np - 1;  // the owner i has off[i] <= e < off[i + 1]
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (S.off[mid] <= e)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    uint32_t h = fl_hash(v_[j]), row = FL_ROWS;
+                    for (int probe = 0; probe < FL_PROBES; ++probe) {
+                        const uint32_t old = atomicCAS(&S.key[h], FL_EMPTY, v_[j]);
+                        if (old == FL_EMPTY || old == v_[j]) {
+                            row = h;
+                            break;
                         }
-                        if (g == h) {
-                            a.x = fmaf(ww, f[r].x, a.x);
-                            a.y = fmaf(ww, f[r].y, a.y);
-                            a.z = fmaf(ww, f[r].z, a.z);
-                            a.w = fmaf(ww, f[r].w, a.w);
-                        }
-                        ws += ww;
+                        h = h + 1 == FL_ROWS ? 0u : h + 1;
+                    }
+                    r_[j] = ((uint32_t)lo << 16) | row;
+                    atomicAdd(&S.cnt[row], 1u);
+                }
+            }
+            __syncthreads();
+            // exclusive scan of the FL_ROWS + 1 row counts (one per thread)
+            {
+                const uint32_t x = tid <= FL_ROWS ? S.cnt[tid] : 0u;
+                uint32_t inc = x;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                if (lane == 31) S.wtot[warp] = inc;
+                __syncthreads();
+                uint32_t base = 0;
+                for (int i = 0; i < warp; ++i) base += S.wtot[i];
+                if (tid <= FL_ROWS) {
+                    S.start[tid] = base + inc - x;
+                    S.cnt[tid] = 0;
+                }
+                if (tid == FL_ROWS) S.start[FL_ROWS + 1] = base + inc;
+            }
+            __syncthreads();
+            // group the slots by row
+#pragma unroll
+            for (int j = 0; j < FL_SPT; ++j) {
+                const int k = tid + j * FL_THREADS;
+                if (k < ns) {
+                    const uint32_t row = r_[j] & 0xffffu;
+                    const uint32_t pos = S.start[row] + atomicAdd(&S.cnt[row], 1u);
+                    S.sw[pos] = w_[j];
+                    S.order[pos] = (uint16_t)k;
+                    S.spl[pos] = (uint8_t)(r_[j] >> 16);
+                }
+            }
+            if (VEC && e0 == S.off[0]) fl_cp_async_wait_all();  // the feature slice has landed
+            __syncthreads();
+            // per row: the two halves of the warp take alternate slots, sums in registers
+            for (int r = warp; r <= FL_ROWS; r += FL_THREADS / 32) {
+                const uint32_t s0 = S.start[r], s1 = S.start[r + 1];
+                if (s0 == s1) continue;
+                if (r < FL_ROWS) {
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float ws = 0.0f;
+#pragma unroll 4
+                    for (uint32_t i = s0 + g; i < s1; i += 2) {
+                        const float wv = S.sw[i];
+                        fl_add4(a, wv, S.f[S.spl[i]][q]);
+                        ws += wv;
+                    }
+                    a.x += __shfl_xor_sync(0xffffffffu, a.x, 16);
+                    a.y += __shfl_xor_sync(0xffffffffu, a.y, 16);
+                    a.z += __shfl_xor_sync(0xffffffffu, a.z, 16);
+                    a.w += __shfl_xor_sync(0xffffffffu, a.w, 16);
+                    ws += __shfl_xor_sync(0xffffffffu, ws, 16);
+                    const uint32_t v = S.key[r];
+                    if (g == 0) fl_flush4<VEC>(acc, v, C, c0 + 4 * q, a);
+                    if (lane == 0 && wsum && c0 == 0 && ws != 0.0f) atomicAdd(wsum + v, ws);
+                } else {
+                    // overflow row: every slot added on its own
+                    for (uint32_t i = s0 + g; i < s1; i += 2) {
+                        const float wv = S.sw[i];
+                        const uint32_t v = __ldg(vox + e0 + S.order[i]);
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                        fl_add4(a, wv, S.f[S.spl[i]][q]);
+                        fl_flush4<VEC>(acc, v, C, c0 + 4 * q, a);
+                        if (q == 0 && wsum && c0 == 0 && wv != 0.0f) atomicAdd(wsum + v, wv);
                     }
                 }
             }
+            __syncthreads();
+            for (int i = tid; i < FL_ROWS; i += FL_THREADS) S.key[i] = FL_EMPTY;
         }
+        if (VEC) fl_cp_async_wait_all();  // a chunk without slots: no copy outlives the task
     }
-    flush();
 }
 
 // the 16-byte render path needs C = 4 Q with Q a divisor of 32 and 16-byte aligned rows
@@ -278,63 +318,26 @@ cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t
 }
 
 cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt, const float* f2d,
-                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s, bool* sort_timeout) {
-    *sort_timeout = false;
+                      int C, float* acc, float* wsum, cudaStream_t s) {
     if (n_pix <= 0 || C <= 0) return cudaSuccess;
-    int64_t n = 0;
-    cudaError_t e = cudaMemcpyAsync(&n, off + n_pix, sizeof(n), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    if (n <= 0) return cudaSuccess;
-    if (n > (int64_t)UINT32_MAX || n_pix > (int64_t)UINT32_MAX) return cudaErrorInvalidValue;  // 32-bit slot and pixel indices
-    uint32_t* k0 = ar.alloc<uint32_t>(n);
-    uint32_t* k1 = ar.alloc<uint32_t>(n);
-    uint32_t* v0 = ar.alloc<uint32_t>(n);
-    uint32_t* v1 = ar.alloc<uint32_t>(n);
-    uint2* pw = ar.alloc<uint2>(n);
-    uint32_t* vmax = ar.alloc<uint32_t>(2);  // [0] largest voxel index, [1] the sort's wait flag
-    if (ar.err != cudaSuccess) return ar.err;
-    e = cudaMemsetAsync(vmax, 0, 2 * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    k_fuse_prep<<<(unsigned)((n_pix + FZ_PREP - 1) / FZ_PREP), FZ_PREP, 0, s>>>(n_pix, off, vox, wgt, k0, v0, pw, vmax);
-    count_launches(1);
-    uint32_t vm = 0;
-    e = cudaMemcpyAsync(&vm, vmax, sizeof(vm), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    int bits = 0;
-    while (bits < 32 && (vm >> bits)) ++bits;
-    uint32_t* kk = k0;
-    uint32_t* vv = v0;
-    e = radix_sort_u32(kk, vv, k1, v1, n, bits, ar, s, vmax + 1);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((n + FZ_CHUNK * 8 - 1) / (FZ_CHUNK * 8));
-    const float4* f4 = reinterpret_cast<const float4*>(f2d);
-    float4* a4 = reinterpret_cast<float4*>(acc);
-    if (quad_path(C, f2d, acc)) {
-        switch (C / 4) {
-            case 1: k_fuse_runs4<1><<<grid, 256, 0, s>>>(n, kk, vv, pw, f4, a4, wsum); break;
-            case 2: k_fuse_runs4<2><<<grid, 256, 0, s>>>(n, kk, vv, pw, f4, a4, wsum); break;
-            case 4: k_fuse_runs4<4><<<grid, 256, 0, s>>>(n, kk, vv, pw, f4, a4, wsum); break;
-            case 8: k_fuse_runs4<8><<<grid, 256, 0, s>>>(n, kk, vv, pw, f4, a4, wsum); break;
-            case 16: k_fuse_runs4<16><<<grid, 256, 0, s>>>(n, kk, vv, pw, f4, a4, wsum); break;
-            default: k_fuse_runs4<32><<<grid, 256, 0, s>>>(n, kk, vv, pw, f4, a4, wsum); break;
-        }
-    } else if (C <= 32) {
-        k_fuse_runs<1><<<grid, 256, 0, s>>>(n, kk, vv, pw, f2d, C, acc, wsum);
-    } else if (C <= 64) {
-        k_fuse_runs<2><<<grid, 256, 0, s>>>(n, kk, vv, pw, f2d, C, acc, wsum);
+    const int64_t n_chunks = (n_pix + FL_PIX - 1) / FL_PIX;
+    const int64_t tasks = n_chunks * ((C + FL_SW - 1) / FL_SW);
+    const int64_t cap = (int64_t)sm_count() * 3;  // three 66 KB blocks per SM
+    const unsigned grid = (unsigned)(tasks < cap ? tasks : cap);
+    const size_t smem = sizeof(FuseSmem);
+    // 16-byte copies of the 2-D features and vector atomics need 16-byte aligned rows of both arrays
+    const bool vec = C % 4 == 0 && ((reinterpret_cast<uintptr_t>(acc) | reinterpret_cast<uintptr_t>(f2d)) & 15) == 0;
+    cudaError_t e;
+    if (vec) {
+        e = cudaFuncSetAttribute(k_fuse_local<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) k_fuse_local<true><<<grid, FL_THREADS, smem, s>>>(n_pix, off, vox, wgt, f2d, C, acc, wsum);
     } else {
-        k_fuse_runs<4><<<grid, 256, 0, s>>>(n, kk, vv, pw, f2d, C, acc, wsum);
+        e = cudaFuncSetAttribute(k_fuse_local<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) k_fuse_local<false><<<grid, FL_THREADS, smem, s>>>(n_pix, off, vox, wgt, f2d, C, acc, wsum);
     }
+    if (e != cudaSuccess) return e;
     count_launches(1);
-    e = cudaGetLastError();
-    // the sort's own wait flag: a run-out look-back left the slots unsorted and the sums wrong
-    uint32_t flag = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, vmax + 1, sizeof(flag), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    *sort_timeout = flag != 0;
-    return e;
+    return cudaGetLastError();
 }
 
 }  // namespace dv

@@ -254,10 +254,9 @@ cudaError_t launch_sh_bwd(const BatchParams& bp, const uint32_t* sorted_g, int64
 // feature fields over a weights export (see dv_features.cu)
 cudaError_t launch_feat_render(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt,
                                const float* feat, int C, float* out, cudaStream_t s);
-// sorts the slots by voxel (scratch from ar; reads the slot count back, so it synchronises s);
-// *sort_timeout (host) is set when the sort's bounded wait ran out (read after a final synchronisation)
+// one launch, no scratch and no synchronisation (chunks of consecutive pixels grouped in shared memory)
 cudaError_t feat_fuse(int64_t n_pix, const int64_t* off, const uint32_t* vox, const float* wgt, const float* f2d,
-                      int C, float* acc, float* wsum, Arena& ar, cudaStream_t s, bool* sort_timeout);
+                      int C, float* acc, float* wsum, cudaStream_t s);
 
 // LiDAR-guided initialisation (see dv_init.cu); the calls that return a size synchronise the stream.
 // The calls that sort set *sort_timeout (host) when the sort's bounded wait ran out; they synchronise
