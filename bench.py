@@ -679,11 +679,13 @@ def run_ours(args):
         feats = {"what": "weights export of the frame, then a 64-channel feature render and 2-D feature fusion",
                  "slots": slots, "export_us": 1e3 * t_ex / reps, "render64_us": 1e3 * t_r / reps,
                  "fuse64_us": 1e3 * t_fu / reps,
-                 "render64_gbs": (slots * (8 + 64 * 4) + n_pix * 64 * 4) / (t_r / reps * 1e-3) / 1e9,
-                 "fuse64_gbs": (slots * (8 + 64 * 4) + n_pix * 64 * 4) / (t_fu / reps * 1e-3) / 1e9,
-                 "bytes_model": ("per slot its (voxel, weight) and one 64-float feature row (the voxel's for the "
-                                 "render, the pixel's for the fusion), plus one 64-float row per pixel; rows are "
-                                 "counted once per slot (no reuse)")}
+                 # unique bytes: the slots once, one 64-float row per pixel once, and one 64-float row per
+                 # visible voxel (read for the render; read and written by the fusion's additions)
+                 "render64_gbs": (slots * 8 + n_pix * 64 * 4 + stats["n_visible"] * 64 * 4) / (t_r / reps * 1e-3) / 1e9,
+                 "fuse64_gbs": (slots * 8 + n_pix * 64 * 4 + 2 * stats["n_visible"] * 64 * 4) / (t_fu / reps * 1e-3) / 1e9,
+                 "bytes_model": ("unique bytes: per slot its (voxel, weight) once, one 64-float row per pixel "
+                                 "(written by the render, read by the fusion) and one 64-float row per visible voxel "
+                                 "(read by the render, read and written by the fusion)")}
         feats["render64_hbm_frac"] = feats["render64_gbs"] / pk["hbm_gbs"]
         feats["fuse64_hbm_frac"] = feats["fuse64_gbs"] / pk["hbm_gbs"]
 
