@@ -212,7 +212,7 @@ STAGE_KERNELS = {
     "sort_vox": (("k_os_pass<unsigned long",), ("dv_scan_sort.cu", "dv_internal.cuh")),
     "records": (("k_records_emit",), ("dv_project.cu", "dv_internal.cuh")),
     "sort_pairs": (("k_os_pass<unsigned int",), ("dv_scan_sort.cu", "dv_internal.cuh")),
-    "ranges": (("k_pair_mask", "k_tile_order"), ("dv_project.cu", "dv_internal.cuh")),
+    "ranges": (("k_pair_mask", "k_tile_count", "k_tile_scatter"), ("dv_project.cu", "dv_internal.cuh")),
     "composite_fwd": (("k_composite<0",), ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")),
     "composite_bwd": (("k_composite<1",), ("dv_composite.cu", "dv_internal.cuh", "dv_project.cu")),
     "sh_bwd": (("k_sh_bwd",), ("dv_composite.cu", "dv_internal.cuh")),

@@ -86,13 +86,15 @@ __global__ void __launch_bounds__(FT_WARPS * 32) k_feat_render4(int64_t n_pix, c
 //  * The slots, FL_PIECE at a time, get a row from an open-addressing table keyed by the voxel
 //    index (compare-and-swap inserts, FL_ROWS rows); a voxel that finds no row within FL_PROBES
 //    probes goes to the overflow row, whose slots are added to the global sums one by one.
-//  * A counting sort by row groups the piece's slots; warp w then takes rows w, w + 8, ...: its two
-//    16-lane halves walk alternate slots of the row, a lane holding a 4-channel quad of the sums in
-//    registers, and the halves' sums are added by shuffles before one atomic add per quad.
+//  * A counting sort by row groups the piece's slots and lists the rows that hold any; warp w takes
+//    listed rows w, w + 8, ...: its four 8-lane groups walk every fourth slot of the row, a lane
+//    holding two 4-channel quads of the sums in registers, and the groups' sums are added by
+//    shuffles before one atomic add per quad.
 constexpr int FL_PIX = 128;     // pixels per chunk
 constexpr int FL_SW = 64;       // channels per slice (16 quads)
-constexpr int FL_ROWS = 255;    // voxel rows; row FL_ROWS holds the overflow slots
-constexpr int FL_PIECE = 3072;  // slots grouped at once (three 59 KB blocks fit an SM)
+constexpr int FL_ROWS = 1023;   // voxel rows; row FL_ROWS holds the overflow slots
+constexpr int FL_TE = FL_ROWS + 1;  // table entries, FL_TE / FL_THREADS per thread in the scan
+constexpr int FL_PIECE = 3072;  // slots grouped at once (three 70 KB blocks fit an SM)
 constexpr int FL_PROBES = 32;
 constexpr int FL_THREADS = 256;
 constexpr int FL_SPT = FL_PIECE / FL_THREADS;  // slots per thread and piece
@@ -102,9 +104,12 @@ struct FuseSmem {
     float4 f[FL_PIX][FL_SW / 4];      // 2-D features of the chunk's pixels, this slice
     int64_t off[FL_PIX + 1];          // slot offsets of the chunk's pixels
     uint32_t key[FL_ROWS];            // voxel of each row (FL_EMPTY: free)
-    uint32_t cnt[FL_ROWS + 1];        // slots per row, then the fill cursors
-    uint32_t start[FL_ROWS + 2];      // first grouped slot of each row
-    uint32_t wtot[FL_THREADS / 32];   // scan: warp totals
+    uint32_t cnt[FL_TE];              // slots per row, then the fill cursors
+    uint32_t start[FL_TE + 1];        // first grouped slot of each row
+    uint16_t occ[FL_TE];              // the rows that hold slots, in row order
+    uint32_t n_occ;
+    uint32_t wtot[FL_THREADS / 32];   // scan: warp totals (slots, then rows)
+    uint32_t wocc[FL_THREADS / 32];
     float sw[FL_PIECE];               // grouped by row: the slot's weight,
     uint16_t order[FL_PIECE];         //   its index in the piece,
     uint8_t spl[FL_PIECE];            //   and its pixel within the chunk
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(FL_THREADS, 3) k_fuse_local(int64_t n_pix, con
     extern __shared__ __align__(16) unsigned char fl_raw[];
     FuseSmem& S = *reinterpret_cast<FuseSmem*>(fl_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int q = lane & 15, g = lane >> 4;  // channel quad, half-warp
+    const int q0 = 2 * (lane & 7), g = lane >> 3;  // first of the lane's two channel quads, 8-lane group
     for (int i = tid; i < FL_ROWS; i += FL_THREADS) S.key[i] = FL_EMPTY;
     const int64_t n_chunks = (n_pix + FL_PIX - 1) / FL_PIX;
     const int n_slices = (C + FL_SW - 1) / FL_SW;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(FL_THREADS, 3) k_fuse_local(int64_t n_pix, con
         const int64_t e_end = S.off[np];
         for (int64_t e0 = S.off[0]; e0 < e_end; e0 += FL_PIECE) {
             const int ns = (int)min((int64_t)FL_PIECE, e_end - e0);
-            for (int i = tid; i <= FL_ROWS; i += FL_THREADS) S.cnt[i] = 0;
+            for (int i = tid; i < FL_TE; i += FL_THREADS) S.cnt[i] = 0;
             // this thread's slots tid + j * FL_THREADS: loads first (all in flight together)
             uint32_t v_[FL_SPT], r_[FL_SPT];
             float w_[FL_SPT];
@@ -222,24 +227,49 @@ __global__ void __launch_bounds__(FL_THREADS, 3) k_fuse_local(int64_t n_pix, con
                 }
             }
             __syncthreads();
-            // exclusive scan of the FL_ROWS + 1 row counts (one per thread)
+            // exclusive scan of the FL_TE row counts (FL_TE / FL_THREADS consecutive entries per thread),
+            // and the list of the rows that hold slots
             {
-                const uint32_t x = tid <= FL_ROWS ? S.cnt[tid] : 0u;
-                uint32_t inc = x;
+                constexpr int EPT = FL_TE / FL_THREADS;
+                uint32_t c[EPT], sum = 0, nocc = 0;
+#pragma unroll
+                for (int t = 0; t < EPT; ++t) {
+                    c[t] = S.cnt[tid * EPT + t];
+                    sum += c[t];
+                    nocc += c[t] ? 1u : 0u;
+                }
+                uint32_t inc = sum, ino = nocc;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-                    if (lane >= d) inc += y;
+                    const uint32_t z = __shfl_up_sync(0xffffffffu, ino, d);
+                    if (lane >= d) {
+                        inc += y;
+                        ino += z;
+                    }
                 }
-                if (lane == 31) S.wtot[warp] = inc;
+                if (lane == 31) {
+                    S.wtot[warp] = inc;
+                    S.wocc[warp] = ino;
+                }
                 __syncthreads();
-                uint32_t base = 0;
-                for (int i = 0; i < warp; ++i) base += S.wtot[i];
-                if (tid <= FL_ROWS) {
-                    S.start[tid] = base + inc - x;
-                    S.cnt[tid] = 0;
+                uint32_t base = inc - sum, bo = ino - nocc;
+                for (int w = 0; w < warp; ++w) {
+                    base += S.wtot[w];
+                    bo += S.wocc[w];
                 }
-                if (tid == FL_ROWS) S.start[FL_ROWS + 1] = base + inc;
+#pragma unroll
+                for (int t = 0; t < EPT; ++t) {
+                    const int r = tid * EPT + t;
+                    S.start[r] = base;
+                    S.cnt[r] = 0;
+                    if (c[t]) S.occ[bo++] = (uint16_t)r;
+                    base += c[t];
+                }
+                if (tid == FL_THREADS - 1) {
+                    S.start[FL_TE] = base;
+                    S.n_occ = bo;
+                }
             }
             __syncthreads();
             // group the slots by row
@@ -256,36 +286,53 @@ __global__ void __launch_bounds__(FL_THREADS, 3) k_fuse_local(int64_t n_pix, con
             }
             if (VEC && e0 == S.off[0]) fl_cp_async_wait_all();  // the feature slice has landed
             __syncthreads();
-            // per row: the two halves of the warp take alternate slots, sums in registers
-            for (int r = warp; r <= FL_ROWS; r += FL_THREADS / 32) {
+            // per row with slots: the warp's four 8-lane groups take every fourth slot, a lane holding
+            // two 4-channel quads (q0, q0 + 1) of the sums in registers
+            const uint32_t n_occ = S.n_occ;
+            for (uint32_t oi = warp; oi < n_occ; oi += FL_THREADS / 32) {
+                const uint32_t r = S.occ[oi];
                 const uint32_t s0 = S.start[r], s1 = S.start[r + 1];
-                if (s0 == s1) continue;
                 if (r < FL_ROWS) {
-                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
                     float ws = 0.0f;
-#pragma unroll 4
-                    for (uint32_t i = s0 + g; i < s1; i += 2) {
+#pragma unroll 2
+                    for (uint32_t i = s0 + g; i < s1; i += 4) {
                         const float wv = S.sw[i];
-                        fl_add4(a, wv, S.f[S.spl[i]][q]);
+                        const float4* fr = S.f[S.spl[i]];
+                        fl_add4(a, wv, fr[q0]);
+                        fl_add4(b, wv, fr[q0 + 1]);
                         ws += wv;
                     }
-                    a.x += __shfl_xor_sync(0xffffffffu, a.x, 16);
-                    a.y += __shfl_xor_sync(0xffffffffu, a.y, 16);
-                    a.z += __shfl_xor_sync(0xffffffffu, a.z, 16);
-                    a.w += __shfl_xor_sync(0xffffffffu, a.w, 16);
-                    ws += __shfl_xor_sync(0xffffffffu, ws, 16);
+#pragma unroll
+                    for (int d = 8; d < 32; d <<= 1) {
+                        a.x += __shfl_xor_sync(0xffffffffu, a.x, d);
+                        a.y += __shfl_xor_sync(0xffffffffu, a.y, d);
+                        a.z += __shfl_xor_sync(0xffffffffu, a.z, d);
+                        a.w += __shfl_xor_sync(0xffffffffu, a.w, d);
+                        b.x += __shfl_xor_sync(0xffffffffu, b.x, d);
+                        b.y += __shfl_xor_sync(0xffffffffu, b.y, d);
+                        b.z += __shfl_xor_sync(0xffffffffu, b.z, d);
+                        b.w += __shfl_xor_sync(0xffffffffu, b.w, d);
+                        ws += __shfl_xor_sync(0xffffffffu, ws, d);
+                    }
                     const uint32_t v = S.key[r];
-                    if (g == 0) fl_flush4<VEC>(acc, v, C, c0 + 4 * q, a);
+                    if (g == 0) {
+                        fl_flush4<VEC>(acc, v, C, c0 + 4 * q0, a);
+                        fl_flush4<VEC>(acc, v, C, c0 + 4 * q0 + 4, b);
+                    }
                     if (lane == 0 && wsum && c0 == 0 && ws != 0.0f) atomicAdd(wsum + v, ws);
                 } else {
                     // overflow row: every slot added on its own
-                    for (uint32_t i = s0 + g; i < s1; i += 2) {
+                    for (uint32_t i = s0 + g; i < s1; i += 4) {
                         const float wv = S.sw[i];
                         const uint32_t v = __ldg(vox + e0 + S.order[i]);
-                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                        fl_add4(a, wv, S.f[S.spl[i]][q]);
-                        fl_flush4<VEC>(acc, v, C, c0 + 4 * q, a);
-                        if (q == 0 && wsum && c0 == 0 && wv != 0.0f) atomicAdd(wsum + v, wv);
+                        const float4* fr = S.f[S.spl[i]];
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                        fl_add4(a, wv, fr[q0]);
+                        fl_add4(b, wv, fr[q0 + 1]);
+                        fl_flush4<VEC>(acc, v, C, c0 + 4 * q0, a);
+                        fl_flush4<VEC>(acc, v, C, c0 + 4 * q0 + 4, b);
+                        if (q0 == 0 && wsum && c0 == 0 && wv != 0.0f) atomicAdd(wsum + v, wv);
                     }
                 }
             }
