@@ -962,6 +962,62 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
     stream(s_sub[0], s_sub[1], [&](int slot, uint32_t c0, unsigned m) -> bool {
         // one record of the batch, visited by the whole warp: actor entries, stop rule, gradients
         auto visit = [&](uint32_t j) {
+            if constexpr (BWD && NTA == 0 && KS == 1) {
+                // plain tiles, one sample per segment: a lane meets a record at most once, so once any lane
+                // of the warp hits it every lane runs the same arithmetic without branches, a lane that
+                // misses (or is done) on the empty segment [0, 0], whose optical depth, weight and gradient
+                // are exactly zero; the gradient values are written, not accumulated, so nothing is cleared
+                const float4 g = s_rec[slot][j][0];
+                const bool live = !ps.done;
+                float t_in, t_out;
+                const bool xs = slab_cube(ib, g, t_in, t_out);
+                t_in = fmaxf(fmaxf(t_in, t_near), tau_cur);
+                t_out = fminf(t_out, t_far);
+                const bool hit = live && xs && t_out > t_in;
+                ps.tests += live ? 1u : 0u;
+                if (!__any_sync(0xffffffffu, hit)) return;
+                const float u0 = hit ? t_in : 0.0f, u1 = hit ? t_out : 0.0f;
+                const float4 da = s_rec[slot][j][1], dd = s_rec[slot][j][2], col = s_rec[slot][j][3];
+                const float4 nv = staged_nv(slot, j);
+                const float rel[3] = {g.x, g.y, g.z};
+                float sxyz[4];
+                const float tau = seg_tau<true, 1>(da, dd, col.w, rel, db_, u0, u1, bp.K, bp.inv_k, bp.activation,
+                                                   nullptr, sxyz);
+                const float e = __expf(-tau);
+                const float w = ps.T * (1.0f - e);
+                const float mid = 0.5f * (u0 + u1);
+                float sg = fmaf(bw.g0, col.x, fmaf(bw.g1, col.y, fmaf(bw.g2, col.z, bw.gD * mid)));
+                if constexpr (NRM) sg = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, sg)));
+                ps.R = fmaf(w, sg, ps.R);
+                ps.T = ps.T * e;
+                ps.n += hit ? 1u : 0u;
+                const float gt = fmaf(ps.T, sg, bw.base + ps.R);
+                float acc[NV];
+                {
+                    const float a = gt * sxyz[0];
+                    const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
+                    const float2 xw = make_float2(1.0f - x, x);
+                    const float2 ay = __fmul2_rn(make_float2(a, a), make_float2(1.0f - y, y));
+                    const float2 cz0 = __fmul2_rn(ay, make_float2(1.0f - z, 1.0f - z));
+                    const float2 cz1 = __fmul2_rn(ay, make_float2(z, z));
+                    float2 r;
+                    r = __fmul2_rn(xw, make_float2(cz0.x, cz0.x)); acc[0] = r.x; acc[1] = r.y;
+                    r = __fmul2_rn(xw, make_float2(cz0.y, cz0.y)); acc[2] = r.x; acc[3] = r.y;
+                    r = __fmul2_rn(xw, make_float2(cz1.x, cz1.x)); acc[4] = r.x; acc[5] = r.y;
+                    r = __fmul2_rn(xw, make_float2(cz1.y, cz1.y)); acc[6] = r.x; acc[7] = r.y;
+                    acc[8] = bw.g0 * w;
+                    acc[9] = bw.g1 * w;
+                    acc[10] = bw.g2 * w;
+                    if constexpr (NRM) {
+                        acc[NRM ? 11 : 0] = bw.gN0 * w;
+                        acc[NRM ? 12 : 0] = bw.gN1 * w;
+                        acc[NRM ? 13 : 0] = bw.gN2 * w;
+                    }
+                }
+                if (ps.T < bp.eps_stop) ps.done = true;
+                warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
+                return;
+            }
             float acc[NV];
             if (BWD) {
 #pragma unroll
