@@ -188,7 +188,7 @@ def stage_models(stats, work, n_vox_total, n_pix, K, sh_bytes_per_vox, key_bits)
     tb = max(1, math.ceil(math.log2(max(T, 2)) / 8))
     tests, boxes, segs = work["tests"], work["box_tests"], work["segments"]
     return {
-        "project": ("hbm", V * 32 + nv * 24),
+        "project": ("hbm", V * 8 + nv * 24),  # each voxel's 8-byte key; per visible voxel key, index, count, rectangle
         "records": ("hbm", nv * (4 + 8 + 4 + 8 + 32 + sh_bytes_per_vox + 64 + 8) + P * 8),
         "sort_vox": ("hbm", vb * nv * 24),
         "sort_pairs": ("hbm", tb * P * 16),
