@@ -121,10 +121,11 @@ def test_colour_features_reproduce_the_render(dv):
 @pytest.mark.parametrize("Cc", [1, 4, 8, 16, 32, 40, 64, 100, 128, 300])
 def test_feature_kernels_on_synthetic_slots(dv, Cc):
     # Slot lists with the export's layout but chosen to reach every kernel path: a skewed voxel
-    # mix (a few voxels own thousands of slots, so their runs cross the 256-slot chunks of the
-    # fusion), empty pixels, zero weights, and channel counts for the 16-byte and the scalar
-    # render paths and for one, two and four channels per lane (300: several passes).  The
-    # sums are plain definitions, compared with FP64 numpy.
+    # mix (a few voxels own thousands of slots; the rest are spread over 5,000 voxels, so a
+    # 128-pixel chunk of the fusion holds about 5,000 slots in two pieces over more distinct voxels
+    # than its 1,023-row table, and the overflow row is used), empty pixels, zero weights, and
+    # channel counts for the 16-byte and the scalar paths of both kernels (300: five 64-channel
+    # slices of the fusion).  The sums are plain definitions, compared with FP64 numpy.
     import torch
     import paper_2606_23031_gb300 as m
     rng = np.random.default_rng(70 + Cc)
