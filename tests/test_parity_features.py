@@ -122,8 +122,9 @@ def test_colour_features_reproduce_the_render(dv):
 def test_feature_kernels_on_synthetic_slots(dv, Cc):
     # Slot lists with the export's layout but chosen to reach every kernel path: a skewed voxel
     # mix (a few voxels own thousands of slots; the rest are spread over 5,000 voxels, so a
-    # 128-pixel chunk of the fusion holds about 5,000 slots in two pieces over more distinct voxels
-    # than its 1,023-row table, and the overflow row is used), empty pixels, zero weights, and
+    # 128-pixel chunk of the fusion holds about 2,200 slots over more distinct voxels than its
+    # 1,023-row table, and the overflow row is used; the first chunk holds about 5,700 slots, more
+    # than one 3,072-slot piece), empty pixels, zero weights, and
     # channel counts for the 16-byte and the scalar paths of both kernels (300: five 64-channel
     # slices of the fusion).  The sums are plain definitions, compared with FP64 numpy.
     import torch
@@ -132,6 +133,7 @@ def test_feature_kernels_on_synthetic_slots(dv, Cc):
     P, nv = 3000, 5000
     cnt = rng.integers(0, 40, size=P)
     cnt[rng.random(P) < 0.1] = 0
+    cnt[:128] = rng.integers(30, 60, size=128)  # the first 128-pixel chunk of the fusion: two pieces
     off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
     n = int(off[-1])
     heavy = rng.integers(0, nv, size=4)
