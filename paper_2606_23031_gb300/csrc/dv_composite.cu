@@ -369,6 +369,57 @@ __device__ __forceinline__ void add_segment(Pix<NRM>& ps, const Bwd<NRM>& bw, co
     if (STOP && ps.T < bp.eps_stop) ps.done = true;
 }
 
+// One backward step in residual form with one sample, for a lane that meets the record at most once
+// (a plain tile, or one actor interval): [u0, u1] is the lane's segment, the empty segment [0, 0] for a
+// lane that misses or has finished (zero optical depth, weight and gradient, state unchanged).  The
+// record's gradient values (8 densities, 3 colour, + 3 normal) are written into acc, not added, so the
+// caller clears nothing and the warp runs it without branches once any lane hits.
+template <bool NRM>
+__device__ __forceinline__ void bwd_single_step(Pix<NRM>& ps, const Bwd<NRM>& bw, const BatchParams& bp, float4 g,
+                                                float4 da, float4 dd, float4 col, float4 nv, const float* d, float u0,
+                                                float u1, bool hit, float* acc) {
+    const float rel[3] = {g.x, g.y, g.z};
+    float sxyz[4];
+    const float tau = seg_tau<true, 1>(da, dd, col.w, rel, d, u0, u1, bp.K, bp.inv_k, bp.activation, nullptr, sxyz);
+    const float e = __expf(-tau);
+    const float w = ps.T * (1.0f - e);
+    const float mid = 0.5f * (u0 + u1);
+    float sg = fmaf(bw.g0, col.x, fmaf(bw.g1, col.y, fmaf(bw.g2, col.z, bw.gD * mid)));
+    if constexpr (NRM) sg = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, sg)));
+    ps.R = fmaf(w, sg, ps.R);
+    ps.T = ps.T * e;
+    ps.n += hit ? 1u : 0u;
+    const float gt = fmaf(ps.T, sg, bw.base + ps.R);
+    const float a = gt * sxyz[0];
+    const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
+    const float2 xw = make_float2(1.0f - x, x);
+    const float2 ay = __fmul2_rn(make_float2(a, a), make_float2(1.0f - y, y));
+    const float2 cz0 = __fmul2_rn(ay, make_float2(1.0f - z, 1.0f - z));
+    const float2 cz1 = __fmul2_rn(ay, make_float2(z, z));
+    float2 r;
+    r = __fmul2_rn(xw, make_float2(cz0.x, cz0.x));
+    acc[0] = r.x;
+    acc[1] = r.y;
+    r = __fmul2_rn(xw, make_float2(cz0.y, cz0.y));
+    acc[2] = r.x;
+    acc[3] = r.y;
+    r = __fmul2_rn(xw, make_float2(cz1.x, cz1.x));
+    acc[4] = r.x;
+    acc[5] = r.y;
+    r = __fmul2_rn(xw, make_float2(cz1.y, cz1.y));
+    acc[6] = r.x;
+    acc[7] = r.y;
+    acc[8] = bw.g0 * w;
+    acc[9] = bw.g1 * w;
+    acc[10] = bw.g2 * w;
+    if constexpr (NRM) {
+        acc[NRM ? 11 : 0] = bw.gN0 * w;
+        acc[NRM ? 12 : 0] = bw.gN1 * w;
+        acc[NRM ? 13 : 0] = bw.gN2 * w;
+    }
+    if (ps.T < bp.eps_stop) ps.done = true;
+}
+
 // next actor interval ahead of tau_cur (first-entered box owns overlaps)
 __device__ __forceinline__ ActInt next_interval(const OctParams* __restrict__ vo, float t_near, float t_far,
                                                 const int16_t* tact, int n_ta, const float* dc, float tau_cur) {
@@ -810,6 +861,68 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                 if (__all_sync(0xffffffffu, pt.done)) return true;
                 const uint32_t j = c0 + (uint32_t)(__ffs(m) - 1);
                 m &= m - 1;
+                if constexpr (!G && !X && KS == 1) {
+                    if (m) {
+                        // two records at once (no gradients): both slab tests and optical depths, then the
+                        // two compositing steps in list order with the stop rule -- the arithmetic of two
+                        // single steps, with more independent work per warp on the actor walks
+                        const uint32_t j1 = c0 + (uint32_t)(__ffs(m) - 1);
+                        m &= m - 1;
+                        const float4 g0 = s_rec[slot][j][0], g1 = s_rec[slot][j1][0];
+                        float u0, v0, u1, v1;
+                        const bool x0 = slab_cube(inv, g0, u0, v0), x1 = slab_cube(inv, g1, u1, v1);
+                        u0 = fmaxf(u0, a);
+                        v0 = fminf(v0, b);
+                        u1 = fmaxf(u1, a);
+                        v1 = fminf(v1, b);
+                        const bool live = !pt.done;
+                        const bool h0 = live && x0 && v0 > u0, h1 = live && x1 && v1 > u1;
+                        const float s0 = h0 ? u0 : 0.0f, e0 = h0 ? v0 : 0.0f, s1 = h1 ? u1 : 0.0f, e1 = h1 ? v1 : 0.0f;
+                        const float4 col0 = s_rec[slot][j][3], col1 = s_rec[slot][j1][3];
+                        const float r0[3] = {g0.x, g0.y, g0.z}, r1[3] = {g1.x, g1.y, g1.z};
+                        const float tau0 = seg_tau<false, 1>(s_rec[slot][j][1], s_rec[slot][j][2], col0.w, r0, d, s0,
+                                                             e0, bp.K, bp.inv_k, bp.activation, nullptr, nullptr);
+                        const float tau1 = seg_tau<false, 1>(s_rec[slot][j1][1], s_rec[slot][j1][2], col1.w, r1, d, s1,
+                                                             e1, bp.K, bp.inv_k, bp.activation, nullptr, nullptr);
+                        auto apply = [&](float tau, float4 col, float4 nv, float t0, float t1) {
+                            if constexpr (RFORM) {
+                                const float ee = __expf(-tau);
+                                const float w = pt.T * (1.0f - ee);
+                                const float mid = 0.5f * (t0 + t1);
+                                float sg = fmaf(bw.g0, col.x, fmaf(bw.g1, col.y, fmaf(bw.g2, col.z, bw.gD * mid)));
+                                if constexpr (NRM) sg = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, sg)));
+                                pt.R = fmaf(w, sg, pt.R);
+                                pt.T = pt.T * ee;
+                                pt.n += 1;
+                                if (pt.T < bp.eps_stop) pt.done = true;
+                            } else {
+                                composite_tau<NRM>(pt, tau, col, nv, t0, t1, bp.eps_stop);
+                            }
+                        };
+                        pt.tests += live ? 1u : 0u;
+                        if (h0) apply(tau0, col0, staged_nv(slot, j), s0, e0);
+                        pt.tests += (live && !pt.done) ? 1u : 0u;
+                        if (h1 && !pt.done) apply(tau1, col1, staged_nv(slot, j1), s1, e1);
+                        continue;
+                    }
+                }
+                if constexpr (G && RFORM && !X && KS == 1) {
+                    // replay with gradients: inside one actor interval a lane meets a record at most once
+                    const float4 g = s_rec[slot][j][0];
+                    const bool live = !pt.done;
+                    float t0, t1;
+                    const bool xs = slab_cube(inv, g, t0, t1);
+                    t0 = fmaxf(t0, a);
+                    t1 = fminf(t1, b);
+                    const bool hit = live && xs && t1 > t0;
+                    pt.tests += live ? 1u : 0u;
+                    if (!__any_sync(0xffffffffu, hit)) continue;
+                    float acc[NV];
+                    bwd_single_step<NRM>(pt, bw, bp, g, s_rec[slot][j][1], s_rec[slot][j][2], s_rec[slot][j][3],
+                                         staged_nv(slot, j), d, hit ? t0 : 0.0f, hit ? t1 : 0.0f, hit, acc);
+                    warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
+                    continue;
+                }
                 float acc[NV];
                 if (G) {
 #pragma unroll
@@ -977,44 +1090,9 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                 ps.tests += live ? 1u : 0u;
                 if (!__any_sync(0xffffffffu, hit)) return;
                 const float u0 = hit ? t_in : 0.0f, u1 = hit ? t_out : 0.0f;
-                const float4 da = s_rec[slot][j][1], dd = s_rec[slot][j][2], col = s_rec[slot][j][3];
-                const float4 nv = staged_nv(slot, j);
-                const float rel[3] = {g.x, g.y, g.z};
-                float sxyz[4];
-                const float tau = seg_tau<true, 1>(da, dd, col.w, rel, db_, u0, u1, bp.K, bp.inv_k, bp.activation,
-                                                   nullptr, sxyz);
-                const float e = __expf(-tau);
-                const float w = ps.T * (1.0f - e);
-                const float mid = 0.5f * (u0 + u1);
-                float sg = fmaf(bw.g0, col.x, fmaf(bw.g1, col.y, fmaf(bw.g2, col.z, bw.gD * mid)));
-                if constexpr (NRM) sg = fmaf(bw.gN0, nv.x, fmaf(bw.gN1, nv.y, fmaf(bw.gN2, nv.z, sg)));
-                ps.R = fmaf(w, sg, ps.R);
-                ps.T = ps.T * e;
-                ps.n += hit ? 1u : 0u;
-                const float gt = fmaf(ps.T, sg, bw.base + ps.R);
                 float acc[NV];
-                {
-                    const float a = gt * sxyz[0];
-                    const float x = sxyz[1], y = sxyz[2], z = sxyz[3];
-                    const float2 xw = make_float2(1.0f - x, x);
-                    const float2 ay = __fmul2_rn(make_float2(a, a), make_float2(1.0f - y, y));
-                    const float2 cz0 = __fmul2_rn(ay, make_float2(1.0f - z, 1.0f - z));
-                    const float2 cz1 = __fmul2_rn(ay, make_float2(z, z));
-                    float2 r;
-                    r = __fmul2_rn(xw, make_float2(cz0.x, cz0.x)); acc[0] = r.x; acc[1] = r.y;
-                    r = __fmul2_rn(xw, make_float2(cz0.y, cz0.y)); acc[2] = r.x; acc[3] = r.y;
-                    r = __fmul2_rn(xw, make_float2(cz1.x, cz1.x)); acc[4] = r.x; acc[5] = r.y;
-                    r = __fmul2_rn(xw, make_float2(cz1.y, cz1.y)); acc[6] = r.x; acc[7] = r.y;
-                    acc[8] = bw.g0 * w;
-                    acc[9] = bw.g1 * w;
-                    acc[10] = bw.g2 * w;
-                    if constexpr (NRM) {
-                        acc[NRM ? 11 : 0] = bw.gN0 * w;
-                        acc[NRM ? 12 : 0] = bw.gN1 * w;
-                        acc[NRM ? 13 : 0] = bw.gN2 * w;
-                    }
-                }
-                if (ps.T < bp.eps_stop) ps.done = true;
+                bwd_single_step<NRM>(ps, bw, bp, g, s_rec[slot][j][1], s_rec[slot][j][2], s_rec[slot][j][3],
+                                     staged_nv(slot, j), db_, u0, u1, hit, acc);
                 warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
                 return;
             }
