@@ -1096,6 +1096,29 @@ __global__ void __launch_bounds__(CT_THREADS, NTA ? ((BWD || WEX) ? DV_BWD_MIN_B
                 warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
                 return;
             }
+            if constexpr (BWD && NTA > 0 && KS == 1) {
+                // actor tiles: a background record that no lane's segment carries into the next actor
+                // interval is met at most once by every lane, so it takes the same branch-free step; a
+                // record some lane crosses an actor entry in goes through the general path below
+                const float4 g = s_rec[slot][j][0];
+                const bool live = !ps.done;
+                float t_in, t_out;
+                const bool xs = slab_cube(ib, g, t_in, t_out);
+                t_in = fmaxf(t_in, t_near);
+                t_out = fminf(t_out, t_far);
+                const bool in = live && xs && t_out > t_in;
+                if (!__any_sync(0xffffffffu, in && nxt.o >= 0 && nxt.a < t_out)) {
+                    const float cur = fmaxf(t_in, tau_cur);
+                    const bool hit = in && t_out > cur;
+                    ps.tests += live ? 1u : 0u;
+                    if (!__any_sync(0xffffffffu, hit)) return;
+                    float acc[NV];
+                    bwd_single_step<NRM>(ps, bw, bp, g, s_rec[slot][j][1], s_rec[slot][j][2], s_rec[slot][j][3],
+                                         staged_nv(slot, j), db_, hit ? cur : 0.0f, hit ? t_out : 0.0f, hit, acc);
+                    warp_reduce_add<NV>(acc, grad_rec + (size_t)s_r[slot][j] * GS);
+                    return;
+                }
+            }
             float acc[NV];
             if (BWD) {
 #pragma unroll
