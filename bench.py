@@ -957,7 +957,7 @@ def run_profile_pass(args):
     return 0
 
 
-def build_traffic(csv_path):
+def build_traffic(csv_path, out_path=TRAFFIC):
     """profiles/traffic.json and a markdown table (stdout) from an ncu --csv capture of one profiled pass
     (metrics dram__bytes_read.sum, dram__bytes_write.sum, gpu__time_duration.sum)."""
     import csv
@@ -1011,7 +1011,7 @@ def build_traffic(csv_path):
                            "source_hash": sources_hash(STAGE_KERNELS[st][1]), "kernels": r["kernels"]}
                       for st, r in stages.items()},
            "kernels": per_kernel}
-    with open(TRAFFIC, "w") as f:
+    with open(out_path, "w") as f:
         json.dump(out, f, indent=1)
     print("| kernel | launches | DRAM bytes (read + write) | ncu time (us, serialised) |")
     print("|---|---|---|---|")
