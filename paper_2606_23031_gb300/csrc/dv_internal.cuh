@@ -154,8 +154,6 @@ cudaError_t scan_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32
 // (the result is then not sorted); the device's wait-error word is set as well.
 cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
                            int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err = nullptr);
-cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err = nullptr);
 // streaming multiprocessors of the current device (cached per device)
 int sm_count();
 // test hook: one sort tile whose predecessor never publishes waits `spin_limit` reads and gives up;

@@ -643,12 +643,4 @@ cudaError_t radix_sort_u64(uint64_t*& keys, uint32_t*& vals, uint64_t* keys_alt,
     return radix_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
 }
 
-cudaError_t radix_sort_u32(uint32_t*& keys, uint32_t*& vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                           int n_bits, Arena& ar, cudaStream_t s, uint32_t* call_err) {
-    if (n <= 1 || n_bits <= 0) return cudaSuccess;
-    if (n < (int64_t)OS_VAL && (n_bits + 7) / 8 <= OS_MAX_PASSES)
-        return onesweep<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, call_err, ar, s);
-    return radix_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, n_bits, ar, s);
-}
-
 }  // namespace dv
