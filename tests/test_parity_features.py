@@ -118,15 +118,18 @@ def test_colour_features_reproduce_the_render(dv):
     assert err <= 1e-5, f"colour features vs RGB: {err:.3g}"
 
 
-@pytest.mark.parametrize("Cc", [1, 4, 8, 16, 32, 40, 64, 100, 128, 300])
-def test_feature_kernels_on_synthetic_slots(dv, Cc):
+@pytest.mark.parametrize("Cc,shift", [(1, 0), (4, 0), (8, 0), (16, 0), (32, 0), (40, 0), (64, 0), (64, 1), (100, 0),
+                                      (128, 0), (300, 0)])
+def test_feature_kernels_on_synthetic_slots(dv, Cc, shift):
     # Slot lists with the export's layout but chosen to reach every kernel path: a skewed voxel
     # mix (a few voxels own thousands of slots; the rest are spread over 5,000 voxels, so a
     # 128-pixel chunk of the fusion holds about 2,200 slots over more distinct voxels than its
     # 1,023-row table, and the overflow row is used; the first chunk holds about 5,700 slots, more
     # than one 3,072-slot piece), empty pixels, zero weights, and
     # channel counts for the 16-byte and the scalar paths of both kernels (300: five 64-channel
-    # slices of the fusion).  The sums are plain definitions, compared with FP64 numpy.
+    # slices of the fusion; shift 1: 64 channels in rows that are only 4-byte aligned, which the
+    # fusion must take through its scalar path).  The sums are plain definitions, compared with
+    # FP64 numpy.
     import torch
     import paper_2606_23031_gb300 as m
     rng = np.random.default_rng(70 + Cc)
@@ -147,7 +150,16 @@ def test_feature_kernels_on_synthetic_slots(dv, Cc):
     F = m.dv_features_render(W, dev(feat)).cpu().numpy()
     acc = torch.zeros((nv, Cc), device="cuda")
     wsum = torch.zeros(nv, device="cuda")
-    m.dv_features_fuse(W, dev(f2d), acc, wsum)
+    if shift:
+        # rows 4-byte aligned only (a view one float into a buffer): the fusion's scalar loads and atomics
+        buf = torch.zeros(P * Cc + shift, device="cuda")
+        f2d_d = buf[shift:].view(P, Cc)
+        f2d_d.copy_(dev(f2d))
+        acc_buf = torch.zeros(nv * Cc + shift, device="cuda")
+        acc = acc_buf[shift:].view(nv, Cc)
+    else:
+        f2d_d = dev(f2d)
+    m.dv_features_fuse(W, f2d_d, acc, wsum)
     torch.cuda.synchronize()
     w64 = np.float64(w)
     F_ref = np.zeros((P, Cc))
